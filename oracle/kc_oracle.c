@@ -1,0 +1,853 @@
+/*
+ * kc_oracle.c -- plain, slow CPU oracle for the reduced-space branch and bound
+ * for K-center clustering (Ren, You, Hua, Ji, Cao, "A Global Optimization
+ * Algorithm for K-Center Clustering of One Billion Samples").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file: only the tests, the smoke check and the CPU baseline leg of
+ * the benchmark do.  It shares no code with the CUDA library.
+ *
+ * Conventions
+ *   - X is row major, X[s*D + a] = x_{s,a}, in double.  Data stored in float
+ *     is promoted exactly to double before it reaches this file.
+ *   - A node is K boxes, lo[k*D + a] <= mu^k_a <= hi[k*D + a].
+ *   - All distances are squared Euclidean (Eq. 1).  Every distance is summed
+ *     over a = 0..D-1 in order, as acc = acc + d*d with two roundings (the
+ *     file is compiled with -ffp-contract=off).
+ *   - Ties in every argmax / argmin go to the smallest sample index.
+ *   - `active` (nullable) is the sample-reduction mask: only samples with
+ *     active[s] != 0 take part (Algorithm 5 deletes the others).
+ *
+ * Readings of the paper where it is silent or garbled are listed in the
+ * design notes; each one used here is named in the comment where it applies.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#define KCO_MAXK 16
+#define KCO_MAXD 64
+#define KCO_MAXREPS 50
+
+/* ---------------------------------------------------------------------- */
+/* Elementary pieces                                                       */
+/* ---------------------------------------------------------------------- */
+
+/* mid{l, x, h}: the median of three numbers (l <= h), the minimiser of
+ * (x - mu)^2 over mu in [l, h] (Section 3.1, analytic solution of Eq. 11). */
+static double mid3(double l, double x, double h)
+{
+    if (x < l) return l;
+    if (x > h) return h;
+    return x;
+}
+
+/* ||x - y||^2 summed in attribute order (Eq. 1). */
+static double sqdist(const double *x, const double *y, int D)
+{
+    double acc = 0.0;
+    for (int a = 0; a < D; ++a) {
+        double d = x[a] - y[a];
+        acc = acc + d * d;
+    }
+    return acc;
+}
+
+/* beta_s^k(M^k) = min over mu in M^k of ||x_s - mu||^2, Eq. 11, evaluated at
+ * its closed-form minimiser mu_a = mid{lo_a, x_a, hi_a}. */
+double kco_beta_sk(const double *x, const double *lo, const double *hi, int D)
+{
+    double acc = 0.0;
+    for (int a = 0; a < D; ++a) {
+        double mu = mid3(lo[a], x[a], hi[a]);
+        double d = x[a] - mu;
+        acc = acc + d * d;
+    }
+    return acc;
+}
+
+/* alpha_s(M^k) for one cluster: max over mu in M^k of ||x_s - mu||^2 (Eq. 13),
+ * attained at the corner mu_a = lo_a if |lo_a - x_a| > |hi_a - x_a| else hi_a. */
+static double farthest_corner_sk(const double *x, const double *lo, const double *hi, int D)
+{
+    double acc = 0.0;
+    for (int a = 0; a < D; ++a) {
+        double mu = (fabs(lo[a] - x[a]) > fabs(hi[a] - x[a])) ? lo[a] : hi[a];
+        double d = x[a] - mu;
+        acc = acc + d * d;
+    }
+    return acc;
+}
+
+static int is_active(const uint8_t *active, int64_t s) { return active == NULL || active[s] != 0; }
+
+static int in_box(const double *x, const double *lo, const double *hi, int D)
+{
+    for (int a = 0; a < D; ++a)
+        if (x[a] < lo[a] || x[a] > hi[a]) return 0;
+    return 1;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Root region M0 (Section 2.1)                                             */
+/* ---------------------------------------------------------------------- */
+
+/* M0: lo_a = min_s x_{s,a}, hi_a = max_s x_{s,a} (the same box for every k). */
+int kco_root_box(const double *X, int64_t N, int D, double *lo, double *hi)
+{
+    if (N <= 0 || D <= 0) return 1;
+    for (int a = 0; a < D; ++a) { lo[a] = X[a]; hi[a] = X[a]; }
+    for (int64_t s = 1; s < N; ++s)
+        for (int a = 0; a < D; ++a) {
+            double v = X[s * D + a];
+            if (v < lo[a]) lo[a] = v;
+            if (v > hi[a]) hi[a] = v;
+        }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Lower bound (Section 3.1)                                               */
+/* ---------------------------------------------------------------------- */
+
+/* beta(M) = max_s min_k beta_s^k(M^k)  (Eq. 9 with Eqs. 10-11).
+ * Writes the bound and the sample attaining it (-1 if no active sample). */
+int kco_lower_bound(const double *X, int64_t N, int D, int K, const double *lo, const double *hi,
+                    const uint8_t *active, double *beta, int64_t *argmax)
+{
+    double best = -1.0;
+    int64_t arg = -1;
+    for (int64_t s = 0; s < N; ++s) {
+        if (!is_active(active, s)) continue;
+        const double *x = X + s * D;
+        double bs = INFINITY;
+        for (int k = 0; k < K; ++k) {
+            double v = kco_beta_sk(x, lo + k * D, hi + k * D, D);
+            if (v < bs) bs = v;
+        }
+        if (bs > best) { best = bs; arg = s; }
+    }
+    *beta = arg < 0 ? 0.0 : best;
+    if (argmax) *argmax = arg;
+    return 0;
+}
+
+/* The lower bound of B nodes; node b's boxes start at lo + b*K*D. */
+int kco_lower_bounds(const double *X, int64_t N, int D, int K, const double *lo, const double *hi,
+                     int B, const uint8_t *active, double *beta, int64_t *argmax)
+{
+    for (int b = 0; b < B; ++b)
+        kco_lower_bound(X, N, D, K, lo + (int64_t)b * K * D, hi + (int64_t)b * K * D, active,
+                        beta + b, argmax ? argmax + b : NULL);
+    return 0;
+}
+
+/* The matrix beta_s^k (N x K, row major): test helper for the closed form. */
+int kco_beta_matrix(const double *X, int64_t N, int D, int K, const double *lo, const double *hi,
+                    double *out)
+{
+    for (int64_t s = 0; s < N; ++s)
+        for (int k = 0; k < K; ++k)
+            out[s * K + k] = kco_beta_sk(X + s * D, lo + k * D, hi + k * D, D);
+    return 0;
+}
+
+/* alpha_s(M) = min_k max over mu^k in M^k of ||x_s - mu^k||^2 (Eq. 13), N values. */
+int kco_alpha_s(const double *X, int64_t N, int D, int K, const double *lo, const double *hi,
+                double *out)
+{
+    for (int64_t s = 0; s < N; ++s) {
+        double best = INFINITY;
+        for (int k = 0; k < K; ++k) {
+            double v = farthest_corner_sk(X + s * D, lo + k * D, hi + k * D, D);
+            if (v < best) best = v;
+        }
+        out[s] = best;
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Upper bound (Section 3.2)                                               */
+/* ---------------------------------------------------------------------- */
+
+/* alpha = max_s min_k ||x_s - x_{c_k}||^2 for centers on samples c (Eq. 12 and
+ * the objective of Eq. 1).  Writes the value and the sample attaining it. */
+int kco_objective(const double *X, int64_t N, int D, int K, const int64_t *centers,
+                  const uint8_t *active, double *value, int64_t *argmax)
+{
+    double best = -1.0;
+    int64_t arg = -1;
+    for (int64_t s = 0; s < N; ++s) {
+        if (!is_active(active, s)) continue;
+        double q = INFINITY;
+        for (int k = 0; k < K; ++k) {
+            double v = sqdist(X + s * D, X + centers[k] * D, D);
+            if (v < q) q = v;
+        }
+        if (q > best) { best = q; arg = s; }
+    }
+    *value = arg < 0 ? 0.0 : best;
+    if (argmax) *argmax = arg;
+    return 0;
+}
+
+/* Candidate centre of one box (Section 3.2, children): the active sample
+ * inside [lo, hi] closest to the box midpoint (lo + hi) / 2.  -1 if the box
+ * holds no active sample.  (Reading: candidates are drawn from X cap M^k.) */
+int64_t kco_mid_candidate(const double *X, int64_t N, int D, const double *lo, const double *hi,
+                          const uint8_t *active, double *dist_out)
+{
+    double mid[KCO_MAXD];
+    for (int a = 0; a < D; ++a) mid[a] = 0.5 * (lo[a] + hi[a]);
+    double best = INFINITY;
+    int64_t arg = -1;
+    for (int64_t s = 0; s < N; ++s) {
+        if (!is_active(active, s)) continue;
+        const double *x = X + s * D;
+        if (!in_box(x, lo, hi, D)) continue;
+        double v = sqdist(x, mid, D);
+        if (v < best) { best = v; arg = s; }
+    }
+    if (dist_out) *dist_out = best;
+    return arg;
+}
+
+/* Farthest First Traversal, Algorithm 2: start at sample `start`, then add the
+ * sample farthest from the chosen set (d(x_s, T) = min over T) until |T| = K.
+ * Writes the K indices and the objective (Eq. 1) of the chosen set. */
+int kco_fft(const double *X, int64_t N, int D, int K, int64_t start, int64_t *centers, double *obj)
+{
+    double *dmin = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!dmin) return 2;
+    centers[0] = start;
+    for (int64_t s = 0; s < N; ++s) dmin[s] = sqdist(X + s * D, X + start * D, D);
+    for (int t = 1; t < K; ++t) {
+        double best = -1.0;
+        int64_t arg = 0;
+        for (int64_t s = 0; s < N; ++s)
+            if (dmin[s] > best) { best = dmin[s]; arg = s; }
+        centers[t] = arg;
+        for (int64_t s = 0; s < N; ++s) {
+            double v = sqdist(X + s * D, X + arg * D, D);
+            if (v < dmin[s]) dmin[s] = v;
+        }
+    }
+    double best = -1.0;
+    for (int64_t s = 0; s < N; ++s)
+        if (dmin[s] > best) best = dmin[s];
+    *obj = best;
+    free(dmin);
+    return 0;
+}
+
+/* Exact optimum of Eq. 1 by enumerating every K-subset of samples in
+ * lexicographic order (the first subset reaching the minimum is kept).
+ * Feasible only for tiny N. */
+int kco_bruteforce(const double *X, int64_t N, int D, int K, double *obj, int64_t *centers)
+{
+    if (K < 1 || K > KCO_MAXK || N < K) return 1;
+    int64_t c[KCO_MAXK];
+    for (int k = 0; k < K; ++k) c[k] = k;
+    double best = INFINITY;
+    for (;;) {
+        double v;
+        kco_objective(X, N, D, K, c, NULL, &v, NULL);
+        if (v < best) {
+            best = v;
+            for (int k = 0; k < K; ++k) centers[k] = c[k];
+        }
+        int i = K - 1;
+        while (i >= 0 && c[i] == N - K + i) --i;
+        if (i < 0) break;
+        ++c[i];
+        for (int j = i + 1; j < K; ++j) c[j] = c[j - 1] + 1;
+    }
+    *obj = best;
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Outward rounding to the data's precision                                */
+/* ---------------------------------------------------------------------- */
+
+/* Box bounds produced by bounds tightening are rounded outward to a value the
+ * data type can hold (float data: is_f32 = 1), so the tightened box always
+ * contains the exact real-number box (reading of Algorithm 4 under rounding). */
+static double round_down_dt(double v, int is_f32)
+{
+    if (!is_f32) return v;
+    float f = (float)v;
+    if ((double)f > v) f = nextafterf(f, -INFINITY);
+    return (double)f;
+}
+
+static double round_up_dt(double v, int is_f32)
+{
+    if (!is_f32) return v;
+    float f = (float)v;
+    if ((double)f < v) f = nextafterf(f, INFINITY);
+    return (double)f;
+}
+
+/* Branching value (Section 3.3): the midpoint of [lo, hi] in the data's
+ * precision; children are [lo, m] and [succ(m), hi] where succ is the next
+ * value of the data type, so every sample value lies in exactly one child and
+ * both children are strictly smaller than the parent (reading of the
+ * midpoint rule for finite precision).  Requires lo < hi. */
+static void split_point(double lo, double hi, int is_f32, double *m_out, double *succ_out)
+{
+    if (is_f32) {
+        float m = (float)(0.5 * (lo + hi));
+        if ((double)m >= hi) m = (float)lo;
+        if ((double)m < lo) m = (float)lo;
+        *m_out = (double)m;
+        *succ_out = (double)nextafterf(m, INFINITY);
+    } else {
+        double m = 0.5 * (lo + hi);
+        if (m >= hi) m = lo;
+        if (m < lo) m = lo;
+        *m_out = m;
+        *succ_out = nextafter(m, INFINITY);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Cluster assignment and bounds tightening (Section 4.1, Algorithms 3, 4) */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t status;                 /* 0 feasible, 1 infeasible (proved empty), 2 leaf */
+    double beta;                    /* node lower bound beta(M) over active samples */
+    int64_t beta_arg;
+    double lo[KCO_MAXK * KCO_MAXD]; /* tightened box */
+    double hi[KCO_MAXK * KCO_MAXD];
+    int64_t count[KCO_MAXK];        /* |S_+^k|: samples allowed as centre k */
+    int64_t cand[KCO_MAXK];         /* UB candidate per cluster (closest to box-BT midpoint) */
+    int64_t n_assigned[KCO_MAXK];   /* |J^k| after both assignment rules */
+    int32_t n_reps[KCO_MAXK];
+    int64_t reps[KCO_MAXK * KCO_MAXREPS];
+} kco_tighten_out;
+
+/* Representatives ("balls") of cluster k, from its assigned set: the seed of
+ * cluster k (if seeds exist), then for a = 0..D-1 the assigned samples with
+ * the smallest and the largest x_a (smallest index on ties), duplicates
+ * skipped, at most `cap` of them (reading of the 50-ball cap of Section
+ * 4.1.2).  `amin_idx`/`amax_idx` hold those arg-extremes ([D], -1 if none). */
+static int build_reps(int64_t seed_k, const int64_t *amin_idx, const int64_t *amax_idx, int D,
+                      int cap, int64_t *reps)
+{
+    int n = 0;
+#define KCO_ADD_REP(idx)                                            \
+    do {                                                            \
+        int64_t v_ = (idx);                                         \
+        if (v_ >= 0 && n < cap) {                                   \
+            int dup_ = 0;                                           \
+            for (int q_ = 0; q_ < n; ++q_) if (reps[q_] == v_) dup_ = 1; \
+            if (!dup_) reps[n++] = v_;                              \
+        }                                                           \
+    } while (0)
+    KCO_ADD_REP(seed_k);
+    for (int a = 0; a < D; ++a) {
+        KCO_ADD_REP(amin_idx[a]);
+        KCO_ADD_REP(amax_idx[a]);
+    }
+#undef KCO_ADD_REP
+    return n;
+}
+
+/* One node's cluster assignment and bounds tightening.
+ *
+ * Step A (Algorithm 3, center-based): for every active sample compute
+ *   beta_s^k; exclude k when beta_s^k > alpha (Lemma 1).  A sample with
+ *   exactly one cluster k' left is assigned to k'; with none left the node
+ *   cannot hold a solution of value <= alpha (infeasible).  J_A^k = seed of k
+ *   plus the samples assigned to k.
+ * Box-based BT (Section 4.1.2): M'^k = M^k cap [max_j x_j - r, min_j x_j + r]
+ *   over j in J_A^k, r = sqrt(alpha) rounded up, bounds rounded outward.
+ * Step B (Algorithm 3, sample-based, when every J_A^k is non-empty): an
+ *   unassigned sample is excluded from k when some representative j of k has
+ *   ||x_s - x_j||^2 > 4 alpha (Lemma 2); exactly one cluster left assigns it
+ *   (J_B), none left makes the node infeasible.
+ * Ball-based BT and "centers on samples" (Algorithm 4): S_+^k = active
+ *   samples in M'^k within sqrt(alpha) of every representative of k;
+ *   M^k_hat = bbox(S_+^k) cap box-BT over J_B^k.
+ * Also returns beta(M) (from step A's values), |S_+^k|, and the candidate
+ * centre per cluster: the sample of S_+^k closest to the midpoint of M'^k.
+ * A node whose tightened boxes all have zero range is a leaf (status 2).
+ */
+int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, const double *hi,
+                double alpha, const int64_t *seeds, const uint8_t *active, int is_f32,
+                int ball_cap, kco_tighten_out *out)
+{
+    if (K > KCO_MAXK || D > KCO_MAXD) return 1;
+    if (ball_cap > KCO_MAXREPS) ball_cap = KCO_MAXREPS;
+    const int KD = K * D;
+    int8_t *asg = (int8_t *)malloc((size_t)N);
+    if (!asg) return 2;
+    memset(out, 0, sizeof(*out));
+    out->status = 0;
+
+    /* step A */
+    double jmin[KCO_MAXK * KCO_MAXD], jmax[KCO_MAXK * KCO_MAXD];
+    int64_t jmin_i[KCO_MAXK * KCO_MAXD], jmax_i[KCO_MAXK * KCO_MAXD];
+    int64_t na[KCO_MAXK];
+    for (int i = 0; i < KD; ++i) { jmin[i] = INFINITY; jmax[i] = -INFINITY; jmin_i[i] = -1; jmax_i[i] = -1; }
+    for (int k = 0; k < K; ++k) na[k] = 0;
+    double beta = -1.0;
+    int64_t beta_arg = -1;
+    int infeasible = 0;
+    for (int64_t s = 0; s < N; ++s) {
+        asg[s] = -1;
+        if (!is_active(active, s)) continue;
+        const double *x = X + s * D;
+        double bmin = INFINITY;
+        int left = 0, kk = -1;
+        for (int k = 0; k < K; ++k) {
+            double v = kco_beta_sk(x, lo + k * D, hi + k * D, D);
+            if (v < bmin) bmin = v;
+            if (!(v > alpha)) { ++left; kk = k; }
+        }
+        if (bmin > beta) { beta = bmin; beta_arg = s; }
+        if (left == 0) infeasible = 1;
+        if (left == 1) asg[s] = (int8_t)kk;
+    }
+    if (seeds)
+        for (int k = 0; k < K; ++k) asg[seeds[k]] = (int8_t)k; /* seeds are assigned in every node */
+    for (int64_t s = 0; s < N; ++s) {
+        int k = asg[s];
+        if (k < 0) continue;
+        ++na[k];
+        const double *x = X + s * D;
+        for (int a = 0; a < D; ++a) {
+            int i = k * D + a;
+            if (x[a] < jmin[i]) { jmin[i] = x[a]; jmin_i[i] = s; }
+            if (x[a] > jmax[i]) { jmax[i] = x[a]; jmax_i[i] = s; }
+        }
+    }
+    out->beta = beta_arg < 0 ? 0.0 : beta;
+    out->beta_arg = beta_arg;
+
+    /* box-based BT over J_A */
+    double r = nextafter(sqrt(alpha), INFINITY);
+    double blo[KCO_MAXK * KCO_MAXD], bhi[KCO_MAXK * KCO_MAXD];
+    for (int k = 0; k < K; ++k)
+        for (int a = 0; a < D; ++a) {
+            int i = k * D + a;
+            blo[i] = lo[i];
+            bhi[i] = hi[i];
+            if (na[k] > 0) {
+                double l = round_down_dt(nextafter(jmax[i] - r, -INFINITY), is_f32);
+                double h = round_up_dt(nextafter(jmin[i] + r, INFINITY), is_f32);
+                if (l > blo[i]) blo[i] = l;
+                if (h < bhi[i]) bhi[i] = h;
+            }
+            if (blo[i] > bhi[i]) infeasible = 1;
+        }
+
+    /* representatives from J_A */
+    int all_have = 1;
+    for (int k = 0; k < K; ++k) {
+        out->n_reps[k] = build_reps(seeds ? seeds[k] : -1, jmin_i + k * D, jmax_i + k * D, D,
+                                    ball_cap, out->reps + k * KCO_MAXREPS);
+        if (out->n_reps[k] == 0) all_have = 0;
+    }
+
+    /* step B */
+    double slo[KCO_MAXK * KCO_MAXD], shi[KCO_MAXK * KCO_MAXD];
+    double bmin2[KCO_MAXK * KCO_MAXD], bmax2[KCO_MAXK * KCO_MAXD];
+    int64_t nb[KCO_MAXK];
+    double cdist[KCO_MAXK], mid[KCO_MAXK * KCO_MAXD];
+    for (int i = 0; i < KD; ++i) {
+        slo[i] = INFINITY; shi[i] = -INFINITY; bmin2[i] = INFINITY; bmax2[i] = -INFINITY;
+        mid[i] = 0.5 * (blo[i] + bhi[i]);
+    }
+    for (int k = 0; k < K; ++k) { out->count[k] = 0; out->cand[k] = -1; cdist[k] = INFINITY; nb[k] = 0; }
+    const double four_alpha = 4.0 * alpha;
+    for (int64_t s = 0; s < N; ++s) {
+        if (!is_active(active, s)) continue;
+        const double *x = X + s * D;
+        if (all_have && asg[s] < 0) {
+            int left = 0, kk = -1;
+            for (int k = 0; k < K; ++k) {
+                int excl = 0;
+                for (int q = 0; q < out->n_reps[k] && !excl; ++q)
+                    if (sqdist(x, X + out->reps[k * KCO_MAXREPS + q] * D, D) > four_alpha) excl = 1;
+                if (!excl) { ++left; kk = k; }
+            }
+            if (left == 0) infeasible = 1;
+            if (left == 1) {
+                ++nb[kk];
+                for (int a = 0; a < D; ++a) {
+                    int i = kk * D + a;
+                    if (x[a] < bmin2[i]) bmin2[i] = x[a];
+                    if (x[a] > bmax2[i]) bmax2[i] = x[a];
+                }
+            }
+        }
+        for (int k = 0; k < K; ++k) {
+            if (!in_box(x, blo + k * D, bhi + k * D, D)) continue;
+            int ok = 1;
+            for (int q = 0; q < out->n_reps[k] && ok; ++q)
+                if (sqdist(x, X + out->reps[k * KCO_MAXREPS + q] * D, D) > alpha) ok = 0;
+            if (!ok) continue;
+            ++out->count[k];
+            for (int a = 0; a < D; ++a) {
+                int i = k * D + a;
+                if (x[a] < slo[i]) slo[i] = x[a];
+                if (x[a] > shi[i]) shi[i] = x[a];
+            }
+            double dm = sqdist(x, mid + k * D, D);
+            if (dm < cdist[k]) { cdist[k] = dm; out->cand[k] = s; }
+        }
+    }
+    for (int k = 0; k < K; ++k) {
+        out->n_assigned[k] = na[k] + nb[k];
+        if (out->count[k] == 0) infeasible = 1;
+        for (int a = 0; a < D; ++a) {
+            int i = k * D + a;
+            double l = slo[i], h = shi[i];
+            if (nb[k] > 0) {
+                double l2 = round_down_dt(nextafter(bmax2[i] - r, -INFINITY), is_f32);
+                double h2 = round_up_dt(nextafter(bmin2[i] + r, INFINITY), is_f32);
+                if (l2 > l) l = l2;
+                if (h2 < h) h = h2;
+            }
+            out->lo[i] = l;
+            out->hi[i] = h;
+            if (!(l <= h)) infeasible = 1;
+        }
+    }
+    free(asg);
+    if (infeasible) { out->status = 1; return 0; }
+    int leaf = 1;
+    for (int i = 0; i < KD; ++i)
+        if (out->hi[i] > out->lo[i]) leaf = 0;
+    out->status = leaf ? 2 : 0;
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Symmetry breaking (Section 4.1.3)                                       */
+/* ---------------------------------------------------------------------- */
+
+/* mu^1_1 <= mu^2_1 <= ... <= mu^K_1 on the first attribute, propagated to the
+ * boxes: lo^k_0 >= lo^{k-1}_0 forward and hi^k_0 <= hi^{k+1}_0 backward.
+ * Returns 1 when some box becomes empty. */
+static int symmetry_break(double *lo, double *hi, int K, int D)
+{
+    for (int k = 1; k < K; ++k)
+        if (lo[(k - 1) * D] > lo[k * D]) lo[k * D] = lo[(k - 1) * D];
+    for (int k = K - 2; k >= 0; --k)
+        if (hi[(k + 1) * D] < hi[k * D]) hi[k * D] = hi[(k + 1) * D];
+    for (int k = 0; k < K; ++k)
+        if (lo[k * D] > hi[k * D]) return 1;
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sample reduction (Section 4.2, Algorithm 5)                             */
+/* ---------------------------------------------------------------------- */
+
+/* A sample is deleted when, in every node of the list, it is redundant for the
+ * lower bound (alpha_s(M) < beta_glob, Section 4.2.1) and for the upper bound
+ * (for every k: x_s outside M^k or some representative j of k has
+ * ||x_s - x_j||^2 > alpha, Section 4.2.2).  `reps`/`n_reps` give each node's
+ * representatives (KCO_MAXREPS slots per cluster); a node with n_reps NULL uses
+ * none.  Returns the number of samples deleted. */
+int64_t kco_sample_reduction(const double *X, int64_t N, int D, int K, int n_nodes,
+                             const double *lo, const double *hi, const int64_t *reps,
+                             const int32_t *n_reps, double beta_glob, double alpha,
+                             uint8_t *active)
+{
+    const int KD = K * D;
+    int64_t deleted = 0;
+    for (int64_t s = 0; s < N; ++s) {
+        if (!active[s]) continue;
+        const double *x = X + s * D;
+        int redundant = 1;
+        for (int m = 0; m < n_nodes && redundant; ++m) {
+            const double *l = lo + (int64_t)m * KD, *h = hi + (int64_t)m * KD;
+            double as = INFINITY;
+            for (int k = 0; k < K; ++k) {
+                double v = farthest_corner_sk(x, l + k * D, h + k * D, D);
+                if (v < as) as = v;
+            }
+            if (!(as < beta_glob)) { redundant = 0; break; }
+            for (int k = 0; k < K && redundant; ++k) {
+                if (!in_box(x, l + k * D, h + k * D, D)) continue;
+                int excl = 0;
+                if (n_reps) {
+                    int nr = n_reps[m * K + k];
+                    const int64_t *rp = reps + ((int64_t)m * K + k) * KCO_MAXREPS;
+                    for (int q = 0; q < nr && !excl; ++q)
+                        if (sqdist(x, X + rp[q] * D, D) > alpha) excl = 1;
+                }
+                if (!excl) redundant = 0;
+            }
+        }
+        if (redundant) { active[s] = 0; ++deleted; }
+    }
+    return deleted;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Branch and bound (Algorithm 1)                                          */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    double tol;          /* stop when (alpha - beta)/alpha <= tol; prune beta >= alpha(1 - tol) */
+    int32_t use_bt;      /* 1: BB+CF+BT (assignment, tightening); 0: BB+CF */
+    int32_t use_sr;      /* sample reduction (Algorithm 5) */
+    int32_t i_sr;        /* run sample reduction every i_sr iterations */
+    int32_t ball_cap;    /* representatives per cluster (default 50) */
+    int32_t is_f32;      /* data are float values promoted to double */
+    int64_t seed;        /* FFT start = seed mod N */
+    int64_t node_limit;  /* 0: none */
+    double time_limit;   /* seconds, 0: none */
+} kco_opts;
+
+typedef struct {
+    double objective;
+    double lower_bound;
+    int64_t centers[KCO_MAXK];
+    int64_t nodes;        /* nodes selected and processed (iterations) */
+    int64_t created;      /* nodes pushed to the open set */
+    int32_t seeds_found;
+    int32_t status;       /* 0 optimal within tol, 4 time limit, 5 node limit */
+    int64_t active_final; /* samples left after sample reduction */
+    double fft_objective;
+} kco_result;
+
+typedef struct {
+    double lo[KCO_MAXK * KCO_MAXD];
+    double hi[KCO_MAXK * KCO_MAXD];
+    double beta;
+    int64_t id;
+} kco_node;
+
+typedef struct {
+    kco_node *v;
+    int64_t n, cap;
+} kco_nodes;
+
+static int nodes_push(kco_nodes *q, const kco_node *nd)
+{
+    if (q->n == q->cap) {
+        int64_t nc = q->cap ? 2 * q->cap : 64;
+        kco_node *nv = (kco_node *)realloc(q->v, sizeof(kco_node) * (size_t)nc);
+        if (!nv) return 2;
+        q->v = nv;
+        q->cap = nc;
+    }
+    q->v[q->n++] = *nd;
+    return 0;
+}
+
+/* Bound a freshly created child (Algorithm 1, Bounding): returns 0 when some
+ * cluster box holds no active sample (the child is not added), else 1 with
+ * beta(M_i) and the UB candidates (closest sample to each box midpoint). */
+static int bound_child(const double *X, int64_t N, int D, int K, kco_node *c, const uint8_t *active,
+                       int64_t *cand)
+{
+    for (int k = 0; k < K; ++k) {
+        cand[k] = kco_mid_candidate(X, N, D, c->lo + k * D, c->hi + k * D, active, NULL);
+        if (cand[k] < 0) return 0;
+    }
+    kco_lower_bound(X, N, D, K, c->lo, c->hi, active, &c->beta, NULL);
+    return 1;
+}
+
+int kco_solve(const double *X, int64_t N, int D, int K, const kco_opts *opt, kco_result *res)
+{
+    if (K < 1 || K > KCO_MAXK || D < 1 || D > KCO_MAXD || N < K) return 1;
+    const int KD = K * D;
+    clock_t t0 = clock();
+    memset(res, 0, sizeof(*res));
+    uint8_t *active = (uint8_t *)malloc((size_t)N);
+    if (!active) return 2;
+    memset(active, 1, (size_t)N);
+
+    /* root: M0, FFT upper bound (Algorithm 2), initial seeds (Section 4.1.1) */
+    double lo0[KCO_MAXD], hi0[KCO_MAXD];
+    kco_root_box(X, N, D, lo0, hi0);
+    int64_t start = (int64_t)((uint64_t)opt->seed % (uint64_t)N);
+    int64_t inc[KCO_MAXK];
+    double alpha;
+    kco_fft(X, N, D, K, start, inc, &alpha);
+    res->fft_objective = alpha;
+    int seeds_found = 0;
+    if (opt->use_bt) {
+        seeds_found = 1;
+        for (int i = 0; i < K && seeds_found; ++i)
+            for (int j = i + 1; j < K; ++j)
+                if (!(sqdist(X + inc[i] * D, X + inc[j] * D, D) > 4.0 * alpha)) { seeds_found = 0; break; }
+    }
+    int64_t seeds[KCO_MAXK];
+    for (int k = 0; k < K; ++k) seeds[k] = inc[k];
+    const int use_sb = opt->use_bt && !seeds_found;
+
+    kco_nodes open = {0};
+    kco_node root;
+    for (int k = 0; k < K; ++k)
+        for (int a = 0; a < D; ++a) { root.lo[k * D + a] = lo0[a]; root.hi[k * D + a] = hi0[a]; }
+    kco_lower_bound(X, N, D, K, root.lo, root.hi, NULL, &root.beta, NULL);
+    root.id = 0;
+    int64_t next_id = 1;
+    nodes_push(&open, &root);
+    res->created = 1;
+
+    kco_tighten_out *tz = (kco_tighten_out *)malloc(sizeof(kco_tighten_out));
+    int64_t *sr_reps = NULL;
+    int32_t *sr_nreps = NULL;
+    double *sr_lo = NULL, *sr_hi = NULL;
+    int64_t iter = 0;
+    int status = 0;
+    double beta_glob = 0.0;
+    for (;;) {
+        if (open.n == 0) { beta_glob = alpha; break; }
+        /* beta_i = min over open nodes; node selection picks (beta, id) smallest */
+        int64_t sel = 0;
+        for (int64_t i = 1; i < open.n; ++i)
+            if (open.v[i].beta < open.v[sel].beta ||
+                (open.v[i].beta == open.v[sel].beta && open.v[i].id < open.v[sel].id))
+                sel = i;
+        beta_glob = open.v[sel].beta;
+        if (alpha - beta_glob <= opt->tol * alpha) break;
+        if (opt->node_limit > 0 && iter >= opt->node_limit) { status = 5; break; }
+        if (opt->time_limit > 0 && (double)(clock() - t0) / CLOCKS_PER_SEC > opt->time_limit) { status = 4; break; }
+        kco_node M = open.v[sel];
+        open.v[sel] = open.v[--open.n];
+        ++iter;
+
+        /* bounds tightening */
+        kco_node Mh = M;
+        int leaf = 0;
+        int32_t cur_nreps[KCO_MAXK];
+        int64_t cur_reps[KCO_MAXK * KCO_MAXREPS];
+        for (int k = 0; k < K; ++k) cur_nreps[k] = 0;
+        if (opt->use_bt) {
+            kco_tighten(X, N, D, K, M.lo, M.hi, alpha, seeds_found ? seeds : NULL, active, opt->is_f32,
+                        opt->ball_cap, tz);
+            if (tz->status == 1) goto prune_step;
+            memcpy(Mh.lo, tz->lo, sizeof(double) * KD);
+            memcpy(Mh.hi, tz->hi, sizeof(double) * KD);
+            for (int k = 0; k < K; ++k) cur_nreps[k] = tz->n_reps[k];
+            memcpy(cur_reps, tz->reps, sizeof(cur_reps));
+        } else {
+            /* BB+CF keeps only the "centers on samples" tightening */
+            for (int k = 0; k < K; ++k) {
+                double *l = Mh.lo + k * D, *h = Mh.hi + k * D;
+                double bl[KCO_MAXD], bh[KCO_MAXD];
+                int64_t cnt = 0;
+                for (int a = 0; a < D; ++a) { bl[a] = INFINITY; bh[a] = -INFINITY; }
+                for (int64_t s = 0; s < N; ++s) {
+                    if (!active[s] || !in_box(X + s * D, l, h, D)) continue;
+                    ++cnt;
+                    for (int a = 0; a < D; ++a) {
+                        double v = X[s * D + a];
+                        if (v < bl[a]) bl[a] = v;
+                        if (v > bh[a]) bh[a] = v;
+                    }
+                }
+                if (cnt == 0) goto prune_step;
+                memcpy(l, bl, sizeof(double) * D);
+                memcpy(h, bh, sizeof(double) * D);
+            }
+        }
+        if (use_sb && symmetry_break(Mh.lo, Mh.hi, K, D)) goto prune_step;
+        leaf = 1;
+        for (int i = 0; i < KD; ++i)
+            if (Mh.hi[i] > Mh.lo[i]) leaf = 0;
+
+        /* sample reduction every i_sr iterations, over the open nodes and this one */
+        if (opt->use_sr && opt->i_sr > 0 && iter % opt->i_sr == 0) {
+            int64_t nn = open.n + 1;
+            sr_lo = (double *)realloc(sr_lo, sizeof(double) * (size_t)(nn * KD));
+            sr_hi = (double *)realloc(sr_hi, sizeof(double) * (size_t)(nn * KD));
+            sr_reps = (int64_t *)realloc(sr_reps, sizeof(int64_t) * (size_t)(nn * K * KCO_MAXREPS));
+            sr_nreps = (int32_t *)realloc(sr_nreps, sizeof(int32_t) * (size_t)(nn * K));
+            for (int64_t i = 0; i < nn; ++i) {
+                const kco_node *src = i < open.n ? &open.v[i] : &Mh;
+                memcpy(sr_lo + i * KD, src->lo, sizeof(double) * KD);
+                memcpy(sr_hi + i * KD, src->hi, sizeof(double) * KD);
+                for (int k = 0; k < K; ++k) {
+                    int64_t *rp = sr_reps + (i * K + k) * KCO_MAXREPS;
+                    if (i < open.n) {
+                        /* open nodes: the seeds are the assignments known there */
+                        sr_nreps[i * K + k] = seeds_found ? 1 : 0;
+                        rp[0] = seeds[k];
+                    } else {
+                        sr_nreps[i * K + k] = cur_nreps[k];
+                        memcpy(rp, cur_reps + k * KCO_MAXREPS, sizeof(int64_t) * KCO_MAXREPS);
+                    }
+                }
+            }
+            kco_sample_reduction(X, N, D, K, (int)nn, sr_lo, sr_hi, sr_reps, sr_nreps, beta_glob, alpha,
+                                 active);
+        }
+
+        if (!leaf) {
+            /* branching: max-range variable (smallest k*D+a on ties), midpoint value */
+            int bi = 0;
+            double br = -1.0;
+            for (int i = 0; i < KD; ++i)
+                if (Mh.hi[i] - Mh.lo[i] > br) { br = Mh.hi[i] - Mh.lo[i]; bi = i; }
+            double m, succ;
+            split_point(Mh.lo[bi], Mh.hi[bi], opt->is_f32, &m, &succ);
+            kco_node c[2];
+            c[0] = Mh; c[0].hi[bi] = m;
+            c[1] = Mh; c[1].lo[bi] = succ;
+            for (int i = 0; i < 2; ++i) {
+                int64_t cand[KCO_MAXK];
+                if (!bound_child(X, N, D, K, &c[i], active, cand)) continue;
+                double ub;
+                kco_objective(X, N, D, K, cand, active, &ub, NULL);
+                if (ub < alpha) { alpha = ub; memcpy(inc, cand, sizeof(int64_t) * K); }
+                c[i].id = next_id++;
+                ++res->created;
+                if (c[i].beta < alpha - opt->tol * alpha) nodes_push(&open, &c[i]);
+            }
+        } else {
+            /* leaf: every box is one point, a sample; its objective is exact */
+            int64_t cand[KCO_MAXK];
+            int ok = 1;
+            for (int k = 0; k < K && ok; ++k) {
+                cand[k] = kco_mid_candidate(X, N, D, Mh.lo + k * D, Mh.hi + k * D, active, NULL);
+                if (cand[k] < 0) ok = 0;
+            }
+            if (ok) {
+                double ub;
+                kco_objective(X, N, D, K, cand, active, &ub, NULL);
+                if (ub < alpha) { alpha = ub; memcpy(inc, cand, sizeof(int64_t) * K); }
+            }
+        }
+    prune_step:
+        /* remove every node with beta >= alpha (Algorithm 1, Bounding) */
+        {
+            int64_t w = 0;
+            for (int64_t i = 0; i < open.n; ++i)
+                if (open.v[i].beta < alpha - opt->tol * alpha) open.v[w++] = open.v[i];
+            open.n = w;
+        }
+    }
+    /* the incumbent's objective over all samples, the value reported */
+    double obj;
+    kco_objective(X, N, D, K, inc, NULL, &obj, NULL);
+    res->objective = obj;
+    res->lower_bound = beta_glob < obj ? beta_glob : obj;
+    memcpy(res->centers, inc, sizeof(int64_t) * K);
+    res->nodes = iter;
+    res->seeds_found = seeds_found;
+    res->status = status;
+    int64_t na = 0;
+    for (int64_t s = 0; s < N; ++s) na += active[s];
+    res->active_final = na;
+    free(open.v);
+    free(tz);
+    free(sr_lo); free(sr_hi); free(sr_reps); free(sr_nreps);
+    free(active);
+    return 0;
+}

@@ -1,0 +1,343 @@
+"""Pins for the CPU oracle: each test checks the oracle against something other
+than itself -- hand-derived examples (tests/golden), brute force, dense grids,
+scipy routines for special cases, and the invariants the paper proves.
+
+The oracle is the parity reference for the CUDA path, so these run on CPU only.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+from scipy.spatial.distance import cdist
+
+import oracle
+import synth
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")))
+
+
+def _blobs(n, d, seed, k=3):
+    return synth.gaussian_mixture(n, d, (1 / k,) * k, (1.0,) * k, (1.0,) * k, 10.0, seed,
+                                  dtype=np.float64)
+
+
+def _objective_np(X, centers):
+    """Eq. 1 at fixed centers via scipy's squared-Euclidean cdist."""
+    Dm = cdist(X, X[np.asarray(centers)], "sqeuclidean")
+    q = Dm.min(axis=1)
+    return q.max(), int(np.argmax(q))
+
+
+def _bruteforce_np(X, k):
+    """Independent brute force with itertools and cdist (tiny N only)."""
+    Dm = cdist(X, X, "sqeuclidean")
+    best = np.inf
+    for c in itertools.combinations(range(X.shape[0]), k):
+        v = Dm[:, list(c)].min(axis=1).max()
+        best = min(best, v)
+    return best
+
+
+# ---------------------------------------------------------------- golden ---
+
+@pytest.mark.parametrize("ex", GOLD["objective"])
+def test_golden_objective(ex):
+    X = np.array(ex["X"], dtype=np.float64)
+    z, c = oracle.bruteforce(X, ex["K"])
+    assert z == ex["z"]
+    r = oracle.solve(X, ex["K"], tol=0.0)
+    assert r["objective"] == ex["z"]
+    assert oracle.objective(X, c)[0] == ex["z"]
+
+
+@pytest.mark.parametrize("ex", GOLD["lower_bound"])
+def test_golden_lower_bound(ex):
+    X = np.array(ex["X"])
+    lo = np.array(ex["lo"]); hi = np.array(ex["hi"])
+    bm = oracle.beta_matrix(X, lo, hi)
+    assert np.array_equal(bm.min(axis=1), np.array(ex["beta_s"]))
+    b, arg = oracle.lower_bound(X, lo, hi)
+    assert b == ex["beta"] and arg == ex["argmax"]
+
+
+@pytest.mark.parametrize("ex", GOLD["farthest_corner"])
+def test_golden_farthest_corner(ex):
+    x = np.array([ex["x"]])
+    out = oracle.alpha_s(x, np.array(ex["lo"]), np.array(ex["hi"]))
+    assert out[0] == ex["alpha_s"]
+
+
+# ----------------------------------------------------- closed forms ---
+
+def test_root_box_is_columnwise_min_max():
+    X = _blobs(500, 5, 3)
+    lo, hi = oracle.root_box(X)
+    assert np.array_equal(lo, X.min(axis=0)) and np.array_equal(hi, X.max(axis=0))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_objective_matches_cdist(seed):
+    rng = np.random.default_rng(seed)
+    X = _blobs(300, 1 + seed * 2, seed)
+    c = rng.choice(300, size=4, replace=False)
+    v, arg = oracle.objective(X, c)
+    v2, arg2 = _objective_np(X, c)
+    assert v == pytest.approx(v2, rel=1e-13)
+    assert X[arg].tolist() == X[arg2].tolist() or abs(v - v2) < 1e-12 * v2
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 8])
+def test_beta_sk_is_box_minimum(d):
+    """beta_s^k is the minimum of ||x - mu||^2 over the box (Eq. 11):
+    compare with a bounded numerical minimiser started from many points."""
+    rng = np.random.default_rng(d)
+    for _ in range(20):
+        lo = rng.uniform(-3, 3, size=d)
+        hi = lo + rng.uniform(0, 2, size=d) * (rng.uniform(size=d) < 0.8)
+        x = rng.uniform(-6, 6, size=d)
+        v = oracle.beta_sk(x, lo, hi)
+        best = np.inf
+        for _ in range(4):
+            x0 = rng.uniform(lo, hi)
+            r = minimize(lambda m: np.sum((x - m) ** 2), x0, jac=lambda m: 2 * (m - x),
+                         bounds=list(zip(lo, hi)), method="L-BFGS-B", tol=1e-14)
+            best = min(best, r.fun)
+        assert v <= best * (1 + 1e-9) + 1e-12
+        assert v == pytest.approx(best, rel=1e-7, abs=1e-9)
+
+
+def test_beta_sk_dense_grid_2d():
+    """Brute force on a dense grid (with the box's edges) bounds the closed form."""
+    rng = np.random.default_rng(11)
+    for _ in range(10):
+        lo = rng.uniform(0, 2, size=2)
+        hi = lo + rng.uniform(0.1, 2, size=2)
+        x = rng.uniform(-2, 5, size=2)
+        g0 = np.linspace(lo[0], hi[0], 801)
+        g1 = np.linspace(lo[1], hi[1], 801)
+        G = np.stack(np.meshgrid(g0, g1), -1).reshape(-1, 2)
+        grid_min = ((G - x) ** 2).sum(1).min()
+        v = oracle.beta_sk(x, lo, hi)
+        step = max(hi - lo) / 800
+        assert v <= grid_min + 1e-12
+        assert grid_min - v <= 2 * step * (np.sqrt(grid_min) + step) + 1e-12
+
+
+@pytest.mark.parametrize("d", [1, 2, 4, 6])
+def test_farthest_corner_is_max_over_corners(d):
+    """alpha_s: a convex function's maximum over a box sits at a corner, so
+    enumerating all 2^D corners is a brute force for Eq. 13."""
+    rng = np.random.default_rng(100 + d)
+    k = 3
+    X = rng.uniform(-4, 4, size=(40, d))
+    lo = rng.uniform(-3, 0, size=(k, d))
+    hi = lo + rng.uniform(0, 3, size=(k, d))
+    got = oracle.alpha_s(X, lo, hi)
+    for s in range(40):
+        per_k = []
+        for j in range(k):
+            corners = np.array(list(itertools.product(*zip(lo[j], hi[j]))))
+            per_k.append(((corners - X[s]) ** 2).sum(1).max())
+        assert got[s] == pytest.approx(min(per_k), rel=1e-13)
+
+
+def test_bruteforce_matches_independent_enumeration():
+    for seed in range(6):
+        X = _blobs(14, 2, seed)
+        for k in (1, 2, 3):
+            z, c = oracle.bruteforce(X, k)
+            assert z == pytest.approx(_bruteforce_np(X, k), rel=1e-13)
+            assert oracle.objective(X, c)[0] == z
+
+
+# -------------------------------------------------------- invariants ---
+
+def test_root_lower_bound_is_zero():
+    X = _blobs(400, 3, 5)
+    lo, hi = oracle.root_box(X)
+    L = np.tile(lo, (3, 1)); H = np.tile(hi, (3, 1))
+    assert oracle.lower_bound(X, L, H)[0] == 0.0
+
+
+def test_lower_bound_at_degenerate_box_is_objective():
+    """At M = {mu} with mu on samples the relaxation is exact (Section 5)."""
+    X = _blobs(500, 4, 6)
+    rng = np.random.default_rng(0)
+    for _ in range(10):
+        c = rng.choice(500, size=3, replace=False)
+        b, _ = oracle.lower_bound(X, X[c], X[c])
+        assert b == oracle.objective(X, c)[0]
+        assert b == pytest.approx(_objective_np(X, c)[0], rel=1e-13)
+
+
+def test_lower_bound_below_node_optimum():
+    """beta(M) <= z(M) = min over centers in X cap M of the objective."""
+    rng = np.random.default_rng(7)
+    X = _blobs(24, 2, 8)
+    Dm = cdist(X, X, "sqeuclidean")
+    for _ in range(30):
+        lo, hi = synth.random_boxes(X, 2, 1, int(rng.integers(1 << 30)), 0.2, 0.9)
+        lo, hi = lo[0], hi[0]
+        inb = [np.where(np.all((X >= lo[j]) & (X <= hi[j]), 1))[0] for j in range(2)]
+        if any(len(i) == 0 for i in inb):
+            continue
+        zM = min(Dm[:, [a, b]].min(1).max() for a in inb[0] for b in inb[1])
+        b, _ = oracle.lower_bound(X, lo, hi)
+        assert b <= zM + 1e-12
+
+
+def test_lower_bound_monotone_under_shrink_and_below_alpha_s():
+    X = _blobs(2000, 3, 9)
+    lo, hi = synth.nested_boxes(X, 3, 12, seed=4, hw_lo=1e-2, hw_hi=8.0)
+    betas, _ = oracle.lower_bounds(X, lo, hi)
+    assert np.all(np.diff(betas) >= 0)
+    for b in (0, 6, 11):
+        bs = oracle.beta_matrix(X, lo[b], hi[b]).min(1)
+        assert np.all(bs <= oracle.alpha_s(X, lo[b], hi[b]))
+
+
+def test_fft_is_greedy_and_two_approximation():
+    """Algorithm 2: each new point is the farthest from the chosen set, and
+    FFT is Gonzalez's 2-approximation, i.e. <= 4 z in squared distances."""
+    for seed in range(5):
+        X = _blobs(16, 2, 20 + seed)
+        for k in (2, 3):
+            c, obj = oracle.fft(X, k, start=seed % 16)
+            assert c[0] == seed % 16
+            for t in range(1, k):
+                dmin = cdist(X, X[c[:t]], "sqeuclidean").min(1)
+                assert dmin[c[t]] == dmin.max()
+                assert c[t] == int(np.argmax(dmin))
+            assert obj == pytest.approx(_objective_np(X, c)[0], rel=1e-13)
+            z, _ = oracle.bruteforce(X, k)
+            assert obj <= 4 * z * (1 + 1e-12)
+
+
+# ---------------------------------------------------- branch and bound ---
+
+@pytest.mark.parametrize("use_bt,use_sr", [(True, True), (True, False), (False, False)])
+@pytest.mark.parametrize("seed", range(5))
+def test_solve_matches_bruteforce(seed, use_bt, use_sr):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(8, 30))
+    d = int(rng.integers(1, 4))
+    X = _blobs(n, d, seed)
+    for k in (1, 2, 3):
+        r = oracle.solve(X, k, tol=0.0, use_bt=use_bt, use_sr=use_sr, seed=seed)
+        z, _ = oracle.bruteforce(X, k)
+        assert r["objective"] == pytest.approx(z, rel=1e-12)
+        assert r["lower_bound"] <= r["objective"]
+        assert oracle.objective(X, r["centers"])[0] == r["objective"]
+
+
+def test_solve_float32_data_matches_bruteforce():
+    for seed in range(4):
+        X = synth.gaussian_mixture(25, 2, (0.5, 0.5), (1.0, 1.0), (1.0, 1.0), 5.0, seed,
+                                   dtype=np.float32)
+        for k in (2, 3, 4):
+            r = oracle.solve(X, k, tol=0.0, is_f32=True)
+            z, _ = oracle.bruteforce(X.astype(np.float64), k)
+            assert r["objective"] == pytest.approx(z, rel=1e-12)
+
+
+def test_solve_with_duplicates_and_degenerate_data():
+    X = np.array([[1.0, 1.0]] * 5 + [[3.0, 1.0]] * 4 + [[1.0, 7.0]] * 3)
+    for k in (1, 2, 3, 4):
+        r = oracle.solve(X, k, tol=0.0)
+        z, _ = oracle.bruteforce(X, k)
+        assert r["objective"] == z
+    X1 = np.zeros((7, 2))
+    assert oracle.solve(X1, 2)["objective"] == 0.0
+
+
+def test_small_workload_subsample_bruteforce():
+    """Seed-0 subsample (N=60) of the small workload: B&B equals brute force."""
+    X, w = synth.make_workload("small")
+    Xs = X[synth.subsample_rows(w.n, 60, seed=0)]
+    z, _ = oracle.bruteforce(Xs, 3)
+    assert z == pytest.approx(_bruteforce_np(Xs, 3), rel=1e-13)
+    for bt in (True, False):
+        r = oracle.solve(Xs, 3, tol=0.0, use_bt=bt, use_sr=bt)
+        assert r["objective"] == pytest.approx(z, rel=1e-12)
+
+
+def test_small_workload_acceleration_invariance():
+    """BB+CF+BT, BB+CF and sample reduction on/off reach the same optimum, and
+    acceleration cuts the node count (Section 6.2)."""
+    X, w = synth.make_workload("small")
+    r_full = oracle.solve(X, 3, tol=1e-12)
+    r_nosr = oracle.solve(X, 3, tol=1e-12, use_sr=False)
+    r_plain = oracle.solve(X, 3, tol=1e-12, use_bt=False, use_sr=False)
+    assert r_full["objective"] == r_nosr["objective"] == pytest.approx(r_plain["objective"], rel=1e-12)
+    assert r_full["nodes"] < r_plain["nodes"]
+    assert r_full["fft_objective"] <= 4 * r_full["objective"] * (1 + 1e-12)
+
+
+def test_tighten_keeps_the_optimum():
+    """Lemmas 1 and 2: with alpha >= z, any node whose boxes hold the optimal
+    centers keeps them after assignment and tightening."""
+    rng = np.random.default_rng(3)
+    for trial in range(12):
+        X = _blobs(40, 2, 50 + trial)
+        k = 3
+        z, c = oracle.bruteforce(X, k)
+        alpha = z * (1.0 + 0.5 * rng.uniform())
+        lo0, hi0 = oracle.root_box(X)
+        lo = np.empty((k, 2)); hi = np.empty((k, 2))
+        for j in range(k):
+            w = rng.uniform(0.05, 1.0, size=2) * (hi0 - lo0)
+            lo[j] = np.maximum(lo0, X[c[j]] - rng.uniform(0, 1, size=2) * w)
+            hi[j] = np.minimum(hi0, lo[j] + w)
+            hi[j] = np.maximum(hi[j], X[c[j]])
+        t = oracle.tighten(X, lo, hi, alpha)
+        assert t["status"] in (0, 2)
+        for j in range(k):
+            assert np.all(t["lo"][j] <= X[c[j]]) and np.all(X[c[j]] <= t["hi"][j])
+            assert t["count"][j] >= 1
+        assert t["beta"] <= z
+
+
+def test_tighten_with_seeds_keeps_the_optimum():
+    """Seeds fix cluster labels (Section 4.1.1); relabel the optimum to match."""
+    X = np.concatenate([np.random.default_rng(s).normal(m, 0.3, size=(15, 2))
+                        for s, m in enumerate(([0, 0], [8, 0], [0, 8]))])
+    k = 3
+    c, fobj = oracle.fft(X, k, 0)
+    Dm = cdist(X[c], X[c], "sqeuclidean")
+    assert np.all(Dm[~np.eye(k, dtype=bool)] > 4 * fobj)
+    z, copt = oracle.bruteforce(X, k)
+    lab = cdist(X[c], X[copt], "sqeuclidean").argmin(1)   # seed j sits with center copt[lab[j]]
+    lo0, hi0 = oracle.root_box(X)
+    t = oracle.tighten(X, np.tile(lo0, (k, 1)), np.tile(hi0, (k, 1)), fobj, seeds=c)
+    assert t["status"] in (0, 2)
+    for j in range(k):
+        mu = X[copt[lab[j]]]
+        assert np.all(t["lo"][j] <= mu) and np.all(mu <= t["hi"][j])
+    r = oracle.solve(X, k, tol=0.0)
+    assert r["seeds_found"] and r["objective"] == pytest.approx(z, rel=1e-12)
+
+
+def test_sample_reduction_keeps_bound_samples():
+    """A deleted sample can never be the farthest one: after reduction the
+    objective at the optimum and the node bounds are unchanged (Section 4.2)."""
+    X = _blobs(300, 2, 12)
+    k = 3
+    r = oracle.solve(X, k, tol=0.0, use_sr=False)
+    alpha = r["objective"]
+    lo0, hi0 = oracle.root_box(X)
+    L = np.tile(lo0, (k, 1))[None]; H = np.tile(hi0, (k, 1))[None]
+    # a node well inside: boxes around the optimal centers
+    c = r["centers"]
+    lo = (X[c] - 0.1)[None]; hi = (X[c] + 0.1)[None]
+    beta_glob = oracle.lower_bound(X, lo[0], hi[0])[0]
+    act = oracle.sample_reduction(X, lo, hi, beta_glob, alpha, np.ones(300, bool),
+                                  reps=[[[int(ci)] for ci in c]])
+    assert act.sum() < 300
+    assert oracle.lower_bound(X, lo[0], hi[0], active=act)[0] == beta_glob
+    assert oracle.objective(X, c, active=act)[0] == alpha
+    # the root node keeps everything: alpha_s(M0) is large
+    act0 = oracle.sample_reduction(X, L, H, 0.0, alpha, np.ones(300, bool))
+    assert act0.all()
