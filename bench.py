@@ -1,0 +1,277 @@
+#!/usr/bin/env python3
+"""Benchmark of the K-center node-bound hot path on GB300.
+
+Workload (default): the LB/UB kernel microbenchmark -- N = 10,000,000 samples,
+D = 8, K = 5, float32, a 5-blob Gaussian mixture; each step bounds one batch
+of 256 random nested node boxes over all N samples with one
+``kc_lower_bounds`` call (Section 3.1 closed-form lower bound).  The metric is
+node x sample lower-bound evaluations per second.
+
+Multi-GPU: the node batches are independent problems, so ``--gpus N`` (under
+torchrun) runs one replica per GPU on its own batch with no collective on the
+data path ("scaling": "weak"); only the timing uses a barrier and a max over
+ranks.
+
+``--impl reference`` times the CPU oracle (plain C, FP64, one core) on a
+bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "lb_microbench"
+B_NODES = 256
+METRIC = "node x sample LB evals/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--n", type=int, default=None, help="override N (testing only)")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for i, nm in enumerate(names):
+                if r[5 + i].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_oracle_rate(X, lo, hi, n_sample):
+    """The FP64 oracle's node x sample evaluations per second (one core)."""
+    import oracle
+    Xs = np.ascontiguousarray(X[:n_sample], dtype=np.float64)
+    oracle.lower_bounds(Xs[:1000], lo[:2], hi[:2])    # build / warm
+    t = time.perf_counter()
+    oracle.lower_bounds(Xs, lo, hi)
+    dt = time.perf_counter() - t
+    return lo.shape[0] * n_sample / dt, dt
+
+
+def run_reference(args, ws, rank):
+    """The CPU oracle as the reference arm, rank 0 only."""
+    if rank != 0:
+        return
+    X, w = synth.make_workload(WORKLOAD, n=args.n)
+    lo, hi = synth.nested_boxes(X, w.k, B_NODES, seed=1)
+    n_sample = 16_384
+    for _ in range(args.warmup):
+        cpu_oracle_rate(X, lo, hi, 2048)
+    t = time.perf_counter()
+    evals = 0
+    for _ in range(args.steps):
+        r, dt = cpu_oracle_rate(X, lo, hi, n_sample)
+        evals += B_NODES * n_sample
+    el = time.perf_counter() - t
+    v = evals / el
+    sample = f"{B_NODES} nested nodes x first {n_sample} samples per step (FP64 oracle, one core)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(X.shape[0], w),
+        "cpu_baseline": {"value": v, "unit": "evals/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(n, w):
+    return {"workload": f"{WORKLOAD}: N={n:,} D={w.d} K={w.k} float32, {B_NODES} nested node boxes per launch",
+            "N": n, "D": w.d, "K": w.k, "nodes_per_launch": B_NODES, "parallelism": "replicas",
+            "l2": "inputs larger than L2 (N*D*4 bytes streamed per launch)"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        dist.init_process_group("gloo", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2301_00061_gb300 as kcm
+
+    X, w = synth.make_workload(WORKLOAD, n=args.n)
+    n = X.shape[0]
+    lo, hi = synth.nested_boxes(X, w.k, B_NODES, seed=1 + rank)
+    Xd = torch.from_numpy(X).to(dev)
+    lod, hid = torch.from_numpy(lo).to(dev), torch.from_numpy(hi).to(dev)
+    lb = torch.empty(B_NODES, dtype=torch.float64, device=dev)
+    arg = torch.empty(B_NODES, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    h = kcm.kc_create(Xd, w.k, stream=stream.cuda_stream)
+
+    def step():
+        kcm.kc_lower_bounds(h, lod, hid, lb, None, arg)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    launches0 = kcm.kc_launch_count(h)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)   # let the sampler start before the timed region
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = kcm.kc_launch_count(h) - launches0
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+    evals_per_step = B_NODES * n
+    value = evals_per_step * ws / (ms * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers: upload X from
+    # pinned memory, bound the batch from host boxes, read results to host
+    Xp = torch.from_numpy(X).pin_memory()
+    lop, hip = torch.from_numpy(lo).pin_memory(), torch.from_numpy(hi).pin_memory()
+    lbh = torch.empty(B_NODES, dtype=torch.float64).pin_memory()
+    argh = torch.empty(B_NODES, dtype=torch.int64).pin_memory()
+    e2e_steps = max(1, args.e2e_steps)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        h2 = kcm.kc_create(Xp, w.k, stream=stream.cuda_stream)
+        kcm.kc_lower_bounds(h2, lop, hip, lbh, None, argh)
+        kcm.kc_destroy(h2)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t[0])
+    e2e = {"value": evals_per_step * ws / e2e_s, "unit": "evals/s",
+           "h2d_bytes_per_step": int(X.nbytes + lo.nbytes + hi.nbytes),
+           "d2h_bytes_per_step": int(lbh.numel() * 8 + argh.numel() * 8),
+           "includes": "kc_create upload of X from pinned host memory, boxes host->device, results device->host"}
+
+    # ---- roofline of the dominant kernel (the float lower-bound kernel)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    f_mhz = ck.get("sm_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    # FP32-pipe work per node x sample (see the design notes): per cluster and
+    # attribute two signed differences and one fused multiply-add
+    ops_per_eval = 3 * w.k * w.d
+    achieved = ops_per_eval * evals_per_step / (ms * 1e-3) / 1e12
+    peak = sms * 128 * f_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_basis": f"FP32 pipe: {sms} SMs x 128 lanes x {f_mhz:.0f} MHz (median SM clock sampled)",
+                "hbm_gbs": n * w.d * 4 / (ms * 1e-3) / 1e9}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(n, w),
+        "clocks": ck, "e2e": e2e, "gpu_launches": int(launches) * ws, "roofline": roofline,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, dt = cpu_oracle_rate(X, lo, hi, 200_000)
+        line["cpu_baseline"] = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{B_NODES} nested nodes x first 200,000 samples ({dt:.1f} s, FP64, one core)"}
+    kcm.kc_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * kc.h -- C ABI of the GB300 K-center branch-and-bound library (libkc.so).
+ *
+ * The library evaluates the data-parallel steps of the reduced-space branch
+ * and bound for K-center clustering of Ren, You, Hua, Ji and Cao ("A Global
+ * Optimization Algorithm for K-Center Clustering of One Billion Samples"):
+ * node lower bounds (Section 3.1), upper bounds (Section 3.2), farthest first
+ * traversal (Algorithm 2), cluster assignment and bounds tightening
+ * (Section 4.1, Algorithms 3-4), sample reduction (Section 4.2, Algorithm 5)
+ * and the branch-and-bound loop itself (Algorithm 1), on one CUDA GPU.
+ *
+ * Notation: N samples (the paper's S), D attributes (the paper's A), K
+ * clusters, B nodes.  A node is K axis-aligned boxes, one per cluster:
+ * lo[k*D + a] <= mu^k_a <= hi[k*D + a]; a batch of B nodes is the arrays
+ * lo[B][K][D] and hi[B][K][D] in the data's element type.  All distances are
+ * squared Euclidean (Eq. 1).  Ties in every argmax/argmin go to the smallest
+ * sample index.
+ *
+ * Pointers.  Every array argument may be host memory (pageable or pinned) or
+ * device memory of the context's GPU; the library checks which with
+ * cudaPointerGetAttributes and stages host arrays through its own buffers.
+ * Calls are ordered on the context's stream.  A call whose outputs are all in
+ * device memory returns without waiting for the GPU; a call with any output in
+ * host memory returns after the results are written.
+ *
+ * Errors.  Every call returns a kc_status; nothing is thrown across the ABI.
+ * On failure the outputs are unspecified and kc_last_error() describes the
+ * cause.  After KC_ECUDA the context should be destroyed; after any other
+ * error it stays usable.  Limits: 1 <= K <= 16, 1 <= D <= 64,
+ * K <= N <= 4,294,967,294.
+ */
+#ifndef KC_H_
+#define KC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kc_ctx kc_ctx;
+
+typedef enum {
+    KC_OK = 0,
+    KC_EINVAL = 1,     /* bad argument or non-finite data */
+    KC_ENOMEM = 2,     /* device or host allocation failed */
+    KC_ECUDA = 3,      /* a CUDA call failed; destroy the context */
+    KC_ETIMEOUT = 4,   /* kc_solve stopped at its time limit */
+    KC_ELIMIT = 5,     /* kc_solve stopped at its node limit */
+    KC_EINTERNAL = 6
+} kc_status;
+
+typedef enum { KC_F32 = 0, KC_F64 = 1 } kc_dtype;
+typedef enum { KC_ROW_MAJOR = 0, KC_COL_MAJOR = 1 } kc_layout;
+
+/*
+ * kc_create -- upload a dataset and make a context.
+ *   X       N*D values of type dt; KC_ROW_MAJOR: X[s*D + a]; KC_COL_MAJOR:
+ *           X[a*N + s].  Host or device.  The library keeps its own
+ *           device copy (attribute-major, padded rows), so X may be freed
+ *           after the call returns.
+ *   stream  a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream),
+ *           or NULL for the legacy default stream.  The context must only be
+ *           used from one host thread at a time.
+ *   out     receives the context; NULL on failure.
+ * Rejects NaN or infinite data with KC_EINVAL.  The dataset X of Eq. 1.
+ */
+kc_status kc_create(const void *X, int64_t N, int32_t D, int32_t K, kc_dtype dt, kc_layout layout,
+                    void *stream, kc_ctx **out);
+
+/* Frees the context and everything it owns.  NULL is accepted. */
+void kc_destroy(kc_ctx *ctx);
+
+/* Message of the last failed call on this context (never NULL). */
+const char *kc_last_error(const kc_ctx *ctx);
+
+/* Message of the last failed kc_create in this process (never NULL). */
+const char *kc_create_error(void);
+
+/* Changes the stream later calls are ordered on. */
+kc_status kc_set_stream(kc_ctx *ctx, void *stream);
+
+/* Number of this library's own kernels launched on the context so far. */
+int64_t kc_launch_count(const kc_ctx *ctx);
+
+/*
+ * kc_root_box -- the region of centers M0 (Section 2.1): lo[a] = min_s x_{s,a},
+ * hi[a] = max_s x_{s,a} (the same box for every cluster).  lo, hi: D values of
+ * the data type.  Exact (no rounding).
+ */
+kc_status kc_root_box(kc_ctx *ctx, void *lo, void *hi);
+
+/*
+ * kc_lower_bounds -- the closed-form node lower bound of Section 3.1:
+ *   beta(M) = max_s min_k beta_s^k(M^k),  beta_s^k = sum_a (x_{s,a} - mid{lo, x_{s,a}, hi})^2
+ * (Eqs. 9-11), for B nodes, over all N samples.
+ *   lo, hi     [B][K][D] of the data type, lo <= hi.
+ *   lb_out     [B] double: a certified bound, never above the exact real value
+ *              of beta(M); for float data it is the float evaluation deflated
+ *              by its proved rounding-error bound (relative gap below 1e-6 for
+ *              D <= 16), for double data the double evaluation deflated by a
+ *              few units in the last place.
+ *   lb_raw_out [B] double or NULL: the value as evaluated (float data: the
+ *              float result; double data: bit-identical to a serial
+ *              double-precision evaluation in attribute order).
+ *   argmax_out [B] int64 or NULL: a sample attaining the evaluated maximum
+ *              (smallest index on ties).
+ * Node batches larger than the shared-memory budget are processed in chunks.
+ */
+kc_status kc_lower_bounds(kc_ctx *ctx, const void *lo, const void *hi, int32_t B, double *lb_out,
+                          double *lb_raw_out, int64_t *argmax_out);
+
+/*
+ * kc_upper_bound -- the objective of Eq. 1 at S center sets on samples
+ * (the upper bound alpha(M) of Eq. 12):
+ *   alpha = max_s min_k ||x_s - x_{c_k}||^2.
+ *   centers    [S][K] int64 sample indices in [0, N).
+ *   ub_out     [S] double: the value in double precision, bit-identical to a
+ *              serial double evaluation (attribute order, no fused multiply-add),
+ *              over all N samples.
+ *   worst_out  [S] int64 or NULL: the sample attaining it (smallest index on ties).
+ * Float data are screened in float with a proved error bound and only the
+ * samples that can attain the maximum are re-evaluated in double.
+ */
+kc_status kc_upper_bound(kc_ctx *ctx, const int64_t *centers, int32_t S, double *ub_out,
+                         int64_t *worst_out);
+
+/*
+ * kc_fft -- Farthest First Traversal, Algorithm 2: start at sample `start`,
+ * then repeatedly add the sample farthest (in double precision) from the
+ * chosen set until K are chosen.  centers_out: K int64; obj_out: the
+ * objective (Eq. 1) of the chosen set, or NULL.
+ */
+kc_status kc_fft(kc_ctx *ctx, int64_t start, int64_t *centers_out, double *obj_out);
+
+/*
+ * kc_tighten -- cluster assignment and bounds tightening of B nodes given an
+ * upper bound alpha (Section 4.1, Algorithms 3 and 4):
+ *   step A  center-based assignment: sample s leaves cluster k when
+ *           beta_s^k > alpha (Lemma 1); one cluster left assigns s to it;
+ *   box-BT  M'^k = M^k cap [max_j x_j - sqrt(alpha), min_j x_j + sqrt(alpha)]
+ *           over the samples j assigned to k (and the seed of k);
+ *   step B  sample-based assignment against the representatives of each
+ *           cluster (the seed, then the assigned samples with the smallest
+ *           and largest value of each attribute, at most ball_cap):
+ *           ||x_s - x_j||^2 > 4 alpha excludes k (Lemma 2);
+ *   ball-BT S_+^k = samples in M'^k within sqrt(alpha) of every
+ *           representative of k; M^k_hat = bbox(S_+^k) cap box-BT of the
+ *           step-B assignments ("centers on samples", Algorithm 4).
+ * For float data every exclusion is taken only where the float evaluation
+ * proves it, so the tightened boxes contain the exact ones; for double data
+ * the decisions equal a serial double evaluation.
+ *   lo, hi          [B][K][D] input boxes.
+ *   alpha           the upper bound (double).
+ *   seeds           [K] int64 sample indices pre-assigned to clusters
+ *                   (Section 4.1.1), or NULL.
+ *   lo_out, hi_out  [B][K][D] tightened boxes (may alias lo, hi).
+ *   counts          [B][K] int64 |S_+^k|, or NULL.
+ *   cand            [B][K] int64: the sample of S_+^k closest to the midpoint
+ *                   of M'^k (an upper-bound candidate), -1 if none, or NULL.
+ *   lb_out          [B] double certified lower bound of the input boxes, or NULL.
+ *   status          [B] int8: 0 feasible, 1 proved to hold no solution of
+ *                   value <= alpha, 2 leaf (every tightened box is a point).
+ * ball_cap <= 0 selects the default of 50.
+ */
+kc_status kc_tighten(kc_ctx *ctx, const void *lo, const void *hi, int32_t B, double alpha,
+                     const int64_t *seeds, int32_t ball_cap, void *lo_out, void *hi_out,
+                     int64_t *counts, int64_t *cand, double *lb_out, int8_t *status);
+
+/*
+ * kc_sample_reduction -- Algorithm 5 against a list of M nodes: sample s is
+ * deleted when in every node it is redundant for the lower bound
+ * (alpha_s(M) = min_k max over mu in M^k of ||x_s - mu||^2 < beta_glob,
+ * Eq. 13) and for the upper bound (for every k: x_s outside M^k, or some
+ * representative j of k has ||x_s - x_j||^2 > alpha, Section 4.2.2).
+ *   lo, hi        [M][K][D] node boxes.
+ *   reps          [M][K][R] int64 representatives (-1 = unused slot), or NULL.
+ *   R             slots per cluster in reps.
+ *   beta_glob     the best lower bound; alpha the upper bound.
+ *   active_inout  [N] uint8 mask: 1 = sample still present; cleared where
+ *                 the sample is deleted.  Float data delete only where the
+ *                 float evaluation proves redundancy.
+ *   n_active_out  remaining samples, or NULL.
+ */
+kc_status kc_sample_reduction(kc_ctx *ctx, const void *lo, const void *hi, int32_t M,
+                              const int64_t *reps, int32_t R, double beta_glob, double alpha,
+                              uint8_t *active_inout, int64_t *n_active_out);
+
+/* Options of kc_solve; kc_solve_defaults() fills the defaults shown. */
+typedef struct {
+    double tol;            /* 1e-12: stop when (UB - LB) / UB <= tol (Section 6.1 gap) */
+    double time_limit_s;   /* 0: none */
+    int64_t node_limit;    /* 0: none */
+    int32_t batch;         /* 0: automatic; nodes bounded per launch */
+    int32_t ball_cap;      /* 50: representatives per cluster */
+    int32_t i_sr;          /* 1: sample reduction every i_sr batches, 0: off */
+    int32_t use_bt;        /* 1: assignment + bounds tightening (BB+CF+BT); 0: BB+CF */
+    int32_t order;         /* 0: best bound; 1: learned node scorer (needs weights) */
+    int32_t use_graph;     /* 1: replay each batch's kernels as a CUDA graph */
+    int32_t verbose;       /* 0 */
+    uint64_t seed;         /* 0: FFT start = seed mod N */
+    const char *log_path;  /* NULL, or a file receiving one JSON line per node visit */
+} kc_solve_opts;
+
+typedef struct {
+    double objective;      /* incumbent objective recomputed in double over all N samples */
+    double lower_bound;    /* certified lower bound on the optimum */
+    double gap;            /* (objective - lower_bound) / objective */
+    int64_t centers[16];   /* K sample indices */
+    int64_t nodes;         /* nodes visited */
+    int64_t batches;       /* bounding launches */
+    int64_t active_final;  /* samples left after sample reduction */
+    double fft_objective;  /* objective of the root FFT solution */
+    double seconds;        /* wall time of the solve */
+    int32_t seeds_found;   /* the FFT points were K initial seeds (Section 4.1.1) */
+    int32_t status;        /* KC_OK, KC_ETIMEOUT or KC_ELIMIT */
+} kc_result;
+
+void kc_solve_defaults(kc_solve_opts *opt);
+
+/*
+ * kc_solve -- the branch and bound of Algorithm 1 to a certified optimum:
+ * root box, FFT upper bound and seeds, then batches of open nodes are
+ * bounded, tightened and branched on the GPU (max-range variable, midpoint
+ * value), pruning every node whose certified lower bound reaches the upper
+ * bound, with sample reduction between batches.  The returned objective is
+ * recomputed in double over all samples.  opt may be NULL (defaults); tol
+ * overrides opt->tol when >= 0.  Returns KC_OK at optimality within tol,
+ * KC_ETIMEOUT / KC_ELIMIT (with *out filled) at a limit.
+ */
+kc_status kc_solve(kc_ctx *ctx, double tol, const kc_solve_opts *opt, kc_result *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KC_H_ */

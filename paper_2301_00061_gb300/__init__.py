@@ -1,0 +1,322 @@
+"""GB300 K-center branch and bound: Python binding of ``libkc.so``.
+
+The functions below carry the names of the C ABI in ``include/kc.h`` and only
+marshal arguments (tensor/array -> pointer, dtype and shape checks); every
+step of the computation runs in the library's CUDA kernels.  Arrays may be
+torch tensors (CUDA or CPU) or numpy arrays; CUDA tensors are passed as
+device pointers, everything else as host pointers.
+
+Importing this package raises ImportError when the library has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``): there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "KCError", "KC_F32", "KC_F64", "KC_ROW_MAJOR", "KC_COL_MAJOR", "SolveOpts", "Result",
+    "kc_create", "kc_destroy", "kc_last_error", "kc_set_stream", "kc_launch_count", "kc_root_box",
+    "kc_lower_bounds", "kc_upper_bound", "kc_fft", "kc_tighten", "kc_sample_reduction",
+    "kc_solve_defaults", "kc_solve", "KCenter", "library_path",
+]
+
+KC_F32, KC_F64 = 0, 1
+KC_ROW_MAJOR, KC_COL_MAJOR = 0, 1
+_STATUS = {0: "KC_OK", 1: "KC_EINVAL", 2: "KC_ENOMEM", 3: "KC_ECUDA", 4: "KC_ETIMEOUT",
+           5: "KC_ELIMIT", 6: "KC_EINTERNAL"}
+
+
+class KCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double), ("time_limit_s", C.c_double), ("node_limit", C.c_int64),
+        ("batch", C.c_int32), ("ball_cap", C.c_int32), ("i_sr", C.c_int32), ("use_bt", C.c_int32),
+        ("order", C.c_int32), ("use_graph", C.c_int32), ("verbose", C.c_int32), ("seed", C.c_uint64),
+        ("log_path", C.c_char_p),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("objective", C.c_double), ("lower_bound", C.c_double), ("gap", C.c_double),
+        ("centers", C.c_int64 * 16), ("nodes", C.c_int64), ("batches", C.c_int64),
+        ("active_final", C.c_int64), ("fft_objective", C.c_double), ("seconds", C.c_double),
+        ("seeds_found", C.c_int32), ("status", C.c_int32),
+    ]
+
+
+def library_path():
+    return _build.LIB
+
+
+def _load():
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libkc.so is not built ({_build.LIB}); run __graft_entry__.build()")
+    L = C.CDLL(_build.LIB)
+    P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    sig = {
+        "kc_create": (I32, [P, I64, I32, I32, I32, I32, P, C.POINTER(P)]),
+        "kc_destroy": (None, [P]),
+        "kc_last_error": (C.c_char_p, [P]),
+        "kc_create_error": (C.c_char_p, []),
+        "kc_set_stream": (I32, [P, P]),
+        "kc_launch_count": (I64, [P]),
+        "kc_root_box": (I32, [P, P, P]),
+        "kc_lower_bounds": (I32, [P, P, P, I32, P, P, P]),
+        "kc_upper_bound": (I32, [P, P, I32, P, P]),
+        "kc_fft": (I32, [P, I64, P, P]),
+        "kc_tighten": (I32, [P, P, P, I32, D, P, I32, P, P, P, P, P, P]),
+        "kc_sample_reduction": (I32, [P, P, P, I32, P, I32, D, D, P, P]),
+        "kc_solve_defaults": (None, [C.POINTER(SolveOpts)]),
+        "kc_solve": (I32, [P, D, C.POINTER(SolveOpts), C.POINTER(Result)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+_lib = _load()
+
+
+# ------------------------------------------------------------- marshalling
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _dtype_code(x):
+    name = str(x.dtype)
+    if name.endswith("float32"):
+        return KC_F32
+    if name.endswith("float64"):
+        return KC_F64
+    raise TypeError(f"data must be float32 or float64, got {x.dtype}")
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def _check(h, st):
+    if st != 0:
+        msg = _lib.kc_last_error(h).decode() if h else _lib.kc_create_error().decode()
+        raise KCError(st, msg)
+
+
+# ------------------------------------------------------------- C ABI names
+
+def kc_create(X, K, layout=KC_ROW_MAJOR, stream=None):
+    """X: (N, D) row-major (or (D, N) with layout=KC_COL_MAJOR) float32/float64."""
+    if X.ndim != 2:
+        raise ValueError("X must be 2-D")
+    n, d = (X.shape[0], X.shape[1]) if layout == KC_ROW_MAJOR else (X.shape[1], X.shape[0])
+    h = C.c_void_p()
+    st = _lib.kc_create(_ptr(X), n, d, int(K), _dtype_code(X), int(layout), _stream_ptr(stream), C.byref(h))
+    _check(None, st)
+    return h
+
+
+def kc_destroy(h):
+    _lib.kc_destroy(h)
+
+
+def kc_last_error(h):
+    return _lib.kc_last_error(h).decode()
+
+
+def kc_set_stream(h, stream):
+    _check(h, _lib.kc_set_stream(h, _stream_ptr(stream)))
+
+
+def kc_launch_count(h):
+    return int(_lib.kc_launch_count(h))
+
+
+def kc_root_box(h, lo, hi):
+    _check(h, _lib.kc_root_box(h, _ptr(lo), _ptr(hi)))
+
+
+def kc_lower_bounds(h, lo, hi, lb, lb_raw=None, argmax=None):
+    B = lo.shape[0]
+    _check(h, _lib.kc_lower_bounds(h, _ptr(lo), _ptr(hi), B, _ptr(lb), _ptr(lb_raw), _ptr(argmax)))
+
+
+def kc_upper_bound(h, centers, ub, worst=None):
+    _check(h, _lib.kc_upper_bound(h, _ptr(centers), centers.shape[0], _ptr(ub), _ptr(worst)))
+
+
+def kc_fft(h, start, centers, obj=None):
+    _check(h, _lib.kc_fft(h, int(start), _ptr(centers), _ptr(obj)))
+
+
+def kc_tighten(h, lo, hi, alpha, seeds=None, ball_cap=0, lo_out=None, hi_out=None, counts=None,
+               cand=None, lb=None, status=None):
+    B = lo.shape[0]
+    _check(h, _lib.kc_tighten(h, _ptr(lo), _ptr(hi), B, float(alpha), _ptr(seeds), int(ball_cap),
+                              _ptr(lo_out), _ptr(hi_out), _ptr(counts), _ptr(cand), _ptr(lb),
+                              _ptr(status)))
+
+
+def kc_sample_reduction(h, lo, hi, beta_glob, alpha, active, reps=None, n_active=None):
+    M = lo.shape[0]
+    R = 0 if reps is None else reps.shape[-1]
+    _check(h, _lib.kc_sample_reduction(h, _ptr(lo), _ptr(hi), M, _ptr(reps), R, float(beta_glob),
+                                       float(alpha), _ptr(active), _ptr(n_active)))
+
+
+def kc_solve_defaults():
+    o = SolveOpts()
+    _lib.kc_solve_defaults(C.byref(o))
+    return o
+
+
+def kc_solve(h, tol=-1.0, opts=None):
+    r = Result()
+    st = _lib.kc_solve(h, float(tol), C.byref(opts) if opts is not None else None, C.byref(r))
+    if st not in (0, 4, 5):
+        _check(h, st)
+    return r, st
+
+
+# ------------------------------------------------------------- convenience
+
+class KCenter:
+    """A dataset resident on the GPU plus the bound / solve calls on it.
+
+    Outputs are allocated where the inputs live: CUDA tensors in -> CUDA
+    tensors out, numpy (or CPU tensors) in -> numpy out.
+    """
+
+    def __init__(self, X, K, layout=KC_ROW_MAJOR, stream=None):
+        self.K = int(K)
+        self.dtype = _dtype_code(X)
+        self.N = X.shape[0] if layout == KC_ROW_MAJOR else X.shape[1]
+        self.D = X.shape[1] if layout == KC_ROW_MAJOR else X.shape[0]
+        self.h = kc_create(X, K, layout, stream)
+
+    def close(self):
+        if self.h:
+            kc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # output allocation next to a reference input
+    def _alloc(self, like, shape, kind):
+        if like is not None and _is_torch(like) and like.is_cuda:
+            import torch
+            dt = {"f64": torch.float64, "i64": torch.int64, "i8": torch.int8, "u8": torch.uint8,
+                  "data": torch.float32 if self.dtype == KC_F32 else torch.float64}[kind]
+            return torch.empty(shape, dtype=dt, device=like.device)
+        dt = {"f64": np.float64, "i64": np.int64, "i8": np.int8, "u8": np.uint8,
+              "data": np.float32 if self.dtype == KC_F32 else np.float64}[kind]
+        return np.empty(shape, dtype=dt)
+
+    def launch_count(self):
+        return kc_launch_count(self.h)
+
+    def root_box(self, like=None):
+        lo = self._alloc(like, (self.D,), "data")
+        hi = self._alloc(like, (self.D,), "data")
+        kc_root_box(self.h, lo, hi)
+        return lo, hi
+
+    def lower_bounds(self, lo, hi):
+        B = lo.shape[0]
+        lb = self._alloc(lo, (B,), "f64")
+        raw = self._alloc(lo, (B,), "f64")
+        arg = self._alloc(lo, (B,), "i64")
+        kc_lower_bounds(self.h, lo, hi, lb, raw, arg)
+        return lb, raw, arg
+
+    def upper_bound(self, centers):
+        S = centers.shape[0]
+        ub = self._alloc(centers, (S,), "f64")
+        worst = self._alloc(centers, (S,), "i64")
+        kc_upper_bound(self.h, centers, ub, worst)
+        return ub, worst
+
+    def fft(self, start, like=None):
+        c = self._alloc(like, (self.K,), "i64")
+        obj = self._alloc(like, (1,), "f64")
+        kc_fft(self.h, start, c, obj)
+        return c, obj
+
+    def tighten(self, lo, hi, alpha, seeds=None, ball_cap=0):
+        B = lo.shape[0]
+        lo_o = self._alloc(lo, tuple(lo.shape), "data")
+        hi_o = self._alloc(lo, tuple(lo.shape), "data")
+        counts = self._alloc(lo, (B, self.K), "i64")
+        cand = self._alloc(lo, (B, self.K), "i64")
+        lb = self._alloc(lo, (B,), "f64")
+        status = self._alloc(lo, (B,), "i8")
+        kc_tighten(self.h, lo, hi, alpha, seeds, ball_cap, lo_o, hi_o, counts, cand, lb, status)
+        return {"lo": lo_o, "hi": hi_o, "count": counts, "cand": cand, "lb": lb, "status": status}
+
+    def sample_reduction(self, lo, hi, beta_glob, alpha, active, reps=None):
+        n_act = self._alloc(lo, (1,), "i64")
+        kc_sample_reduction(self.h, lo, hi, beta_glob, alpha, active, reps, n_act)
+        return active, int(n_act[0])
+
+    def solve(self, tol=1e-12, **kw):
+        o = kc_solve_defaults()
+        o.tol = tol
+        log = kw.pop("log_path", None)
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown solve option {k}")
+            setattr(o, k, v)
+        if log is not None:
+            o.log_path = log.encode()
+        r, st = kc_solve(self.h, tol, o)
+        return {
+            "objective": r.objective, "lower_bound": r.lower_bound, "gap": r.gap,
+            "centers": np.array(r.centers[: self.K]), "nodes": r.nodes, "batches": r.batches,
+            "active_final": r.active_final, "fft_objective": r.fft_objective, "seconds": r.seconds,
+            "seeds_found": bool(r.seeds_found), "status": st,
+        }

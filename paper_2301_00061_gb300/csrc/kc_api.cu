@@ -1,0 +1,371 @@
+// kc_api.cu -- the C ABI of include/kc.h: context lifetime, argument
+// validation, host/device pointer staging, and the entry points that are a
+// single kernel family (root box, lower bounds, upper bounds, FFT).
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "kc_internal.cuh"
+
+namespace kc {
+
+namespace {
+thread_local std::string g_create_err;
+}
+
+kc_status set_err(kc_ctx *c, kc_status st, const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_err = buf;
+    return st;
+}
+
+kc_status after_launch(kc_ctx *c, const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(c, KC_ECUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+    ++c->launches;
+    return KC_OK;
+}
+
+kc_status ensure(kc_ctx *c, DevBuf &b, size_t bytes)
+{
+    if (bytes <= b.bytes) return KC_OK;
+    size_t nb = std::max(bytes, b.bytes + b.bytes / 2);
+    nb = (nb + 4095) & ~(size_t)4095;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);   // implicitly waits for work using it
+        b.p = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return set_err(c, KC_ECUDA, "cudaFree: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return set_err(c, KC_ENOMEM, "cudaMalloc(%zu bytes): %s", nb, cudaGetErrorString(e));
+    }
+    b.bytes = nb;
+    return KC_OK;
+}
+
+kc_status ensure_pinned(kc_ctx *c, size_t bytes)
+{
+    if (bytes <= c->pinned_bytes) return KC_OK;
+    if (c->pinned) {
+        KC_CUDA(c, cudaStreamSynchronize(c->stream));
+        cudaFreeHost(c->pinned);
+        c->pinned = nullptr;
+        c->pinned_bytes = 0;
+    }
+    size_t nb = (std::max(bytes, (size_t)1 << 16) + 4095) & ~(size_t)4095;
+    if (cudaMallocHost(&c->pinned, nb) != cudaSuccess) {
+        c->pinned = nullptr;
+        cudaGetLastError();
+        return set_err(c, KC_ENOMEM, "cudaMallocHost(%zu bytes) failed", nb);
+    }
+    c->pinned_bytes = nb;
+    return KC_OK;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Staging of one call's array arguments.  Inputs in host memory are copied to
+// device scratch; outputs in host memory are written to device scratch and
+// copied back by finish().
+struct Stager {
+    kc_ctx *c;
+    struct Item {
+        const void *user;
+        size_t bytes;
+        size_t off;
+        bool in;
+        bool host;
+    };
+    std::vector<Item> items;
+    size_t total = 0;
+    explicit Stager(kc_ctx *cc) : c(cc) {}
+
+    // Registers an argument; returns its index.
+    int add(const void *user, size_t bytes, bool in)
+    {
+        Item it{user, bytes, 0, in, user != nullptr && !is_device_ptr(user)};
+        if (it.host) {
+            it.off = total;
+            total += (bytes + 255) & ~(size_t)255;
+        }
+        items.push_back(it);
+        return (int)items.size() - 1;
+    }
+    // Allocates scratch and copies host inputs; then dev(i) is valid.
+    kc_status begin()
+    {
+        if (total == 0) return KC_OK;
+        KC_TRY(ensure(c, c->stage_in, total));
+        for (auto &it : items)
+            if (it.host && it.in && it.bytes)
+                KC_CUDA(c, cudaMemcpyAsync(static_cast<char *>(c->stage_in.p) + it.off, it.user, it.bytes,
+                                           cudaMemcpyHostToDevice, c->stream));
+        return KC_OK;
+    }
+    void *dev(int i) const
+    {
+        const Item &it = items[i];
+        if (!it.user) return nullptr;
+        return it.host ? static_cast<char *>(c->stage_in.p) + it.off : const_cast<void *>(it.user);
+    }
+    bool any_host_out() const
+    {
+        for (auto &it : items)
+            if (it.host && !it.in) return true;
+        return false;
+    }
+    // Copies host outputs back and waits when any output is in host memory.
+    kc_status finish()
+    {
+        bool wait = false;
+        for (auto &it : items)
+            if (it.host && !it.in && it.bytes) {
+                KC_CUDA(c, cudaMemcpyAsync(const_cast<void *>(it.user), static_cast<char *>(c->stage_in.p) + it.off,
+                                           it.bytes, cudaMemcpyDeviceToHost, c->stream));
+                wait = true;
+            }
+        if (wait) KC_CUDA(c, cudaStreamSynchronize(c->stream));
+        return KC_OK;
+    }
+};
+
+}  // namespace kc
+
+using namespace kc;
+
+extern "C" {
+
+const char *kc_create_error(void) { return g_create_err.c_str(); }
+
+const char *kc_last_error(const kc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t kc_launch_count(const kc_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+kc_status kc_set_stream(kc_ctx *ctx, void *stream)
+{
+    if (!ctx) return KC_EINVAL;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return KC_OK;
+}
+
+void kc_destroy(kc_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (DevBuf *b : {&ctx->part, &ctx->stage_in, &ctx->stage_out, &ctx->work})
+        if (b->p) cudaFree(b->p);
+    if (ctx->X) cudaFree(ctx->X);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    delete ctx;
+}
+
+kc_status kc_create(const void *X, int64_t N, int32_t D, int32_t K, kc_dtype dt, kc_layout layout, void *stream,
+                    kc_ctx **out)
+{
+    g_create_err.clear();
+    if (!out) return set_err(nullptr, KC_EINVAL, "kc_create: out is NULL");
+    *out = nullptr;
+    if (!X) return set_err(nullptr, KC_EINVAL, "kc_create: X is NULL");
+    if (dt != KC_F32 && dt != KC_F64) return set_err(nullptr, KC_EINVAL, "kc_create: bad dtype %d", (int)dt);
+    if (layout != KC_ROW_MAJOR && layout != KC_COL_MAJOR)
+        return set_err(nullptr, KC_EINVAL, "kc_create: bad layout %d", (int)layout);
+    if (K < 1 || K > kMaxK) return set_err(nullptr, KC_EINVAL, "kc_create: K=%d outside [1, %d]", K, kMaxK);
+    if (D < 1 || D > kMaxD) return set_err(nullptr, KC_EINVAL, "kc_create: D=%d outside [1, %d]", D, kMaxD);
+    if (N < K || N > 4294967294ll)
+        return set_err(nullptr, KC_EINVAL, "kc_create: N=%lld outside [K, 4294967294]", (long long)N);
+
+    kc_ctx *c = new (std::nothrow) kc_ctx;
+    if (!c) return set_err(nullptr, KC_ENOMEM, "kc_create: out of host memory");
+    auto fail = [&](kc_status st) {
+        g_create_err = c->err;
+        kc_destroy(c);
+        return st;
+    };
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->N = N;
+    c->D = D;
+    c->K = K;
+    c->dt = dt;
+    c->esize = dt == KC_F32 ? 4 : 8;
+    const int64_t align = 256 / (int64_t)c->esize;
+    c->ldx = (N + align - 1) / align * align;
+    if (cudaGetDevice(&c->dev) != cudaSuccess) {
+        set_err(c, KC_ECUDA, "kc_create: no CUDA device");
+        return fail(KC_ECUDA);
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->dev) != cudaSuccess) {
+        set_err(c, KC_ECUDA, "kc_create: cudaGetDeviceProperties failed");
+        return fail(KC_ECUDA);
+    }
+    c->num_sms = prop.multiProcessorCount;
+    if (const char *e = getenv("KC_LB_ST")) c->lb_st = atoi(e);
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    const size_t xbytes = (size_t)D * c->ldx * c->esize;
+    if (cudaMalloc(&c->X, xbytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->X = nullptr;
+        set_err(c, KC_ENOMEM, "kc_create: cannot allocate %zu bytes for the data", xbytes);
+        return fail(KC_ENOMEM);
+    }
+    const size_t src_bytes = (size_t)N * D * c->esize;
+    kc_status st = KC_OK;
+    if (is_device_ptr(X)) {
+        st = launch_ingest(c, X, layout, N, D);
+    } else if (layout == KC_COL_MAJOR) {
+        cudaError_t e = cudaMemcpy2DAsync(c->X, c->ldx * c->esize, X, N * c->esize, N * c->esize, D,
+                                          cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess && c->ldx > N)
+            e = cudaMemset2DAsync(static_cast<char *>(c->X) + N * c->esize, c->ldx * c->esize, 0,
+                                  (c->ldx - N) * c->esize, D, c->stream);
+        if (e != cudaSuccess) st = set_err(c, KC_ECUDA, "kc_create: upload failed: %s", cudaGetErrorString(e));
+    } else {
+        st = ensure(c, c->work, src_bytes);
+        if (st == KC_OK) {
+            cudaError_t e = cudaMemcpyAsync(c->work.p, X, src_bytes, cudaMemcpyHostToDevice, c->stream);
+            if (e != cudaSuccess) st = set_err(c, KC_ECUDA, "kc_create: upload failed: %s", cudaGetErrorString(e));
+        }
+        if (st == KC_OK) st = launch_ingest(c, c->work.p, layout, N, D);
+    }
+    if (st != KC_OK) return fail(st);
+    // non-finite scan (with the root box, which is cheap)
+    st = ensure(c, c->stage_out, 2 * (size_t)kMaxD * 8 + 256);
+    if (st != KC_OK) return fail(st);
+    char *so = static_cast<char *>(c->stage_out.p);
+    int *flag_dev = reinterpret_cast<int *>(so + 2 * (size_t)kMaxD * 8);
+    st = launch_root_box(c, so, so + (size_t)kMaxD * 8, flag_dev);
+    if (st != KC_OK) return fail(st);
+    int flag = 0;
+    if (cudaMemcpyAsync(&flag, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        set_err(c, KC_ECUDA, "kc_create: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(KC_ECUDA);
+    }
+    if (flag) {
+        set_err(c, KC_EINVAL, "kc_create: the data contain NaN or infinite values");
+        return fail(KC_EINVAL);
+    }
+    if (src_bytes > ((size_t)64 << 20) && c->work.p) {   // do not keep a dataset-sized scratch around
+        cudaFree(c->work.p);
+        c->work.p = nullptr;
+        c->work.bytes = 0;
+    }
+    *out = c;
+    return KC_OK;
+}
+
+kc_status kc_root_box(kc_ctx *c, void *lo, void *hi)
+{
+    if (!c) return KC_EINVAL;
+    if (!lo || !hi) return set_err(c, KC_EINVAL, "kc_root_box: NULL output");
+    const size_t bytes = (size_t)c->D * c->esize;
+    Stager sg(c);
+    int ilo = sg.add(lo, bytes, false), ihi = sg.add(hi, bytes, false);
+    KC_TRY(sg.begin());
+    KC_TRY(ensure(c, c->stage_out, 2 * (size_t)kMaxD * 8 + 256));
+    int *flag = reinterpret_cast<int *>(static_cast<char *>(c->stage_out.p) + 2 * (size_t)kMaxD * 8);
+    KC_TRY(launch_root_box(c, sg.dev(ilo), sg.dev(ihi), flag));
+    return sg.finish();
+}
+
+kc_status kc_lower_bounds(kc_ctx *c, const void *lo, const void *hi, int32_t B, double *lb_out,
+                          double *lb_raw_out, int64_t *argmax_out)
+{
+    if (!c) return KC_EINVAL;
+    if (B < 0) return set_err(c, KC_EINVAL, "kc_lower_bounds: B=%d < 0", B);
+    if (B == 0) return KC_OK;
+    if (!lo || !hi || !lb_out) return set_err(c, KC_EINVAL, "kc_lower_bounds: NULL argument");
+    const size_t box = (size_t)B * c->K * c->D * c->esize;
+    Stager sg(c);
+    int ilo = sg.add(lo, box, true), ihi = sg.add(hi, box, true);
+    int ilb = sg.add(lb_out, (size_t)B * 8, false);
+    int iraw = sg.add(lb_raw_out, (size_t)B * 8, false);
+    int iarg = sg.add(argmax_out, (size_t)B * 8, false);
+    KC_TRY(sg.begin());
+    KC_TRY(launch_lower_bounds(c, sg.dev(ilo), sg.dev(ihi), B, static_cast<double *>(sg.dev(ilb)),
+                               static_cast<double *>(sg.dev(iraw)), static_cast<int64_t *>(sg.dev(iarg))));
+    return sg.finish();
+}
+
+static kc_status check_centers(kc_ctx *c, const int64_t *centers, size_t count)
+{
+    std::vector<int64_t> h(count);
+    const int64_t *p = centers;
+    if (is_device_ptr(centers)) {
+        KC_CUDA(c, cudaMemcpyAsync(h.data(), centers, count * 8, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaStreamSynchronize(c->stream));
+        p = h.data();
+    }
+    for (size_t i = 0; i < count; ++i)
+        if (p[i] < 0 || p[i] >= c->N)
+            return set_err(c, KC_EINVAL, "center index %lld outside [0, %lld)", (long long)p[i], (long long)c->N);
+    return KC_OK;
+}
+
+kc_status kc_upper_bound(kc_ctx *c, const int64_t *centers, int32_t S, double *ub_out, int64_t *worst_out)
+{
+    if (!c) return KC_EINVAL;
+    if (S < 0) return set_err(c, KC_EINVAL, "kc_upper_bound: S=%d < 0", S);
+    if (S == 0) return KC_OK;
+    if (!centers || !ub_out) return set_err(c, KC_EINVAL, "kc_upper_bound: NULL argument");
+    KC_TRY(check_centers(c, centers, (size_t)S * c->K));
+    Stager sg(c);
+    int ic = sg.add(centers, (size_t)S * c->K * 8, true);
+    int iu = sg.add(ub_out, (size_t)S * 8, false);
+    int iw = sg.add(worst_out, (size_t)S * 8, false);
+    KC_TRY(sg.begin());
+    KC_TRY(launch_objective(c, full_view(c), static_cast<const int64_t *>(sg.dev(ic)), S, c->K,
+                            __builtin_huge_val(), static_cast<double *>(sg.dev(iu)),
+                            static_cast<int64_t *>(sg.dev(iw))));
+    return sg.finish();
+}
+
+kc_status kc_fft(kc_ctx *c, int64_t start, int64_t *centers_out, double *obj_out)
+{
+    if (!c) return KC_EINVAL;
+    if (!centers_out) return set_err(c, KC_EINVAL, "kc_fft: NULL argument");
+    if (start < 0 || start >= c->N) return set_err(c, KC_EINVAL, "kc_fft: start %lld outside [0, N)", (long long)start);
+    Stager sg(c);
+    int ic = sg.add(centers_out, (size_t)c->K * 8, false);
+    int io = sg.add(obj_out, 8, false);
+    KC_TRY(sg.begin());
+    int64_t *T = static_cast<int64_t *>(sg.dev(ic));
+    KC_CUDA(c, cudaMemcpyAsync(T, &start, 8, cudaMemcpyHostToDevice, c->stream));
+    KC_CUDA(c, cudaStreamSynchronize(c->stream));   // `start` lives on this stack frame
+    KC_TRY(ensure(c, c->stage_out, 2 * (size_t)kMaxD * 8 + 256 + 64));
+    double *scratch = reinterpret_cast<double *>(static_cast<char *>(c->stage_out.p) + 2 * (size_t)kMaxD * 8 + 256);
+    // Algorithm 2: the t-th point is the sample farthest from the first t.
+    for (int t = 1; t < c->K; ++t)
+        KC_TRY(launch_objective(c, full_view(c), T, 1, t, __builtin_huge_val(), scratch, T + t));
+    if (obj_out)
+        KC_TRY(launch_objective(c, full_view(c), T, 1, c->K, __builtin_huge_val(), static_cast<double *>(sg.dev(io)),
+                                nullptr));
+    return sg.finish();
+}
+
+}  // extern "C"

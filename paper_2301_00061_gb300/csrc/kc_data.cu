@@ -1,0 +1,141 @@
+// kc_data.cu -- dataset ingest (attribute-major padded copy), the root region
+// M0 of Section 2.1 (per-attribute min / max) with the non-finite check, and
+// stream compaction of the surviving samples after sample reduction.
+#include <cuda_runtime.h>
+
+#include "kc_device.cuh"
+#include "kc_internal.cuh"
+
+namespace kc {
+
+namespace {
+
+// Row-major [N][D] -> attribute-major [D][ld], zero padding in [N, ld).
+template <typename T>
+__global__ void transpose_in(const T *__restrict__ src, int64_t N, int D, int64_t ld, T *__restrict__ dst)
+{
+    const int64_t total = (int64_t)D * ld;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(i / ld);
+        const int64_t s = i - (int64_t)a * ld;
+        dst[i] = s < N ? src[s * D + a] : T(0);
+    }
+}
+
+// Per-attribute min / max with order-preserving integer atomics (exact), and
+// a flag for NaN / Inf.
+template <typename T>
+__global__ void root_box_kernel(const T *__restrict__ X, int64_t ld, int64_t N, int D,
+                                unsigned long long *__restrict__ omin, unsigned long long *__restrict__ omax,
+                                int *__restrict__ nonfinite)
+{
+    __shared__ unsigned long long smin[kMaxD], smax[kMaxD];
+    __shared__ int sbad;
+    for (int a = threadIdx.x; a < D; a += blockDim.x) { smin[a] = ~0ull; smax[a] = 0ull; }
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    for (int a = 0; a < D; ++a) {
+        unsigned long long mn = ~0ull, mx = 0ull;
+        int bad = 0;
+        for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N;
+             s += (int64_t)gridDim.x * blockDim.x) {
+            const T v = X[(size_t)a * ld + s];
+            if (!isfinite((double)v)) bad = 1;
+            unsigned long long o;
+            if constexpr (sizeof(T) == 4) o = ord_f32((float)v);
+            else o = ord_f64((double)v);
+            mn = o < mn ? o : mn;
+            mx = o > mx ? o : mx;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long a2 = __shfl_xor_sync(0xffffffffu, mn, off);
+            const unsigned long long b2 = __shfl_xor_sync(0xffffffffu, mx, off);
+            mn = a2 < mn ? a2 : mn;
+            mx = b2 > mx ? b2 : mx;
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&smin[a], mn);
+            atomicMax(&smax[a], mx);
+            if (bad) sbad = 1;
+        }
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < D; a += blockDim.x) {
+        atomicMin(&omin[a], smin[a]);
+        atomicMax(&omax[a], smax[a]);
+    }
+    if (threadIdx.x == 0 && sbad) atomicOr(nonfinite, 1);
+}
+
+__global__ void init_minmax(unsigned long long *omin, unsigned long long *omax, int D, int *flag)
+{
+    for (int a = threadIdx.x; a < D; a += blockDim.x) { omin[a] = ~0ull; omax[a] = 0ull; }
+    if (threadIdx.x == 0 && flag) *flag = 0;
+}
+
+template <typename T>
+__global__ void decode_minmax(const unsigned long long *omin, const unsigned long long *omax, int D, T *lo, T *hi)
+{
+    for (int a = threadIdx.x; a < D; a += blockDim.x) {
+        if constexpr (sizeof(T) == 4) {
+            lo[a] = unord_f32((uint32_t)omin[a]);
+            hi[a] = unord_f32((uint32_t)omax[a]);
+        } else {
+            lo[a] = unord_f64(omin[a]);
+            hi[a] = unord_f64(omax[a]);
+        }
+    }
+}
+
+}  // namespace
+
+kc_status launch_ingest(kc_ctx *c, const void *src_dev, kc_layout layout, int64_t N, int D)
+{
+    // src_dev is device memory holding the caller's layout.
+    if (layout == KC_COL_MAJOR) {
+        KC_CUDA(c, cudaMemcpy2DAsync(c->X, c->ldx * c->esize, src_dev, N * c->esize, N * c->esize, D,
+                                     cudaMemcpyDeviceToDevice, c->stream));
+        if (c->ldx > N)
+            KC_CUDA(c, cudaMemset2DAsync(static_cast<char *>(c->X) + N * c->esize, c->ldx * c->esize, 0,
+                                         (c->ldx - N) * c->esize, D, c->stream));
+        return KC_OK;
+    }
+    const int grid = c->num_sms * 8;
+    if (c->dt == KC_F32)
+        transpose_in<float><<<grid, 256, 0, c->stream>>>(static_cast<const float *>(src_dev), N, D, c->ldx,
+                                                         static_cast<float *>(c->X));
+    else
+        transpose_in<double><<<grid, 256, 0, c->stream>>>(static_cast<const double *>(src_dev), N, D, c->ldx,
+                                                          static_cast<double *>(c->X));
+    return after_launch(c, "ingest transpose");
+}
+
+kc_status launch_root_box(kc_ctx *c, void *lo, void *hi, int *nonfinite_dev)
+{
+    const int D = c->D;
+    KC_TRY(ensure(c, c->part, (size_t)2 * kMaxD * 8 + 16));
+    unsigned long long *omin = static_cast<unsigned long long *>(c->part.p);
+    unsigned long long *omax = omin + kMaxD;
+    init_minmax<<<1, 64, 0, c->stream>>>(omin, omax, D, nonfinite_dev);
+    KC_TRY(after_launch(c, "root box init"));
+    const int grid = c->num_sms * 4;
+    if (c->dt == KC_F32)
+        root_box_kernel<float><<<grid, 256, 0, c->stream>>>(static_cast<const float *>(c->X), c->ldx, c->N, D,
+                                                            omin, omax, nonfinite_dev);
+    else
+        root_box_kernel<double><<<grid, 256, 0, c->stream>>>(static_cast<const double *>(c->X), c->ldx, c->N,
+                                                             D, omin, omax, nonfinite_dev);
+    KC_TRY(after_launch(c, "root box"));
+    if (c->dt == KC_F32)
+        decode_minmax<float><<<1, 64, 0, c->stream>>>(omin, omax, D, static_cast<float *>(lo),
+                                                      static_cast<float *>(hi));
+    else
+        decode_minmax<double><<<1, 64, 0, c->stream>>>(omin, omax, D, static_cast<double *>(lo),
+                                                       static_cast<double *>(hi));
+    return after_launch(c, "root box decode");
+}
+
+}  // namespace kc

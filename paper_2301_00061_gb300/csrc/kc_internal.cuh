@@ -1,0 +1,171 @@
+// kc_internal.cuh -- private declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/kc.h"
+
+namespace kc {
+
+constexpr int kMaxK = 16;
+constexpr int kMaxD = 64;
+constexpr int kMaxReps = 50;
+constexpr int kThreads = 256;
+
+// Growable device buffer owned by a context.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace kc
+
+struct kc_ctx {
+    int dev = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;       // max dynamic shared memory per block
+    cudaStream_t stream = nullptr;
+    int64_t N = 0;
+    int D = 0, K = 0;
+    kc_dtype dt = KC_F32;
+    size_t esize = 4;
+    int64_t ldx = 0;             // padded row length of the attribute-major copy
+    void *X = nullptr;           // [D][ldx] owned device copy
+    // scratch
+    kc::DevBuf part;             // per-CTA partial results
+    kc::DevBuf stage_in;         // staged host inputs
+    kc::DevBuf stage_out;        // device-side outputs destined for host
+    kc::DevBuf work;             // per-call work arrays
+    void *pinned = nullptr;      // pinned host staging
+    size_t pinned_bytes = 0;
+    int64_t launches = 0;
+    std::string err;
+    // autotuned launch shapes, keyed by kernel family (see kc_tune.cu)
+    int lb_st = 0;               // samples per thread of the float lower-bound kernel
+    int lb_ctas_per_sm = 0;
+};
+
+namespace kc {
+
+// ------------------------------------------------------------------ errors
+
+kc_status set_err(kc_ctx *c, kc_status st, const char *fmt, ...);
+
+#define KC_CUDA(ctx, call)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return ::kc::set_err((ctx), KC_ECUDA, "%s: %s (%s:%d)", #call,              \
+                                 cudaGetErrorString(e_), __FILE__, __LINE__);           \
+    } while (0)
+
+#define KC_TRY(expr)                                                                    \
+    do {                                                                                \
+        kc_status s_ = (expr);                                                          \
+        if (s_ != KC_OK) return s_;                                                     \
+    } while (0)
+
+// Checks the launch that was just issued and counts it.
+kc_status after_launch(kc_ctx *c, const char *what);
+
+// ------------------------------------------------------------ buffers
+
+kc_status ensure(kc_ctx *c, DevBuf &b, size_t bytes);
+kc_status ensure_pinned(kc_ctx *c, size_t bytes);
+bool is_device_ptr(const void *p);
+
+// A host or device array argument resolved to a device pointer.  Inputs in
+// host memory are copied into `buf` (cudaMemcpyAsync on the context stream);
+// outputs in host memory get device scratch and are copied back by
+// finish_outputs().
+struct OutArg {
+    void *user = nullptr;   // caller pointer
+    void *dev = nullptr;    // where kernels write
+    size_t bytes = 0;
+    bool host = false;
+};
+
+// --------------------------------------------------------- rounding margins
+
+// gamma_n = n u / (1 - n u): relative error bound of n roundings (Higham 3.1).
+inline double gamma_n(int n, double u) { return (n * u) / (1.0 - n * u); }
+
+// Float evaluation of a clamp or point distance in this library: the
+// difference (one rounding, squared), ceil(D/2) fused multiply-adds in each
+// of two interleaved chains, one final add.
+inline int f32_roundings(int D) { return 2 + (D + 1) / 2 + 1; }
+// Double evaluation in attribute order with separate multiply and add.
+inline int f64_roundings(int D) { return D + 3; }
+
+constexpr double kU32 = 5.9604644775390625e-08;   // 2^-24
+constexpr double kU64 = 1.1102230246251565e-16;   // 2^-53
+
+// Multiplier that maps an evaluated distance to a certified lower bound
+// (applied with round-down); and the absolute slack for underflow.
+inline double deflate_factor(kc_dtype dt, int D)
+{
+    double g = dt == KC_F32 ? gamma_n(f32_roundings(D), kU32) : gamma_n(f64_roundings(D) + 1, kU64);
+    return (1.0 - g) * (1.0 - 4 * kU64);
+}
+inline double underflow_slack(kc_dtype dt, int D)
+{
+    return dt == KC_F32 ? (D + 2) * 1.401298464324817e-45 : (D + 2) * 4.9406564584124654e-324;
+}
+
+// A set of samples the kernels stream: attribute-major rows X[a*ld + pos],
+// pos < n; ids[pos] is the sample's index in the full dataset (NULL: pos).
+struct View {
+    const void *X = nullptr;
+    int64_t ld = 0;
+    int64_t n = 0;
+    const uint32_t *ids = nullptr;
+};
+inline View full_view(const kc_ctx *c)
+{
+    View v;
+    v.X = c->X;
+    v.ld = c->ldx;
+    v.n = c->N;
+    return v;
+}
+
+// ----------------------------------------------------------- kernel launchers
+// (implemented in the .cu files; all run on c->stream)
+
+// Lower bounds of B nodes (device lo/hi [B][K][D]) -> device lb, lb_raw, argmax.
+kc_status launch_lower_bounds(kc_ctx *c, const void *lo, const void *hi, int B, double *lb,
+                              double *lb_raw, int64_t *argmax);
+kc_status launch_lower_bounds_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int B,
+                                   double *lb, double *lb_raw, int64_t *arg, int st_override);
+
+// Objective (Eq. 1) of S center sets given by device indices [S][K] ->
+// device values [S] (double, exact serial-double value) and argmax [S].
+// alpha_cut: sets whose float screen proves a value >= alpha_cut are not
+// evaluated exactly (their val is set to +inf); pass +inf to evaluate all.
+kc_status launch_objective(kc_ctx *c, const View &v, const int64_t *centers, int S, int Kc,
+                           double alpha_cut, double *val, int64_t *arg);
+
+// Per-attribute min/max of the data; *nonfinite set if any NaN/Inf.
+kc_status launch_root_box(kc_ctx *c, void *lo, void *hi, int *nonfinite_dev);
+
+// Attribute-major padded copy from the user's layout.
+kc_status launch_ingest(kc_ctx *c, const void *src, kc_layout layout, int64_t N, int D);
+
+// Cluster assignment + bounds tightening (see kc.h).
+kc_status launch_tighten(kc_ctx *c, const void *lo, const void *hi, int B, double alpha,
+                         const int64_t *seeds_dev, int ball_cap, void *lo_out, void *hi_out,
+                         int64_t *counts, int64_t *cand, double *lb, int8_t *status);
+
+// Sample reduction against M nodes; updates the device mask.
+kc_status launch_sample_reduction(kc_ctx *c, const void *lo, const void *hi, int M,
+                                  const int64_t *reps, int R, double beta_glob, double alpha,
+                                  uint8_t *mask, unsigned long long *n_active_dev);
+
+}  // namespace kc

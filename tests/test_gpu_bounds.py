@@ -1,0 +1,165 @@
+"""Parity of the CUDA bound kernels with the CPU oracle (Section 3.1 lower
+bound, Section 3.2 upper bound, Algorithm 2 FFT, Section 2.1 root box).
+
+Tolerances: double data -- the raw lower bound and the objective are
+bit-identical to the oracle (same operation order); float data -- the
+certified lower bound lies in [beta * (1 - 1e-6), beta] of the oracle's FP64
+value beta, and the objective (re-evaluated in double) is bit-identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2301_00061_gb300 import KCenter, KCError  # noqa: E402
+
+DEV = torch.device("cuda:0")
+REL = 1e-6
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _mix(n, d, k, seed, dtype=np.float32):
+    return synth.gaussian_mixture(n, d, (1 / k,) * k, (0.5,) * k, (2.0,) * k, 20.0, seed, dtype=dtype)
+
+
+def _check_lb_f32(X, lo, hi, lb, raw, arg):
+    ref, refarg = oracle.lower_bounds(X, lo, hi)
+    assert np.all(lb <= ref), np.max(lb - ref)
+    assert np.all(lb >= ref * (1 - REL)), np.min(lb / np.maximum(ref, 1e-300))
+    assert np.all(np.abs(raw - ref) <= 4.2e-7 * ref + 1e-38)
+    # the GPU argmax is decided in float: its FP64 value must be the maximum
+    # within the float error, and equal the oracle's argmax when unique
+    for b in range(lo.shape[0]):
+        bs = oracle.beta_matrix(X[arg[b]:arg[b] + 1], lo[b], hi[b]).min()
+        assert bs >= ref[b] * (1 - 1e-6) - 1e-30
+
+
+@pytest.mark.parametrize("d,k", [(2, 3), (2, 4), (3, 3), (4, 3), (8, 5), (5, 2), (1, 1), (13, 7)])
+def test_lower_bounds_f32_ragged(d, k):
+    n = 70_001 + 37 * d
+    X = _mix(n, d, k, seed=d * 10 + k)
+    lo, hi = synth.random_boxes(X, k, 23, seed=k, frac_lo=0.0, frac_hi=0.4)
+    kc = KCenter(_t(X), k)
+    lb, raw, arg = kc.lower_bounds(_t(lo), _t(hi))
+    torch.cuda.synchronize()
+    _check_lb_f32(X, lo, hi, lb.cpu().numpy(), raw.cpu().numpy(), arg.cpu().numpy())
+
+
+@pytest.mark.parametrize("st", [2, 4])
+def test_lower_bounds_f32_nested_microbench_shape(st, monkeypatch):
+    """The microbenchmark's node family (nested boxes, D=8, K=5) at N=200k,
+    for both samples-per-thread variants of the kernel."""
+    monkeypatch.setenv("KC_LB_ST", str(st))
+    X, _ = synth.make_workload("lb_microbench", n=200_003)
+    lo, hi = synth.nested_boxes(X, 5, 256, seed=1)
+    kc = KCenter(_t(X), 5)
+    lb, raw, arg = kc.lower_bounds(_t(lo), _t(hi))
+    torch.cuda.synchronize()
+    sel = np.arange(0, 256, 17)
+    _check_lb_f32(X, lo[sel], hi[sel], lb.cpu().numpy()[sel], raw.cpu().numpy()[sel], arg.cpu().numpy()[sel])
+    ref, _ = oracle.lower_bounds(X, lo[sel], hi[sel])
+    assert np.all(np.diff(ref) >= 0)  # nesting: bounds grow
+
+
+@pytest.mark.parametrize("d,k", [(2, 3), (4, 2), (9, 3)])
+def test_lower_bounds_f64_bit_exact(d, k):
+    X = _mix(5_003, d, k, seed=d, dtype=np.float64)
+    lo, hi = synth.random_boxes(X, k, 29, seed=d, frac_lo=0.0, frac_hi=0.6)
+    kc = KCenter(_t(X), k)
+    lb, raw, arg = kc.lower_bounds(_t(lo), _t(hi))
+    torch.cuda.synchronize()
+    ref, refarg = oracle.lower_bounds(X, lo, hi)
+    assert np.array_equal(raw.cpu().numpy(), ref)
+    assert np.array_equal(arg.cpu().numpy(), refarg)
+    lbn = lb.cpu().numpy()
+    assert np.all(lbn <= ref) and np.all(lbn >= ref * (1 - 1e-14))
+
+
+def test_lower_bound_host_pointers_and_edge_cases():
+    X = _mix(1_000, 3, 3, seed=5)
+    kc = KCenter(X, 3)           # host data
+    lo, hi = synth.random_boxes(X, 3, 5, seed=2)
+    lb, raw, arg = kc.lower_bounds(lo, hi)   # host boxes -> host outputs
+    ref, _ = oracle.lower_bounds(X, lo, hi)
+    assert np.all(lb <= ref) and np.all(lb >= ref * (1 - REL))
+    # degenerate boxes at sample points: LB equals the objective there (Section 5)
+    c = np.array([3, 500, 999])
+    lo2 = np.repeat(X[c][None], 2, 0).copy()
+    lb2, raw2, _ = kc.lower_bounds(lo2, lo2.copy())
+    obj = oracle.objective(X, c)[0]
+    assert np.all(lb2 <= obj) and np.all(lb2 >= obj * (1 - REL))
+    # root box: bound 0, smallest index attains it
+    rlo, rhi = kc.root_box()
+    assert np.array_equal(rlo, X.min(0)) and np.array_equal(rhi, X.max(0))
+    L = np.tile(rlo, (1, 3, 1)).astype(np.float32); H = np.tile(rhi, (1, 3, 1)).astype(np.float32)
+    lb3, raw3, arg3 = kc.lower_bounds(L, H)
+    assert lb3[0] == 0.0 and raw3[0] == 0.0 and arg3[0] == 0
+
+
+def test_lower_bounds_ties_and_duplicates():
+    base = np.array([[0.0, 0.0], [4.0, 0.0], [0.0, 4.0]], np.float32)
+    X = np.concatenate([base, base, base[:1]])      # duplicates: ties at equal distance
+    kc = KCenter(_t(X), 1)
+    lo = np.array([[[1.0, 1.0]]], np.float32); hi = np.array([[[1.0, 1.0]]], np.float32)
+    lb, raw, arg = kc.lower_bounds(_t(lo), _t(hi))
+    # (4,0) and (0,4) both at 9+1 = 10; smallest index is 1
+    assert float(raw[0]) == 10.0 and int(arg[0]) == 1
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("d,k", [(2, 3), (3, 3), (8, 5), (6, 2)])
+def test_upper_bound_bit_exact(dtype, d, k):
+    X = _mix(30_011, d, k, seed=d + k, dtype=dtype)
+    rng = np.random.default_rng(d)
+    C = rng.integers(0, X.shape[0], size=(7, k))
+    kc = KCenter(_t(X), k)
+    ub, worst = kc.upper_bound(_t(C))
+    torch.cuda.synchronize()
+    for s in range(C.shape[0]):
+        v, a = oracle.objective(X, C[s])
+        assert float(ub[s]) == v
+        assert int(worst[s]) == a
+
+
+def test_fft_matches_oracle():
+    for dtype in (np.float32, np.float64):
+        X = _mix(12_345, 3, 4, seed=9, dtype=dtype)
+        kc = KCenter(_t(X), 4)
+        for start in (0, 17, 12_344):
+            c, obj = kc.fft(start, like=_t(X))
+            ref, refobj = oracle.fft(X, 4, start)
+            assert np.array_equal(c.cpu().numpy(), ref)
+            assert float(obj[0]) == refobj
+
+
+def test_nonfinite_data_rejected():
+    X = _mix(100, 2, 2, seed=1)
+    X[50, 1] = np.nan
+    with pytest.raises(KCError) as e:
+        KCenter(_t(X), 2)
+    assert e.value.status == 1
+
+
+def test_full_size_microbench_sampled_nodes():
+    """The benchmark's launch at full size (N=1e7, D=8, K=5, 256 nested boxes):
+    the oracle evaluates a few sampled nodes one by one over all N samples."""
+    X, _ = synth.make_workload("lb_microbench")
+    lo, hi = synth.nested_boxes(X, 5, 256, seed=1)
+    kc = KCenter(_t(X), 5)
+    lb, raw, arg = kc.lower_bounds(_t(lo), _t(hi))
+    torch.cuda.synchronize()
+    lb, raw, arg = lb.cpu().numpy(), raw.cpu().numpy(), arg.cpu().numpy()
+    for b in (0, 101, 255):
+        ref, _ = oracle.lower_bound(X, lo[b], hi[b])
+        assert lb[b] <= ref and lb[b] >= ref * (1 - REL)
+    assert np.all(np.diff(raw) >= 0)
