@@ -367,8 +367,11 @@ static int build_reps(int64_t seed_k, const int64_t *amin_idx, const int64_t *am
  *   plus the samples assigned to k.
  * Box-based BT (Section 4.1.2): M'^k = M^k cap [max_j x_j - r, min_j x_j + r]
  *   over j in J_A^k, r = sqrt(alpha) rounded up, bounds rounded outward.
- * Step B (Algorithm 3, sample-based, when every J_A^k is non-empty): an
- *   unassigned sample is excluded from k when some representative j of k has
+ *   With seeds, a node whose box k is farther than alpha from seed k holds
+ *   no such solution either (infeasible).
+ * Step B (Algorithm 3, sample-based, when every J_A^k is non-empty): every
+ *   active sample (the sample-based loop of Algorithm 3 has no "unassigned"
+ *   guard) is excluded from k when some representative j of k has
  *   ||x_s - x_j||^2 > 4 alpha (Lemma 2); exactly one cluster left assigns it
  *   (J_B), none left makes the node infeasible.
  * Ball-based BT and "centers on samples" (Algorithm 4): S_+^k = active
@@ -415,7 +418,12 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
         if (left == 1) asg[s] = (int8_t)kk;
     }
     if (seeds)
-        for (int k = 0; k < K; ++k) asg[seeds[k]] = (int8_t)k; /* seeds are assigned in every node */
+        for (int k = 0; k < K; ++k) {
+            /* seeds are assigned in every node; a node whose box k is farther
+             * than alpha from seed k cannot hold a solution of value <= alpha */
+            if (kco_beta_sk(X + seeds[k] * D, lo + k * D, hi + k * D, D) > alpha) infeasible = 1;
+            asg[seeds[k]] = (int8_t)k;
+        }
     for (int64_t s = 0; s < N; ++s) {
         int k = asg[s];
         if (k < 0) continue;
@@ -469,7 +477,7 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
     for (int64_t s = 0; s < N; ++s) {
         if (!is_active(active, s)) continue;
         const double *x = X + s * D;
-        if (all_have && asg[s] < 0) {
+        if (all_have) {
             int left = 0, kk = -1;
             for (int k = 0; k < K; ++k) {
                 int excl = 0;

@@ -11,8 +11,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def kcpkg():
-    from paper_2301_00061_gb300 import build as kbuild
-    kbuild.build()
+    import __graft_entry__
+    __graft_entry__._builder().build()
     import paper_2301_00061_gb300 as pkg
     return pkg
 
