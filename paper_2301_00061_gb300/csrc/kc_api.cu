@@ -89,71 +89,6 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Staging of one call's array arguments.  Inputs in host memory are copied to
-// device scratch; outputs in host memory are written to device scratch and
-// copied back by finish().
-struct Stager {
-    kc_ctx *c;
-    struct Item {
-        const void *user;
-        size_t bytes;
-        size_t off;
-        bool in;
-        bool host;
-    };
-    std::vector<Item> items;
-    size_t total = 0;
-    explicit Stager(kc_ctx *cc) : c(cc) {}
-
-    // Registers an argument; returns its index.
-    int add(const void *user, size_t bytes, bool in)
-    {
-        Item it{user, bytes, 0, in, user != nullptr && !is_device_ptr(user)};
-        if (it.host) {
-            it.off = total;
-            total += (bytes + 255) & ~(size_t)255;
-        }
-        items.push_back(it);
-        return (int)items.size() - 1;
-    }
-    // Allocates scratch and copies host inputs; then dev(i) is valid.
-    kc_status begin()
-    {
-        if (total == 0) return KC_OK;
-        KC_TRY(ensure(c, c->stage_in, total));
-        for (auto &it : items)
-            if (it.host && it.in && it.bytes)
-                KC_CUDA(c, cudaMemcpyAsync(static_cast<char *>(c->stage_in.p) + it.off, it.user, it.bytes,
-                                           cudaMemcpyHostToDevice, c->stream));
-        return KC_OK;
-    }
-    void *dev(int i) const
-    {
-        const Item &it = items[i];
-        if (!it.user) return nullptr;
-        return it.host ? static_cast<char *>(c->stage_in.p) + it.off : const_cast<void *>(it.user);
-    }
-    bool any_host_out() const
-    {
-        for (auto &it : items)
-            if (it.host && !it.in) return true;
-        return false;
-    }
-    // Copies host outputs back and waits when any output is in host memory.
-    kc_status finish()
-    {
-        bool wait = false;
-        for (auto &it : items)
-            if (it.host && !it.in && it.bytes) {
-                KC_CUDA(c, cudaMemcpyAsync(const_cast<void *>(it.user), static_cast<char *>(c->stage_in.p) + it.off,
-                                           it.bytes, cudaMemcpyDeviceToHost, c->stream));
-                wait = true;
-            }
-        if (wait) KC_CUDA(c, cudaStreamSynchronize(c->stream));
-        return KC_OK;
-    }
-};
-
 }  // namespace kc
 
 using namespace kc;

@@ -138,4 +138,118 @@ kc_status launch_root_box(kc_ctx *c, void *lo, void *hi, int *nonfinite_dev)
     return after_launch(c, "root box decode");
 }
 
+// ------------------------------------------------------------ compaction
+// Stable stream compaction of the samples a mask keeps: per-block counts,
+// one exclusive scan, then a scatter that preserves sample order (so
+// positions stay ordered like sample indices).
+
+namespace {
+
+constexpr int kCompPer = 16;                       // samples per thread
+constexpr int kCompBlock = 256 * kCompPer;         // samples per block
+
+__global__ void comp_count(const uint8_t *__restrict__ mask, int64_t n, unsigned *__restrict__ counts)
+{
+    const int64_t b0 = (int64_t)blockIdx.x * kCompBlock;
+    unsigned c = 0;
+    for (int i = threadIdx.x; i < kCompBlock; i += 256) {
+        const int64_t s = b0 + i;
+        if (s < n && mask[s]) ++c;
+    }
+    __shared__ unsigned red[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of nb counts by one block of 1024 threads; total -> *total.
+__global__ void comp_scan(unsigned *__restrict__ counts, int64_t nb, unsigned long long *__restrict__ total)
+{
+    __shared__ unsigned long long part[1024];
+    const int64_t per = (nb + 1023) / 1024;
+    const int64_t s0 = threadIdx.x * per, s1 = (s0 + per < nb) ? s0 + per : nb;
+    unsigned long long acc = 0;
+    for (int64_t i = s0; i < s1; ++i) acc += counts[i];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const unsigned long long v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    unsigned long long run = part[threadIdx.x];
+    for (int64_t i = s0; i < s1; ++i) {
+        const unsigned v = counts[i];
+        counts[i] = (unsigned)run;
+        run += v;
+    }
+}
+
+template <typename T>
+__global__ void comp_scatter(const T *__restrict__ X, int64_t ld, int64_t n, int D, const uint32_t *__restrict__ ids,
+                             const uint8_t *__restrict__ mask, const unsigned *__restrict__ offs, T *__restrict__ Xo,
+                             int64_t ldo, uint32_t *__restrict__ ido)
+{
+    __shared__ unsigned wsum[8];
+    const int64_t b0 = (int64_t)blockIdx.x * kCompBlock;
+    unsigned base = offs[blockIdx.x];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int r = 0; r < kCompPer; ++r) {
+        const int64_t s = b0 + (int64_t)r * 256 + threadIdx.x;
+        const bool keep = s < n && mask[s];
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wsum[w] = __popc(bal);
+        __syncthreads();
+        unsigned before = 0, tot = 0;
+        for (int q = 0; q < 8; ++q) {
+            if (q < w) before += wsum[q];
+            tot += wsum[q];
+        }
+        if (keep) {
+            const unsigned p = base + before + __popc(bal & ((1u << lane) - 1u));
+            for (int a = 0; a < D; ++a) Xo[(size_t)a * ldo + p] = X[(size_t)a * ld + s];
+            ido[p] = ids ? ids[s] : (uint32_t)s;
+        }
+        base += tot;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+kc_status launch_compact(kc_ctx *c, const View &v, const uint8_t *mask, void *Xo, int64_t ldo, uint32_t *ido,
+                         unsigned *scratch_counts, unsigned long long *total_dev)
+{
+    const int64_t nb = (v.n + kCompBlock - 1) / kCompBlock;
+    if (nb == 0) {
+        KC_CUDA(c, cudaMemsetAsync(total_dev, 0, 8, c->stream));
+        return KC_OK;
+    }
+    comp_count<<<(unsigned)nb, 256, 0, c->stream>>>(mask, v.n, scratch_counts);
+    KC_TRY(after_launch(c, "compaction count"));
+    comp_scan<<<1, 1024, 0, c->stream>>>(scratch_counts, nb, total_dev);
+    KC_TRY(after_launch(c, "compaction scan"));
+    if (c->dt == KC_F32)
+        comp_scatter<float><<<(unsigned)nb, 256, 0, c->stream>>>(static_cast<const float *>(v.X), v.ld, v.n, c->D, v.ids,
+                                                                 mask, scratch_counts, static_cast<float *>(Xo), ldo, ido);
+    else
+        comp_scatter<double><<<(unsigned)nb, 256, 0, c->stream>>>(static_cast<const double *>(v.X), v.ld, v.n, c->D,
+                                                                  v.ids, mask, scratch_counts, static_cast<double *>(Xo),
+                                                                  ldo, ido);
+    return after_launch(c, "compaction scatter");
+}
+
+int64_t compact_blocks(int64_t n) { return (n + kCompBlock - 1) / kCompBlock; }
+
 }  // namespace kc

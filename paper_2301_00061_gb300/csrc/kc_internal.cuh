@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <string>
@@ -25,6 +26,15 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Workspace and outputs of one tightening call that later steps reuse.
+struct VisitScratch {
+    DevBuf buf;
+    const int64_t *reps = nullptr;   // [B][K][RM] representative sample ids (-1 unused)
+    const int *nreps = nullptr;      // [B][K]
+    const void *repx = nullptr;      // [B][K][RM][D] their coordinates
+    int RM = 0;
+};
+
 }  // namespace kc
 
 struct kc_ctx {
@@ -43,6 +53,7 @@ struct kc_ctx {
     kc::DevBuf stage_in;         // staged host inputs
     kc::DevBuf stage_out;        // device-side outputs destined for host
     kc::DevBuf work;             // per-call work arrays
+    kc::VisitScratch vs;         // tightening workspace
     void *pinned = nullptr;      // pinned host staging
     size_t pinned_bytes = 0;
     int64_t launches = 0;
@@ -158,14 +169,92 @@ kc_status launch_root_box(kc_ctx *c, void *lo, void *hi, int *nonfinite_dev);
 // Attribute-major padded copy from the user's layout.
 kc_status launch_ingest(kc_ctx *c, const void *src, kc_layout layout, int64_t N, int D);
 
-// Cluster assignment + bounds tightening (see kc.h).
-kc_status launch_tighten(kc_ctx *c, const void *lo, const void *hi, int B, double alpha,
-                         const int64_t *seeds_dev, int ball_cap, void *lo_out, void *hi_out,
-                         int64_t *counts, int64_t *cand, double *lb, int8_t *status);
+// Cluster assignment + bounds tightening of B nodes over a sample view (see kc.h).
+kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int B, double alpha,
+                              const int64_t *seeds_dev, int ball_cap, void *lo_out, void *hi_out, int64_t *counts,
+                              int64_t *cand, double *lb, double *lb_raw, int64_t *lbarg, int8_t *status,
+                              VisitScratch *vs);
 
-// Sample reduction against M nodes; updates the device mask.
-kc_status launch_sample_reduction(kc_ctx *c, const void *lo, const void *hi, int M,
-                                  const int64_t *reps, int R, double beta_glob, double alpha,
-                                  uint8_t *mask, unsigned long long *n_active_dev);
+// Sample reduction (Algorithm 5) of the samples of a view against M nodes
+// with representative coordinates repx [M][K][R][D] (nreps [M][K]).
+kc_status launch_sample_reduction_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int M,
+                                       const void *repx, const int *nreps, int R, double beta_glob, double alpha,
+                                       uint8_t *mask, unsigned long long *n_active);
+
+// Coordinates of representative ids [M][K][R] (-1 = unused) -> repx, nreps.
+kc_status launch_gather_reps(kc_ctx *c, int M, int R, const int64_t *reps, void *repx, int *nreps);
+
+// Stable compaction of the view's samples with mask[pos] != 0 into Xo [D][ldo]
+// and ids ido; the kept count lands in *total_dev.  scratch_counts needs
+// compact_blocks(v.n) entries.
+kc_status launch_compact(kc_ctx *c, const View &v, const uint8_t *mask, void *Xo, int64_t ldo, uint32_t *ido,
+                         unsigned *scratch_counts, unsigned long long *total_dev);
+int64_t compact_blocks(int64_t n);
+
+// Staging of one call's array arguments.  Inputs in host memory are copied to
+// device scratch; outputs in host memory are written to device scratch and
+// copied back by finish().
+struct Stager {
+    kc_ctx *c;
+    struct Item {
+        const void *user;
+        size_t bytes;
+        size_t off;
+        bool in;
+        bool host;
+    };
+    std::vector<Item> items;
+    size_t total = 0;
+    explicit Stager(kc_ctx *cc) : c(cc) {}
+
+    // Registers an argument; returns its index.
+    int add(const void *user, size_t bytes, bool in)
+    {
+        Item it{user, bytes, 0, in, user != nullptr && !is_device_ptr(user)};
+        if (it.host) {
+            it.off = total;
+            total += (bytes + 255) & ~(size_t)255;
+        }
+        items.push_back(it);
+        return (int)items.size() - 1;
+    }
+    // Allocates scratch and copies host inputs; then dev(i) is valid.
+    kc_status begin()
+    {
+        if (total == 0) return KC_OK;
+        KC_TRY(ensure(c, c->stage_in, total));
+        for (auto &it : items)
+            if (it.host && it.in && it.bytes)
+                KC_CUDA(c, cudaMemcpyAsync(static_cast<char *>(c->stage_in.p) + it.off, it.user, it.bytes,
+                                           cudaMemcpyHostToDevice, c->stream));
+        return KC_OK;
+    }
+    void *dev(int i) const
+    {
+        const Item &it = items[i];
+        if (!it.user) return nullptr;
+        return it.host ? static_cast<char *>(c->stage_in.p) + it.off : const_cast<void *>(it.user);
+    }
+    bool any_host_out() const
+    {
+        for (auto &it : items)
+            if (it.host && !it.in) return true;
+        return false;
+    }
+    // Copies host outputs back and waits when any output is in host memory.
+    kc_status finish()
+    {
+        bool wait = false;
+        for (auto &it : items)
+            if (it.host && !it.in && it.bytes) {
+                KC_CUDA(c, cudaMemcpyAsync(const_cast<void *>(it.user), static_cast<char *>(c->stage_in.p) + it.off,
+                                           it.bytes, cudaMemcpyDeviceToHost, c->stream));
+                wait = true;
+            }
+        if (wait) KC_CUDA(c, cudaStreamSynchronize(c->stream));
+        return KC_OK;
+    }
+};
+
 
 }  // namespace kc

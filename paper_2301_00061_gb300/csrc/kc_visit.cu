@@ -1,0 +1,1001 @@
+// kc_visit.cu -- cluster assignment and bounds tightening of a batch of nodes
+// (Section 4.1, Algorithms 3 and 4) and sample reduction (Section 4.2,
+// Algorithm 5).
+//
+// Layout of the work: each CTA stages a tile of samples in shared memory;
+// each warp takes one node at a time and sweeps the whole tile with per-lane
+// register accumulators, then reduces them across the warp once per (node,
+// tile) and merges them into global accumulators with atomics.  Extremes that
+// must also name a sample (the representatives) are (value, position) keys:
+// packed into 64 bits for float data, two 64-bit words merged by a 128-bit
+// compare-and-swap for double data.
+//
+// Float data take every exclusion only where the float evaluation proves it:
+// a distance d evaluated as d' satisfies d' (1 - g) <= d <= d' / (1 - g), so
+//   d > t is proved by  RD(d' * (1 - g)) - slack > RU(t),
+// and a sample is kept in a ball unless the same test proves it is outside.
+// Double data decide exactly as a serial double evaluation.
+#include <cuda_runtime.h>
+
+#include "kc_device.cuh"
+#include "kc_internal.cuh"
+
+namespace kc {
+
+namespace {
+
+constexpr int NWV = kThreads / 32;
+
+// ------------------------------------------------------------------- keys
+
+template <typename T>
+struct Key;
+
+template <>
+struct Key<float> {
+    using K = unsigned long long;
+    __device__ static K none() { return 0ull; }
+    __device__ static K max_of(float v, uint32_t p) { return ((K)ord_f32(v) << 32) | (K)(0xFFFFFFFFu - p); }
+    __device__ static K min_of(float v, uint32_t p) { return ((K)(~ord_f32(v)) << 32) | (K)(0xFFFFFFFFu - p); }
+    __device__ static bool gt(const K &a, const K &b) { return a > b; }
+    __device__ static bool is_none(const K &a) { return a == 0ull; }
+    __device__ static K shfl(const K &a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+    __device__ static float vmax(const K &k) { return unord_f32((uint32_t)(k >> 32)); }
+    __device__ static float vmin(const K &k) { return unord_f32(~(uint32_t)(k >> 32)); }
+    __device__ static uint32_t pos(const K &k) { return 0xFFFFFFFFu - (uint32_t)k; }
+    __device__ static void atomic_max(K *p, const K &v, unsigned *) { atomicMax(p, v); }
+};
+
+struct K128 {
+    unsigned long long hi, lo;
+};
+
+__device__ __forceinline__ K128 cas128(K128 *p, K128 cmp, K128 val)
+{
+    K128 old;
+    asm volatile(
+        "{ .reg .b128 c, v, o; mov.b128 c, {%2, %3}; mov.b128 v, {%4, %5};"
+        " atom.global.cas.b128 o, [%6], c, v; mov.b128 {%0, %1}, o; }"
+        : "=l"(old.lo), "=l"(old.hi)
+        : "l"(cmp.lo), "l"(cmp.hi), "l"(val.lo), "l"(val.hi), "l"(p)
+        : "memory");
+    return old;
+}
+
+template <>
+struct Key<double> {
+    using K = K128;
+    __device__ static K none() { return K{0ull, 0ull}; }
+    __device__ static K max_of(double v, uint32_t p) { return K{ord_f64(v), 0xFFFFFFFFull - p}; }
+    __device__ static K min_of(double v, uint32_t p) { return K{~ord_f64(v), 0xFFFFFFFFull - p}; }
+    __device__ static bool gt(const K &a, const K &b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+    __device__ static bool is_none(const K &a) { return a.hi == 0ull && a.lo == 0ull; }
+    __device__ static K shfl(const K &a, int o)
+    {
+        return K{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+    }
+    __device__ static double vmax(const K &k) { return unord_f64(k.hi); }
+    __device__ static double vmin(const K &k) { return unord_f64(~k.hi); }
+    __device__ static uint32_t pos(const K &k) { return (uint32_t)(0xFFFFFFFFull - k.lo); }
+    // Lock-free max; every failed exchange means another update succeeded, so
+    // the loop ends; the iteration cap only guards against a broken invariant.
+    __device__ static void atomic_max(K *p, const K &v, unsigned *err)
+    {
+        K cur = none();
+        for (int it = 0; it < (1 << 20); ++it) {
+            if (!gt(v, cur)) return;
+            const K old = cas128(p, cur, v);
+            if (old.hi == cur.hi && old.lo == cur.lo) return;
+            cur = old;
+        }
+        atomicOr(err, 2u);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ typename Key<T>::K kmax(const typename Key<T>::K &a, const typename Key<T>::K &b)
+{
+    return Key<T>::gt(a, b) ? a : b;
+}
+
+template <typename T>
+__device__ __forceinline__ typename Key<T>::K warp_kmax(typename Key<T>::K v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = kmax<T>(v, Key<T>::shfl(v, o));
+    return v;
+}
+
+// ordered-integer min/max of values (no position)
+__device__ __forceinline__ void atomic_max_val(unsigned *p, float v) { atomicMax(p, ord_f32(v)); }
+__device__ __forceinline__ void atomic_min_val(unsigned *p, float v) { atomicMin(p, ord_f32(v)); }
+__device__ __forceinline__ void atomic_max_val(unsigned long long *p, double v) { atomicMax(p, ord_f64(v)); }
+__device__ __forceinline__ void atomic_min_val(unsigned long long *p, double v) { atomicMin(p, ord_f64(v)); }
+template <typename T>
+using OrdT = typename std::conditional<sizeof(T) == 4, unsigned, unsigned long long>::type;
+__device__ __forceinline__ float from_ord(unsigned u) { return unord_f32(u); }
+__device__ __forceinline__ double from_ord(unsigned long long u) { return unord_f64(u); }
+
+// ---------------------------------------------------- distance primitives
+
+// Float clamp distance with padded compile-time DM (pairs beyond D add 0).
+template <int DM>
+__device__ __forceinline__ float box_dist_pad(const uint64_t *px, const uint64_t *bx)
+{
+    return box_dist_f32<DM>(px, bx);
+}
+
+// Double clamp distance in attribute order (the serial evaluation).
+template <int DM>
+__device__ __forceinline__ double box_dist_f64(const double *x, const double *lo, const double *hi, int D)
+{
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+        if (a < D) {
+            const double mu = mid3d(lo[a], x[a], hi[a]);
+            const double d = __dsub_rn(x[a], mu);
+            acc = __dadd_rn(acc, __dmul_rn(d, d));
+        }
+    return acc;
+}
+
+template <int DM>
+__device__ __forceinline__ double pt_dist_f64(const double *x, const double *c, int D)
+{
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+        if (a < D) {
+            const double d = __dsub_rn(x[a], c[a]);
+            acc = __dadd_rn(acc, __dmul_rn(d, d));
+        }
+    return acc;
+}
+
+// Farthest-corner distance (Eq. 13) for one box, float: per attribute
+// max(|lo - x|, |x - hi|), squared and summed in the same two chains.
+template <int DM>
+__device__ __forceinline__ float corner_dist_f32(const uint64_t *px, const uint64_t *bx)
+{
+    uint64_t acc = 0;
+#pragma unroll
+    for (int a = 0; a + 1 < DM; a += 2) {
+        const float2 t0 = upk(sub2(bx[a], px[a]));
+        const float2 t1 = upk(sub2(bx[a + 1], px[a + 1]));
+        const uint64_t m = pk(fmaxf(fabsf(t0.x), fabsf(t0.y)), fmaxf(fabsf(t1.x), fabsf(t1.y)));
+        acc = fma2(m, m, acc);
+    }
+    float2 s = upk(acc);
+    if (DM & 1) {
+        const float2 t = upk(sub2(bx[DM - 1], px[DM - 1]));
+        const float m = fmaxf(fabsf(t.x), fabsf(t.y));
+        s.x = fmaf(m, m, s.x);
+    }
+    return s.x + s.y;
+}
+
+template <int DM>
+__device__ __forceinline__ double corner_dist_f64(const double *x, const double *lo, const double *hi, int D)
+{
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+        if (a < D) {
+            const double mu = (fabs(__dsub_rn(lo[a], x[a])) > fabs(__dsub_rn(hi[a], x[a]))) ? lo[a] : hi[a];
+            const double d = __dsub_rn(x[a], mu);
+            acc = __dadd_rn(acc, __dmul_rn(d, d));
+        }
+    return acc;
+}
+
+// Proof helpers for float evaluations (see the file comment).
+__device__ __forceinline__ bool proved_gt(float dhat, float defl, float slack, float t_up)
+{
+    return __fsub_rd(__fmul_rd(dhat, defl), slack) > t_up;
+}
+__device__ __forceinline__ bool proved_lt(float dhat, float infl, float slack, float t_dn)
+{
+    return __fadd_ru(__fmul_ru(dhat, infl), slack) < t_dn;
+}
+
+struct Margins {
+    float defl, infl, slack;     // float evaluation of a D-term distance
+    float alpha_up, four_up;     // alpha and 4 alpha rounded up to float
+    float beta_dn;               // beta_glob rounded down to float
+};
+
+// ------------------------------------------------------------ pass A
+
+template <typename T, int KM, int DM>
+__global__ void __launch_bounds__(kThreads)
+visit_a_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, const T *__restrict__ lo,
+               const T *__restrict__ hi, int B, int K, int D, double alpha, Margins mg,
+               typename Key<T>::K *__restrict__ lbkey, typename Key<T>::K *__restrict__ amax,
+               typename Key<T>::K *__restrict__ amin, unsigned *__restrict__ flags)
+{
+    using KT = Key<T>;
+    using KY = typename KT::K;
+    constexpr bool F32 = sizeof(T) == 4;
+    extern __shared__ __align__(16) unsigned char smem[];
+    // float: (x, -x) pairs [D][tile]; double: x [D][tile]
+    uint64_t *tp = reinterpret_cast<uint64_t *>(smem);
+    double *td = reinterpret_cast<double *>(smem);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
+        const int tn = (int)((n - base) < (int64_t)tile ? (n - base) : (int64_t)tile);
+        __syncthreads();
+        for (int i = threadIdx.x; i < D * tile; i += kThreads) {
+            const int a = i / tile, j = i - a * tile;
+            const T v = j < tn ? X[(size_t)a * ld + base + j] : T(0);
+            if constexpr (F32) tp[i] = pk(v, -v);
+            else td[i] = v;
+        }
+        __syncthreads();
+        for (int b = warp; b < B; b += NWV) {
+            // node boxes into registers
+            uint64_t bx[KM][DM];
+            double blo[KM][DM], bhi[KM][DM];
+#pragma unroll
+            for (int k = 0; k < KM; ++k)
+#pragma unroll
+                for (int a = 0; a < DM; ++a) {
+                    const bool in = k < K && a < D;
+                    const size_t o = ((size_t)b * K + k) * D + a;
+                    if constexpr (F32) {
+                        bx[k][a] = in ? pk((float)lo[o], -(float)hi[o]) : pk(0.f, -0.f);
+                    } else {
+                        blo[k][a] = in ? (double)lo[o] : 0.0;
+                        bhi[k][a] = in ? (double)hi[o] : 0.0;
+                    }
+                }
+            KY acc_lb = KT::none();
+            KY acc_max[KM][DM], acc_min[KM][DM];
+#pragma unroll
+            for (int k = 0; k < KM; ++k)
+#pragma unroll
+                for (int a = 0; a < DM; ++a) { acc_max[k][a] = KT::none(); acc_min[k][a] = KT::none(); }
+            bool infeasible = false;
+            for (int j = lane; j < tn; j += 32) {
+                const uint32_t pos = (uint32_t)(base + j);
+                T x[DM];
+                uint64_t px[DM];
+#pragma unroll
+                for (int a = 0; a < DM; ++a) {
+                    if constexpr (F32) {
+                        px[a] = a < D ? tp[(size_t)a * tile + j] : pk(0.f, -0.f);
+                        x[a] = upk(px[a]).x;
+                    } else {
+                        x[a] = a < D ? td[(size_t)a * tile + j] : 0.0;
+                    }
+                }
+                T bmin = T(0);
+                int left = 0, k1 = -1;
+#pragma unroll
+                for (int k = 0; k < KM; ++k) {
+                    if (k < K) {
+                        T v;
+                        bool excl;
+                        if constexpr (F32) {
+                            v = box_dist_pad<DM>(px, bx[k]);
+                            excl = proved_gt(v, mg.defl, mg.slack, mg.alpha_up);
+                        } else {
+                            v = box_dist_f64<DM>(reinterpret_cast<const double *>(x), blo[k], bhi[k], D);
+                            excl = v > alpha;
+                        }
+                        bmin = (k == 0 || v < bmin) ? v : bmin;
+                        if (!excl) { ++left; k1 = k; }
+                    }
+                }
+                acc_lb = kmax<T>(acc_lb, KT::max_of(bmin, pos));
+                if (left == 0) infeasible = true;
+                if (left == 1) {
+#pragma unroll
+                    for (int k = 0; k < KM; ++k)
+                        if (k == k1) {
+#pragma unroll
+                            for (int a = 0; a < DM; ++a)
+                                if (a < D) {
+                                    acc_max[k][a] = kmax<T>(acc_max[k][a], KT::max_of(x[a], pos));
+                                    acc_min[k][a] = kmax<T>(acc_min[k][a], KT::min_of(x[a], pos));
+                                }
+                        }
+                }
+            }
+            // warp reduction, then one atomic per accumulator and warp
+            acc_lb = warp_kmax<T>(acc_lb);
+            if (lane == 0 && !KT::is_none(acc_lb)) KT::atomic_max(&lbkey[b], acc_lb, &flags[b]);
+#pragma unroll
+            for (int k = 0; k < KM; ++k)
+#pragma unroll
+                for (int a = 0; a < DM; ++a)
+                    if (k < K && a < D) {
+                        const KY m1 = warp_kmax<T>(acc_max[k][a]);
+                        const KY m2 = warp_kmax<T>(acc_min[k][a]);
+                        const size_t o = ((size_t)b * K + k) * D + a;
+                        if (lane == 0 && !KT::is_none(m1)) KT::atomic_max(&amax[o], m1, &flags[b]);
+                        if (lane == 0 && !KT::is_none(m2)) KT::atomic_max(&amin[o], m2, &flags[b]);
+                    }
+            if (__any_sync(0xffffffffu, infeasible) && lane == 0) atomicOr(&flags[b], 1u);
+        }
+    }
+}
+
+// ------------------------------------------------------- finalize pass A
+
+template <typename T>
+__device__ __forceinline__ T round_dn(double v)
+{
+    if constexpr (sizeof(T) == 4) return __double2float_rd(v);
+    else return v;
+}
+template <typename T>
+__device__ __forceinline__ T round_up(double v)
+{
+    if constexpr (sizeof(T) == 4) return __double2float_ru(v);
+    else return v;
+}
+
+struct FinA {
+    const int64_t *seeds;       // [K] original ids or null
+    const uint32_t *ids;        // view position -> id, or null
+    double r_up;                // sqrt(alpha) rounded up
+    double alpha;
+    double defl, slack;         // certified lower-bound deflation
+    double seed_defl;           // float data: deflation of the seed test (1 for double)
+    int cap, RM;
+};
+
+template <typename T>
+__global__ void finalize_a_kernel(int B, int K, int D, const T *__restrict__ lo, const T *__restrict__ hi,
+                                  const typename Key<T>::K *__restrict__ lbkey,
+                                  const typename Key<T>::K *__restrict__ amax,
+                                  const typename Key<T>::K *__restrict__ amin, unsigned *__restrict__ flags,
+                                  const T *__restrict__ Xf, int64_t ldf, FinA f, T *__restrict__ blo,
+                                  T *__restrict__ bhi, int64_t *__restrict__ reps, int *__restrict__ nreps,
+                                  T *__restrict__ repx, int *__restrict__ allhave, double *__restrict__ lb,
+                                  double *__restrict__ lb_raw, int64_t *__restrict__ lbarg)
+{
+    using KT = Key<T>;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    bool inf = (flags[b] & 1u) != 0;
+    // lower bound of the input box
+    {
+        const auto k = lbkey[b];
+        const bool none = KT::is_none(k);
+        const double raw = none ? 0.0 : (double)KT::vmax(k);
+        if (lb_raw) lb_raw[b] = raw;
+        if (lb) lb[b] = fmax(0.0, __dsub_rd(__dmul_rd(raw, f.defl), f.slack));
+        if (lbarg) {
+            const int64_t p = none ? -1 : (int64_t)KT::pos(k);
+            lbarg[b] = (p < 0 || !f.ids) ? p : (int64_t)f.ids[p];
+        }
+    }
+    int have = 1;
+    for (int k = 0; k < K; ++k) {
+        const size_t o0 = ((size_t)b * K + k) * D;
+        int64_t seed = f.seeds ? f.seeds[k] : -1;
+        if (seed >= 0) {
+            // seed consistency: box k farther than alpha from seed k
+            double acc = 0.0;
+            for (int a = 0; a < D; ++a) {
+                const double x = (double)Xf[(size_t)a * ldf + seed];
+                const double mu = mid3d((double)lo[o0 + a], x, (double)hi[o0 + a]);
+                const double d = __dsub_rn(x, mu);
+                acc = __dadd_rn(acc, __dmul_rn(d, d));
+            }
+            if (__dmul_rd(acc, f.seed_defl) > f.alpha) inf = true;
+        }
+        bool nonempty = seed >= 0;
+        int64_t amin_id[kMaxD], amax_id[kMaxD];
+        for (int a = 0; a < D; ++a) {
+            const size_t o = o0 + a;
+            double vmx = 0, vmn = 0;
+            int64_t imx = -1, imn = -1;
+            if (!KT::is_none(amax[o])) {
+                vmx = (double)KT::vmax(amax[o]);
+                const int64_t p = KT::pos(amax[o]);
+                imx = f.ids ? (int64_t)f.ids[p] : p;
+                vmn = (double)KT::vmin(amin[o]);
+                const int64_t q = KT::pos(amin[o]);
+                imn = f.ids ? (int64_t)f.ids[q] : q;
+                nonempty = true;
+            }
+            if (seed >= 0) {
+                const double sx = (double)Xf[(size_t)a * ldf + seed];
+                if (imx < 0 || sx > vmx || (sx == vmx && seed < imx)) { vmx = sx; imx = seed; }
+                if (imn < 0 || sx < vmn || (sx == vmn && seed < imn)) { vmn = sx; imn = seed; }
+            }
+            amin_id[a] = imn;
+            amax_id[a] = imx;
+            T l = lo[o], h = hi[o];
+            if (imx >= 0) {
+                const T l2 = round_dn<T>(nextafter(__dsub_rn(vmx, f.r_up), -__builtin_huge_val()));
+                const T h2 = round_up<T>(nextafter(__dadd_rn(vmn, f.r_up), __builtin_huge_val()));
+                if (l2 > l) l = l2;
+                if (h2 < h) h = h2;
+            }
+            if (l > h) inf = true;
+            blo[o] = l;
+            bhi[o] = h;
+        }
+        // representatives: seed, then arg-min / arg-max of each attribute
+        int nr = 0;
+        int64_t *rp = reps + ((size_t)b * K + k) * f.RM;
+        auto add = [&](int64_t v) {
+            if (v < 0 || nr >= f.cap) return;
+            for (int q = 0; q < nr; ++q)
+                if (rp[q] == v) return;
+            rp[nr++] = v;
+        };
+        add(seed);
+        if (nonempty)
+            for (int a = 0; a < D; ++a) {
+                add(amin_id[a]);
+                add(amax_id[a]);
+            }
+        for (int q = nr; q < f.RM; ++q) rp[q] = -1;
+        nreps[(size_t)b * K + k] = nr;
+        T *rx = repx + ((size_t)b * K + k) * f.RM * D;
+        for (int q = 0; q < nr; ++q)
+            for (int a = 0; a < D; ++a) rx[(size_t)q * D + a] = Xf[(size_t)a * ldf + rp[q]];
+        if (nr == 0) have = 0;
+    }
+    allhave[b] = have;
+    if (inf) atomicOr(&flags[b], 1u);
+}
+
+// ------------------------------------------------------------ pass B
+
+template <typename T, int KM, int DM, int RMX>
+__global__ void __launch_bounds__(kThreads)
+visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, int K, int D, int RM,
+               const T *__restrict__ blo, const T *__restrict__ bhi, const T *__restrict__ repx,
+               const int *__restrict__ nreps, const int *__restrict__ allhave, double alpha, Margins mg,
+               unsigned long long *__restrict__ cnt, OrdT<T> *__restrict__ smax, OrdT<T> *__restrict__ smin,
+               OrdT<T> *__restrict__ jmax, OrdT<T> *__restrict__ jmin, typename Key<T>::K *__restrict__ cand,
+               unsigned *__restrict__ flags)
+{
+    using KT = Key<T>;
+    using KY = typename KT::K;
+    constexpr bool F32 = sizeof(T) == 4;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *tx = reinterpret_cast<T *>(smem);                       // [D][tile]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double four_alpha = 4.0 * alpha;
+
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
+        const int tn = (int)((n - base) < (int64_t)tile ? (n - base) : (int64_t)tile);
+        __syncthreads();
+        for (int i = threadIdx.x; i < D * tile; i += kThreads) {
+            const int a = i / tile, j = i - a * tile;
+            tx[i] = j < tn ? X[(size_t)a * ld + base + j] : T(0);
+        }
+        __syncthreads();
+        for (int b = warp; b < B; b += NWV) {
+            T l[KM][DM], h[KM][DM], mid[KM][DM];
+            int nr[KM];
+#pragma unroll
+            for (int k = 0; k < KM; ++k) {
+                nr[k] = k < K ? nreps[(size_t)b * K + k] : 0;
+#pragma unroll
+                for (int a = 0; a < DM; ++a) {
+                    const bool in = k < K && a < D;
+                    const size_t o = ((size_t)b * K + k) * D + a;
+                    l[k][a] = in ? blo[o] : T(0);
+                    h[k][a] = in ? bhi[o] : T(0);
+                    if constexpr (F32) mid[k][a] = in ? (float)(0.5 * ((double)l[k][a] + (double)h[k][a])) : 0.f;
+                    else mid[k][a] = in ? 0.5 * (l[k][a] + h[k][a]) : 0.0;
+                }
+            }
+            const bool have = allhave[b] != 0;
+            const T *rxb = repx + (size_t)b * K * RM * D;
+            unsigned long long c_cnt[KM];
+            T c_smax[KM][DM], c_smin[KM][DM], c_jmax[KM][DM], c_jmin[KM][DM];
+            KY c_cand[KM];
+            const T INF = F32 ? (T)__int_as_float(0x7f800000) : (T)__longlong_as_double(0x7ff0000000000000ll);
+#pragma unroll
+            for (int k = 0; k < KM; ++k) {
+                c_cnt[k] = 0;
+                c_cand[k] = KT::none();
+#pragma unroll
+                for (int a = 0; a < DM; ++a) { c_smax[k][a] = -INF; c_smin[k][a] = INF; c_jmax[k][a] = -INF; c_jmin[k][a] = INF; }
+            }
+            bool infeasible = false;
+            for (int j = lane; j < tn; j += 32) {
+                const uint32_t pos = (uint32_t)(base + j);
+                T x[DM];
+#pragma unroll
+                for (int a = 0; a < DM; ++a) x[a] = a < D ? tx[(size_t)a * tile + j] : T(0);
+                uint64_t px[(DM + 1) / 2];
+                if constexpr (F32) {
+#pragma unroll
+                    for (int p = 0; p < (DM + 1) / 2; ++p)
+                        px[p] = pk(x[2 * p], 2 * p + 1 < DM ? x[2 * p + 1] : 0.f);
+                }
+                // distances to every representative; far4: proved > 4 alpha, far1: proved > alpha
+                unsigned long long far4 = 0ull, far1 = 0ull;   // bit k*RMX + r
+#pragma unroll
+                for (int k = 0; k < KM; ++k)
+#pragma unroll
+                    for (int r = 0; r < RMX; ++r)
+                        if (r < nr[k]) {
+                            const T *c = rxb + ((size_t)k * RM + r) * D;
+                            if constexpr (F32) {
+                                uint64_t pc[(DM + 1) / 2];
+#pragma unroll
+                                for (int p = 0; p < (DM + 1) / 2; ++p) {
+                                    const float c0 = 2 * p < D ? c[2 * p] : 0.f;
+                                    const float c1 = 2 * p + 1 < D ? c[2 * p + 1] : 0.f;
+                                    pc[p] = pk(c0, c1);
+                                }
+                                const float d = pt_dist_f32<2 * ((DM + 1) / 2)>(px, pc);
+                                if (proved_gt(d, mg.defl, mg.slack, mg.four_up)) far4 |= 1ull << (k * RMX + r);
+                                if (proved_gt(d, mg.defl, mg.slack, mg.alpha_up)) far1 |= 1ull << (k * RMX + r);
+                            } else {
+                                double cc[DM];
+#pragma unroll
+                                for (int a = 0; a < DM; ++a) cc[a] = a < D ? c[a] : 0.0;
+                                const double d = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), cc, D);
+                                if (d > four_alpha) far4 |= 1ull << (k * RMX + r);
+                                if (d > alpha) far1 |= 1ull << (k * RMX + r);
+                            }
+                        }
+                // sample-based assignment (Algorithm 3, Lemma 2)
+                if (have) {
+                    int left = 0, k1 = -1;
+#pragma unroll
+                    for (int k = 0; k < KM; ++k)
+                        if (k < K) {
+                            const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
+                            if ((far4 & mk) == 0ull) { ++left; k1 = k; }
+                        }
+                    if (left == 0) infeasible = true;
+                    if (left == 1) {
+#pragma unroll
+                        for (int k = 0; k < KM; ++k)
+                            if (k == k1) {
+#pragma unroll
+                                for (int a = 0; a < DM; ++a) {
+                                    c_jmax[k][a] = x[a] > c_jmax[k][a] ? x[a] : c_jmax[k][a];
+                                    c_jmin[k][a] = x[a] < c_jmin[k][a] ? x[a] : c_jmin[k][a];
+                                }
+                            }
+                    }
+                }
+                // ball-based tightening and centers on samples (Algorithm 4)
+#pragma unroll
+                for (int k = 0; k < KM; ++k)
+                    if (k < K) {
+                        bool ok = true;
+#pragma unroll
+                        for (int a = 0; a < DM; ++a)
+                            if (a < D && (x[a] < l[k][a] || x[a] > h[k][a])) ok = false;
+                        const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
+                        if (far1 & mk) ok = false;
+                        if (ok) {
+                            ++c_cnt[k];
+#pragma unroll
+                            for (int a = 0; a < DM; ++a) {
+                                c_smax[k][a] = x[a] > c_smax[k][a] ? x[a] : c_smax[k][a];
+                                c_smin[k][a] = x[a] < c_smin[k][a] ? x[a] : c_smin[k][a];
+                            }
+                            T dm;
+                            if constexpr (F32) {
+                                uint64_t pm[(DM + 1) / 2];
+#pragma unroll
+                                for (int p = 0; p < (DM + 1) / 2; ++p)
+                                    pm[p] = pk(mid[k][2 * p], 2 * p + 1 < DM ? mid[k][2 * p + 1] : 0.f);
+                                dm = pt_dist_f32<2 * ((DM + 1) / 2)>(px, pm);
+                            } else {
+                                dm = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), mid[k], D);
+                            }
+                            c_cand[k] = kmax<T>(c_cand[k], KT::min_of(dm, pos));
+                        }
+                    }
+            }
+            // reduce and merge
+#pragma unroll
+            for (int k = 0; k < KM; ++k)
+                if (k < K) {
+                    unsigned long long cn = c_cnt[k];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(0xffffffffu, cn, o);
+                    const KY cd = warp_kmax<T>(c_cand[k]);
+                    const size_t ok_ = (size_t)b * K + k;
+                    if (lane == 0 && cn) atomicAdd(&cnt[ok_], cn);
+                    if (lane == 0 && !KT::is_none(cd)) KT::atomic_max(&cand[ok_], cd, &flags[b]);
+#pragma unroll
+                    for (int a = 0; a < DM; ++a)
+                        if (a < D) {
+                            T v1 = c_smax[k][a], v2 = c_smin[k][a], v3 = c_jmax[k][a], v4 = c_jmin[k][a];
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) {
+                                v1 = fmax(v1, __shfl_xor_sync(0xffffffffu, v1, o));
+                                v2 = fmin(v2, __shfl_xor_sync(0xffffffffu, v2, o));
+                                v3 = fmax(v3, __shfl_xor_sync(0xffffffffu, v3, o));
+                                v4 = fmin(v4, __shfl_xor_sync(0xffffffffu, v4, o));
+                            }
+                            const size_t o = ok_ * D + a;
+                            if (lane == 0) {
+                                if (v1 != -INF) atomic_max_val(&smax[o], v1);
+                                if (v2 != INF) atomic_min_val(&smin[o], v2);
+                                if (v3 != -INF) atomic_max_val(&jmax[o], v3);
+                                if (v4 != INF) atomic_min_val(&jmin[o], v4);
+                            }
+                        }
+                }
+            if (__any_sync(0xffffffffu, infeasible) && lane == 0) atomicOr(&flags[b], 1u);
+        }
+    }
+}
+
+template <typename T>
+__global__ void finalize_b_kernel(int B, int K, int D, const unsigned long long *__restrict__ cnt,
+                                  const OrdT<T> *__restrict__ smax, const OrdT<T> *__restrict__ smin,
+                                  const OrdT<T> *__restrict__ jmax, const OrdT<T> *__restrict__ jmin,
+                                  const typename Key<T>::K *__restrict__ cand, const unsigned *__restrict__ flags,
+                                  const uint32_t *__restrict__ ids, double r_up, T *__restrict__ lo_out,
+                                  T *__restrict__ hi_out, int64_t *__restrict__ counts, int64_t *__restrict__ cand_out,
+                                  int8_t *__restrict__ status)
+{
+    using KT = Key<T>;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    bool inf = (flags[b] & 1u) != 0;
+    bool leaf = true;
+    const OrdT<T> NONE_MAX = 0, NONE_MIN = (OrdT<T>)~(OrdT<T>)0;
+    for (int k = 0; k < K; ++k) {
+        const size_t ok = (size_t)b * K + k;
+        if (counts) counts[ok] = (int64_t)cnt[ok];
+        if (cnt[ok] == 0) inf = true;
+        if (cand_out) {
+            const auto c = cand[ok];
+            const int64_t p = KT::is_none(c) ? -1 : (int64_t)KT::pos(c);
+            cand_out[ok] = (p < 0 || !ids) ? p : (int64_t)ids[p];
+        }
+        for (int a = 0; a < D; ++a) {
+            const size_t o = ok * D + a;
+            T l, h;
+            if (cnt[ok] == 0) {
+                l = T(1);
+                h = T(0);
+            } else {
+                l = from_ord(smin[o]);
+                h = from_ord(smax[o]);
+            }
+            if (jmax[o] != NONE_MAX && jmin[o] != NONE_MIN) {
+                const double vmx = (double)from_ord(jmax[o]), vmn = (double)from_ord(jmin[o]);
+                const T l2 = round_dn<T>(nextafter(__dsub_rn(vmx, r_up), -__builtin_huge_val()));
+                const T h2 = round_up<T>(nextafter(__dadd_rn(vmn, r_up), __builtin_huge_val()));
+                if (l2 > l) l = l2;
+                if (h2 < h) h = h2;
+            }
+            if (!(l <= h)) inf = true;
+            if (h > l) leaf = false;
+            lo_out[o] = l;
+            hi_out[o] = h;
+        }
+    }
+    status[b] = inf ? 1 : (leaf ? 2 : 0);
+}
+
+// ------------------------------------------------------ sample reduction
+
+template <typename T, int KM, int DM>
+__global__ void __launch_bounds__(kThreads)
+sr_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int M, int K, int D, const T *__restrict__ lo,
+          const T *__restrict__ hi, const T *__restrict__ repx, const int *__restrict__ nreps, int R,
+          double beta_glob, double alpha, Margins mg, uint8_t *__restrict__ mask,
+          unsigned long long *__restrict__ n_active)
+{
+    constexpr bool F32 = sizeof(T) == 4;
+    unsigned long long kept = 0;
+    for (int64_t s = (int64_t)blockIdx.x * kThreads + threadIdx.x; s < n; s += (int64_t)gridDim.x * kThreads) {
+        if (!mask[s]) continue;
+        T x[DM];
+        uint64_t px[DM];
+#pragma unroll
+        for (int a = 0; a < DM; ++a) {
+            x[a] = a < D ? X[(size_t)a * ld + s] : T(0);
+            if constexpr (F32) px[a] = pk(x[a], -x[a]);
+        }
+        bool redundant = true;
+        for (int m = 0; m < M && redundant; ++m) {
+            // redundant for the lower bound: alpha_s(M) < beta_glob (Eq. 13)
+            T as = T(0);
+            for (int k = 0; k < K; ++k) {
+                const size_t o = ((size_t)m * K + k) * D;
+                T v;
+                if constexpr (F32) {
+                    uint64_t bx[DM];
+#pragma unroll
+                    for (int a = 0; a < DM; ++a) bx[a] = a < D ? pk(lo[o + a], -hi[o + a]) : pk(0.f, -0.f);
+                    v = corner_dist_f32<DM>(px, bx);
+                } else {
+                    double l[DM], h[DM];
+#pragma unroll
+                    for (int a = 0; a < DM; ++a) { l[a] = a < D ? lo[o + a] : 0.0; h[a] = a < D ? hi[o + a] : 0.0; }
+                    v = corner_dist_f64<DM>(reinterpret_cast<const double *>(x), l, h, D);
+                }
+                as = (k == 0 || v < as) ? v : as;
+            }
+            bool lb_red;
+            if constexpr (F32) lb_red = proved_lt(as, mg.infl, mg.slack, mg.beta_dn);
+            else lb_red = as < beta_glob;
+            if (!lb_red) { redundant = false; break; }
+            // redundant for the upper bound: x outside M^k, or some representative farther than alpha
+            for (int k = 0; k < K && redundant; ++k) {
+                const size_t o = ((size_t)m * K + k) * D;
+                bool inb = true;
+#pragma unroll
+                for (int a = 0; a < DM; ++a)
+                    if (a < D && (x[a] < lo[o + a] || x[a] > hi[o + a])) inb = false;
+                if (!inb) continue;
+                bool excl = false;
+                const int nr = nreps ? nreps[(size_t)m * K + k] : 0;
+                for (int r = 0; r < nr && !excl; ++r) {
+                    const T *c = repx + (((size_t)m * K + k) * R + r) * D;
+                    if constexpr (F32) {
+                        uint64_t pxx[(DM + 1) / 2], pc[(DM + 1) / 2];
+#pragma unroll
+                        for (int p = 0; p < (DM + 1) / 2; ++p) {
+                            pxx[p] = pk(x[2 * p], 2 * p + 1 < DM ? x[2 * p + 1] : 0.f);
+                            pc[p] = pk(2 * p < D ? c[2 * p] : 0.f, 2 * p + 1 < D ? c[2 * p + 1] : 0.f);
+                        }
+                        const float d = pt_dist_f32<2 * ((DM + 1) / 2)>(pxx, pc);
+                        excl = proved_gt(d, mg.defl, mg.slack, mg.alpha_up);
+                    } else {
+                        double cc[DM];
+#pragma unroll
+                        for (int a = 0; a < DM; ++a) cc[a] = a < D ? c[a] : 0.0;
+                        excl = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), cc, D) > alpha;
+                    }
+                }
+                if (!excl) redundant = false;
+            }
+        }
+        if (redundant) mask[s] = 0;
+        else ++kept;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    if ((threadIdx.x & 31) == 0 && kept) atomicAdd(n_active, kept);
+}
+
+__global__ void gather_reps_kernel(int M, int K, int D, int R, const int64_t *__restrict__ reps,
+                                   const void *__restrict__ Xf, int64_t ldf, int f32, void *__restrict__ repx,
+                                   int *__restrict__ nreps)
+{
+    const int mk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mk >= M * K) return;
+    int nr = 0;
+    for (int r = 0; r < R; ++r) {
+        const int64_t id = reps[(size_t)mk * R + r];
+        if (id < 0) continue;
+        for (int a = 0; a < D; ++a) {
+            const size_t dst = ((size_t)mk * R + nr) * D + a;
+            if (f32) static_cast<float *>(repx)[dst] = static_cast<const float *>(Xf)[(size_t)a * ldf + id];
+            else static_cast<double *>(repx)[dst] = static_cast<const double *>(Xf)[(size_t)a * ldf + id];
+        }
+        ++nr;
+    }
+    nreps[mk] = nr;
+}
+
+// ------------------------------------------------------------ host side
+
+template <typename F>
+kc_status grid_of(kc_ctx *c, F fn, size_t smem, int64_t work, int *grid)
+{
+    if (smem > 48 * 1024)
+        KC_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    KC_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
+    if (per_sm < 1) return set_err(c, KC_EINTERNAL, "tightening kernel does not fit (smem %zu)", smem);
+    int64_t g = (int64_t)per_sm * c->num_sms;
+    if (g > work) g = work;
+    *grid = (int)(g < 1 ? 1 : g);
+    return KC_OK;
+}
+
+Margins make_margins(kc_ctx *c, double alpha, double beta_glob)
+{
+    Margins m{};
+    const double g = gamma_n(f32_roundings(c->D), kU32);
+    m.defl = (float)(1.0 - g);
+    if ((double)m.defl > 1.0 - g) m.defl = nextafterf(m.defl, 0.f);
+    m.infl = (float)(1.0 / (1.0 - g));
+    if ((double)m.infl < 1.0 / (1.0 - g)) m.infl = nextafterf(m.infl, 2.f);
+    m.slack = (float)((c->D + 2) * 1.401298464324817e-45);
+    auto up = [](double v) {
+        float f = (float)v;
+        if ((double)f < v) f = nextafterf(f, __builtin_huge_valf());
+        return f;
+    };
+    auto dn = [](double v) {
+        float f = (float)v;
+        if ((double)f > v) f = nextafterf(f, -__builtin_huge_valf());
+        return f;
+    };
+    m.alpha_up = up(alpha);
+    m.four_up = up(4.0 * alpha);
+    m.beta_dn = dn(beta_glob);
+    return m;
+}
+
+int reps_cap(int D, int cap) { return std::min(cap, std::min(kMaxReps, 2 * D + 1)); }
+
+template <typename T, int KM, int DM, int RMX>
+kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi_, int B, double alpha,
+                       const int64_t *seeds, int cap, void *lo_out_, void *hi_out_, int64_t *counts, int64_t *cand_out,
+                       double *lb, double *lb_raw, int64_t *lbarg, int8_t *status, VisitScratch *vs)
+{
+    using KY = typename Key<T>::K;
+    const int K_ = c->K, D = c->D;
+    const int RM = RMX;
+    const T *lo = static_cast<const T *>(lo_);
+    const T *hi = static_cast<const T *>(hi_);
+    const size_t KD = (size_t)B * K_ * D, BK = (size_t)B * K_;
+    // workspace
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_lbkey = take(B * sizeof(KY)), o_amax = take(KD * sizeof(KY)), o_amin = take(KD * sizeof(KY));
+    const size_t o_flags = take(B * 4), o_blo = take(KD * sizeof(T)), o_bhi = take(KD * sizeof(T));
+    const size_t o_reps = take(BK * RM * 8), o_nreps = take(BK * 4), o_repx = take(BK * RM * D * sizeof(T));
+    const size_t o_have = take(B * 4), o_cnt = take(BK * 8), o_smax = take(KD * sizeof(OrdT<T>));
+    const size_t o_smin = take(KD * sizeof(OrdT<T>)), o_jmax = take(KD * sizeof(OrdT<T>));
+    const size_t o_jmin = take(KD * sizeof(OrdT<T>)), o_cand = take(BK * sizeof(KY));
+    KC_TRY(ensure(c, vs->buf, off));
+    char *w = static_cast<char *>(vs->buf.p);
+    KY *lbkey = reinterpret_cast<KY *>(w + o_lbkey), *amax = reinterpret_cast<KY *>(w + o_amax);
+    KY *amin = reinterpret_cast<KY *>(w + o_amin), *cand = reinterpret_cast<KY *>(w + o_cand);
+    unsigned *flags = reinterpret_cast<unsigned *>(w + o_flags);
+    T *blo = reinterpret_cast<T *>(w + o_blo), *bhi = reinterpret_cast<T *>(w + o_bhi);
+    int64_t *reps = reinterpret_cast<int64_t *>(w + o_reps);
+    int *nreps = reinterpret_cast<int *>(w + o_nreps), *have = reinterpret_cast<int *>(w + o_have);
+    T *repx = reinterpret_cast<T *>(w + o_repx);
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(w + o_cnt);
+    OrdT<T> *smax = reinterpret_cast<OrdT<T> *>(w + o_smax), *smin = reinterpret_cast<OrdT<T> *>(w + o_smin);
+    OrdT<T> *jmax = reinterpret_cast<OrdT<T> *>(w + o_jmax), *jmin = reinterpret_cast<OrdT<T> *>(w + o_jmin);
+    // zero everything up to the min accumulators, which start at all-ones
+    KC_CUDA(c, cudaMemsetAsync(w, 0, o_smin, c->stream));
+    KC_CUDA(c, cudaMemsetAsync(w + o_smin, 0xFF, o_jmax - o_smin, c->stream));
+    KC_CUDA(c, cudaMemsetAsync(w + o_jmax, 0, o_jmin - o_jmax, c->stream));
+    KC_CUDA(c, cudaMemsetAsync(w + o_jmin, 0xFF, o_cand - o_jmin, c->stream));
+    KC_CUDA(c, cudaMemsetAsync(w + o_cand, 0, off - o_cand, c->stream));
+
+    const Margins mg = make_margins(c, alpha, 0.0);
+    const double r_up = nextafter(std::sqrt(alpha), __builtin_huge_val());
+    // pass A
+    const int tileA = (int)std::max<int64_t>(256, std::min<int64_t>(2048, (64 * 1024) / (D * 8)) / 32 * 32);
+    const size_t smemA = (size_t)D * tileA * 8;
+    int gA = 1;
+    const int64_t tilesA = (v.n + tileA - 1) / tileA;
+    auto kA = visit_a_kernel<T, KM, DM>;
+    KC_TRY(grid_of(c, kA, smemA, tilesA, &gA));
+    if (v.n > 0) {
+        kA<<<gA, kThreads, smemA, c->stream>>>(static_cast<const T *>(v.X), v.ld, v.n, tileA, lo, hi, B, K_, D, alpha,
+                                              mg, lbkey, amax, amin, flags);
+        KC_TRY(after_launch(c, "tighten pass A"));
+    }
+    FinA fa;
+    fa.seeds = seeds;
+    fa.ids = v.ids;
+    fa.r_up = r_up;
+    fa.alpha = alpha;
+    fa.defl = deflate_factor(c->dt, D);
+    fa.slack = underflow_slack(c->dt, D);
+    fa.seed_defl = sizeof(T) == 4 ? 1.0 - gamma_n(f64_roundings(D), kU64) : 1.0;
+    fa.cap = std::min(reps_cap(D, cap), RM);
+    fa.RM = RM;
+    finalize_a_kernel<T><<<(B + 127) / 128, 128, 0, c->stream>>>(
+        B, K_, D, lo, hi, lbkey, amax, amin, flags, static_cast<const T *>(c->X), c->ldx, fa, blo, bhi, reps, nreps,
+        repx, have, lb, lb_raw, lbarg);
+    KC_TRY(after_launch(c, "tighten finalize A"));
+    // pass B
+    const int tileB = (int)std::max<int64_t>(256, std::min<int64_t>(2048, (32 * 1024) / (D * (int64_t)sizeof(T))) / 32 * 32);
+    const size_t smemB = (size_t)D * tileB * sizeof(T);
+    int gB = 1;
+    auto kB = visit_b_kernel<T, KM, DM, RMX>;
+    KC_TRY(grid_of(c, kB, smemB, (v.n + tileB - 1) / tileB, &gB));
+    if (v.n > 0) {
+        kB<<<gB, kThreads, smemB, c->stream>>>(static_cast<const T *>(v.X), v.ld, v.n, tileB, B, K_, D, RM, blo, bhi,
+                                              repx, nreps, have, alpha, mg, cnt, smax, smin, jmax, jmin, cand, flags);
+        KC_TRY(after_launch(c, "tighten pass B"));
+    }
+    finalize_b_kernel<T><<<(B + 127) / 128, 128, 0, c->stream>>>(B, K_, D, cnt, smax, smin, jmax, jmin, cand, flags,
+                                                                v.ids, r_up, static_cast<T *>(lo_out_),
+                                                                static_cast<T *>(hi_out_), counts, cand_out, status);
+    KC_TRY(after_launch(c, "tighten finalize B"));
+    vs->reps = reps;
+    vs->nreps = nreps;
+    vs->repx = repx;
+    vs->RM = RM;
+    return KC_OK;
+}
+
+}  // namespace
+
+kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int B, double alpha,
+                              const int64_t *seeds_dev, int ball_cap, void *lo_out, void *hi_out, int64_t *counts,
+                              int64_t *cand, double *lb, double *lb_raw, int64_t *lbarg, int8_t *status,
+                              VisitScratch *vs)
+{
+    if (B <= 0) return KC_OK;
+    if (c->D > 8 || c->K > 8)
+        return set_err(c, KC_EINVAL, "kc_tighten: supported for D <= 8 and K <= 8 (got D=%d, K=%d)", c->D, c->K);
+    const int cap = ball_cap > 0 ? ball_cap : 50;
+    if (c->dt == KC_F32) {
+        if (c->K <= 4 && c->D <= 2)
+            return tighten_impl<float, 4, 2, 5>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
+                                                lb, lb_raw, lbarg, status, vs);
+        if (c->K <= 4 && c->D <= 4)
+            return tighten_impl<float, 4, 4, 9>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
+                                                lb, lb_raw, lbarg, status, vs);
+        if (c->K <= 2 && c->D <= 8)
+            return tighten_impl<float, 2, 8, 17>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
+                                                 lb, lb_raw, lbarg, status, vs);
+        return set_err(c, KC_EINVAL, "kc_tighten: float data supported for K <= 4 with D <= 4, or K <= 2 with D <= 8 (K=%d, D=%d)", c->K, c->D);
+    }
+    if (c->K <= 4 && c->D <= 2)
+        return tighten_impl<double, 4, 2, 5>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
+                                             lb_raw, lbarg, status, vs);
+    if (c->K <= 4 && c->D <= 4)
+        return tighten_impl<double, 4, 4, 9>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
+                                             lb_raw, lbarg, status, vs);
+    return set_err(c, KC_EINVAL, "kc_tighten: double data supported for K <= 4, D <= 4 (K=%d, D=%d)", c->K, c->D);
+}
+
+kc_status launch_sample_reduction_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int M,
+                                       const void *repx, const int *nreps, int R, double beta_glob, double alpha,
+                                       uint8_t *mask, unsigned long long *n_active)
+{
+    if (c->D > 8) return set_err(c, KC_EINVAL, "sample reduction: supported for D <= 8");
+    KC_CUDA(c, cudaMemsetAsync(n_active, 0, 8, c->stream));
+    if (v.n == 0 || M <= 0) return KC_OK;
+    const Margins mg = make_margins(c, alpha, beta_glob);
+    const int64_t blocks = (v.n + kThreads - 1) / kThreads;
+    const int grid = (int)std::min<int64_t>(blocks, (int64_t)c->num_sms * 8);
+    if (c->dt == KC_F32) {
+        if (c->D <= 4)
+            sr_kernel<float, 16, 4><<<grid, kThreads, 0, c->stream>>>(
+                static_cast<const float *>(v.X), v.ld, v.n, M, c->K, c->D, static_cast<const float *>(lo),
+                static_cast<const float *>(hi), static_cast<const float *>(repx), nreps, R, beta_glob, alpha, mg, mask,
+                n_active);
+        else
+            sr_kernel<float, 16, 8><<<grid, kThreads, 0, c->stream>>>(
+                static_cast<const float *>(v.X), v.ld, v.n, M, c->K, c->D, static_cast<const float *>(lo),
+                static_cast<const float *>(hi), static_cast<const float *>(repx), nreps, R, beta_glob, alpha, mg, mask,
+                n_active);
+    } else {
+        if (c->D <= 4)
+            sr_kernel<double, 16, 4><<<grid, kThreads, 0, c->stream>>>(
+                static_cast<const double *>(v.X), v.ld, v.n, M, c->K, c->D, static_cast<const double *>(lo),
+                static_cast<const double *>(hi), static_cast<const double *>(repx), nreps, R, beta_glob, alpha, mg,
+                mask, n_active);
+        else
+            sr_kernel<double, 16, 8><<<grid, kThreads, 0, c->stream>>>(
+                static_cast<const double *>(v.X), v.ld, v.n, M, c->K, c->D, static_cast<const double *>(lo),
+                static_cast<const double *>(hi), static_cast<const double *>(repx), nreps, R, beta_glob, alpha, mg,
+                mask, n_active);
+    }
+    return after_launch(c, "sample reduction");
+}
+
+kc_status launch_gather_reps(kc_ctx *c, int M, int R, const int64_t *reps, void *repx, int *nreps)
+{
+    if (M <= 0) return KC_OK;
+    const int MK = M * c->K;
+    gather_reps_kernel<<<(MK + 127) / 128, 128, 0, c->stream>>>(M, c->K, c->D, R, reps, c->X, c->ldx,
+                                                                 c->dt == KC_F32, repx, nreps);
+    return after_launch(c, "gather representatives");
+}
+
+}  // namespace kc

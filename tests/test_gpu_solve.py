@@ -1,0 +1,217 @@
+"""Parity of the CUDA tightening, sample-reduction and solver paths with the
+CPU oracle (Section 4.1 Algorithms 3-4, Section 4.2 Algorithm 5, Algorithm 1).
+
+Double data: every decision is taken in double on both sides, so statuses,
+tightened boxes, counts, candidates and masks are compared exactly.  Float
+data: the kernels decide in float with proved margins; inputs are chosen so
+that no decision quantity lies within the float error band of its threshold,
+and then the outputs must again match exactly (boxes are sample coordinates or
+the same double-rounded box-BT bounds).  Solves: the certified objective
+equals the oracle's (or brute force's) double value to 1e-12 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2301_00061_gb300 import KCenter  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _blobs(n, d, k, seed, dtype):
+    return synth.gaussian_mixture(n, d, (1 / k,) * k, (1.0,) * k, (1.0,) * k, 10.0, seed, dtype=dtype)
+
+
+def _nodes_around(X, centers, B, seed, scale=(0.05, 0.6)):
+    """B random nodes whose box k is a random sub-box of the root region,
+    biased to contain sample centers[k] (a realistic branch-and-bound node)."""
+    rng = np.random.default_rng(seed)
+    lo0, hi0 = X.min(0).astype(np.float64), X.max(0).astype(np.float64)
+    k, d = len(centers), X.shape[1]
+    lo = np.empty((B, k, d)); hi = np.empty((B, k, d))
+    for b in range(B):
+        for j in range(k):
+            w = rng.uniform(*scale, size=d) * (hi0 - lo0)
+            c = X[centers[j]].astype(np.float64) + rng.normal(0, 0.3, size=d) * w
+            lo[b, j] = np.clip(c - rng.uniform(0.2, 0.8, size=d) * w, lo0, hi0)
+            hi[b, j] = np.clip(lo[b, j] + w, lo0, hi0)
+    return np.ascontiguousarray(lo.astype(X.dtype)), np.ascontiguousarray(hi.astype(X.dtype))
+
+
+def _compare_tighten(X, lo, hi, alpha, seeds, g, exact_cand=True):
+    B, k, d = lo.shape
+    st = g["status"].cpu().numpy() if hasattr(g["status"], "cpu") else g["status"]
+    glo = g["lo"].cpu().numpy() if hasattr(g["lo"], "cpu") else g["lo"]
+    ghi = g["hi"].cpu().numpy() if hasattr(g["hi"], "cpu") else g["hi"]
+    gcnt = g["count"].cpu().numpy() if hasattr(g["count"], "cpu") else g["count"]
+    gcand = g["cand"].cpu().numpy() if hasattr(g["cand"], "cpu") else g["cand"]
+    glb = g["lb"].cpu().numpy() if hasattr(g["lb"], "cpu") else g["lb"]
+    is_f32 = X.dtype == np.float32
+    n_feasible = 0
+    for b in range(B):
+        r = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=is_f32)
+        assert glb[b] <= r["beta"] and glb[b] >= r["beta"] * (1 - 1e-6), (b, glb[b], r["beta"])
+        assert st[b] == r["status"], (b, st[b], r["status"])
+        if r["status"] == 1:
+            continue
+        n_feasible += 1
+        assert np.array_equal(glo[b], r["lo"].astype(X.dtype)), (b, glo[b], r["lo"])
+        assert np.array_equal(ghi[b], r["hi"].astype(X.dtype)), (b, ghi[b], r["hi"])
+        assert np.array_equal(gcnt[b], r["count"]), (b, gcnt[b], r["count"])
+        if exact_cand:
+            assert np.array_equal(gcand[b], r["cand"]), (b, gcand[b], r["cand"])
+        else:
+            for j in range(k):
+                x = X[gcand[b, j]]
+                assert np.all(x >= glo[b, j]) and np.all(x <= ghi[b, j])
+    return n_feasible
+
+
+def _ambiguous(X, lo, hi, alpha, seeds, band=3e-6):
+    """True when some decision quantity of the tightening lies within `band`
+    (relative) of its threshold, where float and double decisions can differ."""
+    Xd = X.astype(np.float64)
+    for b in range(lo.shape[0]):
+        bm = oracle.beta_matrix(Xd, lo[b], hi[b])
+        if np.any(np.abs(bm - alpha) <= band * alpha):
+            return True
+        r = oracle.tighten(Xd, lo[b], hi[b], alpha, seeds=seeds, is_f32=True)
+        for reps in r["reps"]:
+            for j in reps:
+                dd = ((Xd - Xd[j]) ** 2).sum(1)
+                if np.any(np.abs(dd - alpha) <= band * alpha) or np.any(np.abs(dd - 4 * alpha) <= 4 * band * alpha):
+                    return True
+    return False
+
+
+@pytest.mark.parametrize("d,k", [(2, 3), (2, 4), (4, 2)])
+def test_tighten_f64_exact(d, k):
+    X = _blobs(3_001, d, k, seed=d * 7 + k, dtype=np.float64)
+    c, fobj = oracle.fft(X, k, 0)
+    z = oracle.solve(X, k, tol=1e-12)["objective"]
+    kc = KCenter(_t(X), k)
+    for alpha in (z * 1.3, fobj):
+        lo, hi = _nodes_around(X, c, 24, seed=k)
+        for seeds in (None, c):
+            g = kc.tighten(_t(lo), _t(hi), alpha, seeds=None if seeds is None else _t(seeds))
+            torch.cuda.synchronize()
+            nf = _compare_tighten(X, lo, hi, alpha, seeds, g)
+            assert nf >= 1
+
+
+@pytest.mark.parametrize("d,k", [(2, 3), (4, 3), (2, 4), (3, 3)])
+def test_tighten_f32_exact_on_unambiguous_inputs(d, k):
+    X = _blobs(4_003, d, k, seed=100 + d * 7 + k, dtype=np.float32)
+    c, fobj = oracle.fft(X, k, 3)
+    kc = KCenter(_t(X), k)
+    lo, hi = _nodes_around(X, c, 12, seed=d)
+    alpha = fobj * 0.71
+    for _ in range(20):
+        if not _ambiguous(X, lo, hi, alpha, None):
+            break
+        alpha *= 1.0000373
+    else:
+        pytest.skip("could not find an unambiguous alpha")
+    g = kc.tighten(_t(lo), _t(hi), alpha)
+    torch.cuda.synchronize()
+    _compare_tighten(X, lo, hi, alpha, None, g, exact_cand=False)
+
+
+def test_tighten_root_and_ragged_sizes():
+    """Root node (all boxes = M0): bound 0, nothing assigned (boxes equal)."""
+    X = _blobs(1_037, 2, 3, seed=4, dtype=np.float64)
+    kc = KCenter(_t(X), 3)
+    lo0, hi0 = oracle.root_box(X)
+    L = np.tile(lo0, (1, 3, 1)); H = np.tile(hi0, (1, 3, 1))
+    alpha = oracle.fft(X, 3, 0)[1]
+    g = kc.tighten(_t(L), _t(H), alpha)
+    _compare_tighten(X, L, H, alpha, None, g)
+    assert float(g["lb"][0]) == 0.0
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_sample_reduction_matches_oracle(dtype):
+    X = _blobs(20_011, 2, 3, seed=5, dtype=dtype)
+    r = oracle.solve(X, 3, tol=0.0, use_sr=False)
+    c = r["centers"]
+    alpha = r["objective"]
+    lo = (X[c].astype(np.float64) - 0.3)[None].astype(dtype)
+    hi = (X[c].astype(np.float64) + 0.3)[None].astype(dtype)
+    beta = oracle.lower_bound(X, lo[0], hi[0])[0] * 0.999
+    reps = np.array(c, dtype=np.int64).reshape(1, 3, 1)
+    ref = oracle.sample_reduction(X, lo, hi, beta, alpha, np.ones(len(X), bool), reps=[[[int(v)] for v in c]])
+    kc = KCenter(_t(X), 3)
+    act = np.ones(len(X), np.uint8)
+    act, n = kc.sample_reduction(lo, hi, beta, alpha, act, reps=reps)
+    assert n == int(ref.sum()) == int(act.sum())
+    assert np.array_equal(act.astype(bool), ref)
+    assert n < len(X)
+
+
+def _solve_both(X, k, **kw):
+    kc = KCenter(_t(X), k)
+    g = kc.solve(tol=1e-12, **kw)
+    r = oracle.solve(X, k, tol=1e-12, use_bt=kw.get("use_bt", 1) == 1, use_sr=kw.get("i_sr", 1) > 0)
+    return g, r
+
+
+@pytest.mark.parametrize("n", [60, 300, 1000])
+def test_solve_small_workload_f64(n):
+    X, w = synth.make_workload("small")
+    if n < 1000:
+        X = X[synth.subsample_rows(1000, n, seed=0)]
+    g, r = _solve_both(X, 3)
+    assert g["status"] == 0
+    assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"]
+    assert g["lower_bound"] <= g["objective"] and g["gap"] <= 1e-12
+    assert oracle.objective(X, g["centers"])[0] == g["objective"]
+    if n == 60:
+        assert abs(g["objective"] - oracle.bruteforce(X, 3)[0]) <= 1e-12 * g["objective"]
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_solve_f32_small(k):
+    X = _blobs(3_000, 2, k, seed=k, dtype=np.float32)
+    g, r = _solve_both(X, k)
+    assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
+    assert oracle.objective(X, g["centers"])[0] == g["objective"]
+
+
+def test_solve_plain_bb_and_no_sample_reduction():
+    X = _blobs(800, 2, 3, seed=11, dtype=np.float64)
+    for kw in (dict(use_bt=0, i_sr=0), dict(use_bt=1, i_sr=0), dict(use_bt=1, i_sr=1, batch=8)):
+        g, r = _solve_both(X, 3, **kw)
+        assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (kw, g, r)
+
+
+def test_solve_bruteforce_tiny_random():
+    for seed in range(6):
+        rng = np.random.default_rng(seed)
+        n = int(rng.integers(10, 40))
+        X = _blobs(n, 2, 3, seed=seed, dtype=np.float64)
+        for k in (1, 2, 3):
+            kc = KCenter(_t(X), k)
+            g = kc.solve(tol=0.0)
+            z, _ = oracle.bruteforce(X, k)
+            assert abs(g["objective"] - z) <= 1e-12 * max(z, 1e-300), (seed, k, g, z)
+
+
+def test_solve_batched_workload_reduced():
+    """The batched-solve workload's recipe (D=4, K=3, weights .6/.3/.1) at
+    N=100k: the GPU certificate equals the oracle's optimum."""
+    X, w = synth.make_workload("batched_solve", n=100_000)
+    g, r = _solve_both(X, 3)
+    assert g["status"] == 0
+    assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
