@@ -111,6 +111,48 @@ kc_status kc_lower_bounds(kc_ctx *ctx, const void *lo, const void *hi, int32_t B
                           double *lb_raw_out, int64_t *argmax_out);
 
 /*
+ * kc_lower_bounds_noalloc -- the float lower bound of kc_lower_bounds without a
+ * context and without allocating any memory.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate GPU memory at the
+ * point where they need bounds -- a process whose device memory is already
+ * reserved by another allocator (a framework's caching pool holding nearly
+ * all of it), or a latency-critical loop where the device-wide
+ * synchronization that cudaMalloc / cudaFree can imply is not acceptable.
+ *   X          device, float, attribute-major: X[a*ld + s]; when X is 16-byte
+ *              aligned and ld is a multiple of 4 the vectorized kernel is used.
+ *   N, ld, D, K  samples, row length (ld >= N), attributes, clusters.
+ *   lo, hi     device [B][K][D] float boxes.
+ *   lb_out, lb_raw_out, argmax_out  device, as in kc_lower_bounds (the last
+ *              two may be NULL).
+ *   stream     cudaStream_t the work is ordered on.
+ * Scratch is one fixed array in the library (512 partial results for each of
+ * 256 nodes, 1 MiB, kept by every GPU that loads the library until the
+ * process exits); nodes are processed 256 at a time and B may be at most
+ * 4096 (larger B returns KC_EINVAL).  The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.  Every call reuses the same array, so calls
+ * that can overlap on the GPU (different streams, no ordering between them)
+ * race and must not be issued.  Returns KC_EINVAL for bad sizes, KC_ECUDA if a
+ * CUDA call fails.  Nothing is written to an error string.
+ */
+kc_status kc_lower_bounds_noalloc(const float *X, int64_t N, int64_t ld, int32_t D, int32_t K,
+                                  const float *lo, const float *hi, int32_t B, double *lb_out,
+                                  double *lb_raw_out, int64_t *argmax_out, void *stream);
+
+/*
+ * kc_autotune -- picks the launch shape of the float lower-bound kernel
+ * (samples per thread, nodes per launch: occupancy against extra passes over
+ * the samples) by timing each candidate with CUDA events on the given batch
+ * of B nodes (lo, hi as in kc_lower_bounds), and keeps the fastest for later
+ * kc_lower_bounds calls on this context.  Outputs (host, each may be NULL):
+ * the chosen samples per thread, nodes per launch, and its time per batch in
+ * ms.  Double data: nothing to tune (outputs 0).  A scheduling choice; the
+ * paper has no counterpart (the bound itself is Section 3.1's).
+ */
+kc_status kc_autotune(kc_ctx *ctx, const void *lo, const void *hi, int32_t B, int32_t *samples_per_thread_out,
+                      int32_t *nodes_per_launch_out, float *ms_out);
+
+/*
  * kc_upper_bound -- the objective of Eq. 1 at S center sets on samples
  * (the upper bound alpha(M) of Eq. 12):
  *   alpha = max_s min_k ||x_s - x_{c_k}||^2.
@@ -186,6 +228,38 @@ kc_status kc_sample_reduction(kc_ctx *ctx, const void *lo, const void *hi, int32
                               const int64_t *reps, int32_t R, double beta_glob, double alpha,
                               uint8_t *active_inout, int64_t *n_active_out);
 
+/*
+ * The learned node scorer: a 12 -> 64 -> 64 -> 2 perceptron with ReLU
+ * activations, bfloat16 weight matrices and float32 biases, activations and
+ * accumulation.  Output 0 ranks open nodes, output 1 is the logit of the
+ * branching rule (> 0: split the box that is nearest to the sample attaining
+ * the node's lower bound, on the attribute where that sample lies farthest
+ * outside it; otherwise the max-range rule of Section 3.3).  The paper has no
+ * learned component: the exact lower bound still decides every prune, so the
+ * certified optimum cannot change.  Parameters are one float vector of 5122
+ * values [W1 64x12, b1 64, W2 64x64, b2 64, W3 2x64, b3 2] (row major);
+ * training minimizes the mean of m0 (y0 - t0)^2 / 2 + m1 (softplus(y1) - t1 y1)
+ * with Adam.  Arrays may be host or device memory.
+ */
+typedef struct kc_mlp kc_mlp;
+kc_status kc_mlp_create(const float *params, void *stream, kc_mlp **out);
+void kc_mlp_destroy(kc_mlp *m);
+const char *kc_mlp_last_error(const kc_mlp *m);
+kc_status kc_mlp_get_params(kc_mlp *m, float *params);
+/* feats [B][12] -> out [B][2]. */
+kc_status kc_mlp_forward(kc_mlp *m, const float *feats, int32_t B, float *out);
+/* Mean loss and its gradient (5122 floats) over n samples; targets, masks [n][2]. */
+kc_status kc_mlp_grad(kc_mlp *m, const float *feats, const float *targets, const float *masks, int32_t n,
+                      float *loss_out, float *grad_out);
+/* epochs x ceil(n / batch) Adam steps (lr, beta1 0.9, beta2 0.999, eps 1e-8) over
+ * a permutation of the samples drawn from `seed` every epoch; loss_out (host or
+ * NULL) receives the mean loss over all n samples afterwards. */
+kc_status kc_mlp_train(kc_mlp *m, const float *feats, const float *targets, const float *masks, int32_t n,
+                       int32_t epochs, int32_t batch, float lr, uint64_t seed, float *loss_out);
+/* Attaches a scorer to a context (NULL detaches); kc_solve with order = 1 uses it.
+ * The scorer must outlive its use by the context. */
+kc_status kc_set_scorer(kc_ctx *ctx, kc_mlp *m);
+
 /* Options of kc_solve; kc_solve_defaults() fills the defaults shown. */
 typedef struct {
     double tol;            /* 1e-12: stop when (UB - LB) / UB <= tol (Section 6.1 gap) */
@@ -195,11 +269,12 @@ typedef struct {
     int32_t ball_cap;      /* 50: representatives per cluster */
     int32_t i_sr;          /* 1: sample reduction every i_sr batches, 0: off */
     int32_t use_bt;        /* 1: assignment + bounds tightening (BB+CF+BT); 0: BB+CF */
-    int32_t order;         /* 0: best bound; 1: learned node scorer (needs weights) */
+    int32_t order;         /* 0: best bound, max-range branching; 1: learned scorer (kc_set_scorer) */
     int32_t use_graph;     /* 1: replay each batch's kernels as a CUDA graph */
-    int32_t verbose;       /* 0 */
+    int32_t verbose;       /* 0; 1: per-phase timings on stderr */
+    int32_t log_labels;    /* 0; 1: the node log also carries strong-branching labels (extra bound passes) */
     uint64_t seed;         /* 0: FFT start = seed mod N */
-    const char *log_path;  /* NULL, or a file receiving one JSON line per node visit */
+    const char *log_path;  /* NULL, or a file receiving one JSON line per branched node (scorer features) */
 } kc_solve_opts;
 
 typedef struct {

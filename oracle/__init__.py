@@ -51,6 +51,8 @@ class TightenOut(C.Structure):
         ("n_assigned", C.c_int64 * MAXK),
         ("n_reps", C.c_int32 * MAXK),
         ("reps", C.c_int64 * (MAXK * MAXREPS)),
+        ("blo", C.c_double * (MAXK * MAXD)),
+        ("bhi", C.c_double * (MAXK * MAXD)),
     ]
 
 
@@ -245,6 +247,8 @@ def tighten(X, lo, hi, alpha, seeds=None, active=None, is_f32=False, ball_cap=50
         "cand": np.array(out.cand[:k]),
         "n_assigned": np.array(out.n_assigned[:k]),
         "reps": [list(out.reps[j * MAXREPS: j * MAXREPS + out.n_reps[j]]) for j in range(k)],
+        "box_bt_lo": np.array(out.blo[:kd]).reshape(k, d),
+        "box_bt_hi": np.array(out.bhi[:kd]).reshape(k, d),
     }
 
 

@@ -329,6 +329,8 @@ typedef struct {
     int64_t n_assigned[KCO_MAXK];   /* |J^k| after both assignment rules */
     int32_t n_reps[KCO_MAXK];
     int64_t reps[KCO_MAXK * KCO_MAXREPS];
+    double blo[KCO_MAXK * KCO_MAXD];  /* the box-BT box M' of step A */
+    double bhi[KCO_MAXK * KCO_MAXD];
 } kco_tighten_out;
 
 /* Representatives ("balls") of cluster k, from its assigned set: the seed of
@@ -454,6 +456,9 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
             }
             if (blo[i] > bhi[i]) infeasible = 1;
         }
+
+    memcpy(out->blo, blo, sizeof(double) * KD);
+    memcpy(out->bhi, bhi, sizeof(double) * KD);
 
     /* representatives from J_A */
     int all_have = 1;

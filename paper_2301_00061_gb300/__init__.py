@@ -22,8 +22,9 @@ from . import build as _build
 __all__ = [
     "KCError", "KC_F32", "KC_F64", "KC_ROW_MAJOR", "KC_COL_MAJOR", "SolveOpts", "Result",
     "kc_create", "kc_destroy", "kc_last_error", "kc_set_stream", "kc_launch_count", "kc_root_box",
-    "kc_lower_bounds", "kc_upper_bound", "kc_fft", "kc_tighten", "kc_sample_reduction",
-    "kc_solve_defaults", "kc_solve", "KCenter", "library_path",
+    "kc_lower_bounds", "kc_lower_bounds_noalloc", "kc_autotune", "kc_upper_bound", "kc_fft", "kc_tighten", "kc_sample_reduction",
+    "kc_solve_defaults", "kc_solve", "KCenter", "library_path", "kc_mlp_create", "kc_mlp_destroy",
+    "kc_mlp_get_params", "kc_mlp_forward", "kc_mlp_grad", "kc_mlp_train", "kc_set_scorer", "Scorer",
 ]
 
 KC_F32, KC_F64 = 0, 1
@@ -42,7 +43,8 @@ class SolveOpts(C.Structure):
     _fields_ = [
         ("tol", C.c_double), ("time_limit_s", C.c_double), ("node_limit", C.c_int64),
         ("batch", C.c_int32), ("ball_cap", C.c_int32), ("i_sr", C.c_int32), ("use_bt", C.c_int32),
-        ("order", C.c_int32), ("use_graph", C.c_int32), ("verbose", C.c_int32), ("seed", C.c_uint64),
+        ("order", C.c_int32), ("use_graph", C.c_int32), ("verbose", C.c_int32), ("log_labels", C.c_int32),
+        ("seed", C.c_uint64),
         ("log_path", C.c_char_p),
     ]
 
@@ -74,11 +76,21 @@ def _load():
         "kc_launch_count": (I64, [P]),
         "kc_root_box": (I32, [P, P, P]),
         "kc_lower_bounds": (I32, [P, P, P, I32, P, P, P]),
+        "kc_lower_bounds_noalloc": (I32, [P, I64, I64, I32, I32, P, P, I32, P, P, P, P]),
+        "kc_autotune": (I32, [P, P, P, I32, P, P, P]),
         "kc_upper_bound": (I32, [P, P, I32, P, P]),
         "kc_fft": (I32, [P, I64, P, P]),
         "kc_tighten": (I32, [P, P, P, I32, D, P, I32, P, P, P, P, P, P]),
         "kc_sample_reduction": (I32, [P, P, P, I32, P, I32, D, D, P, P]),
         "kc_solve_defaults": (None, [C.POINTER(SolveOpts)]),
+        "kc_mlp_create": (I32, [P, P, C.POINTER(P)]),
+        "kc_mlp_destroy": (None, [P]),
+        "kc_mlp_last_error": (C.c_char_p, [P]),
+        "kc_mlp_get_params": (I32, [P, P]),
+        "kc_mlp_forward": (I32, [P, P, I32, P]),
+        "kc_mlp_grad": (I32, [P, P, P, P, I32, P, P]),
+        "kc_mlp_train": (I32, [P, P, P, P, I32, I32, I32, C.c_float, C.c_uint64, P]),
+        "kc_set_scorer": (I32, [P, P]),
         "kc_solve": (I32, [P, D, C.POINTER(SolveOpts), C.POINTER(Result)]),
     }
     for name, (res, args) in sig.items():
@@ -176,6 +188,22 @@ def kc_lower_bounds(h, lo, hi, lb, lb_raw=None, argmax=None):
     _check(h, _lib.kc_lower_bounds(h, _ptr(lo), _ptr(hi), B, _ptr(lb), _ptr(lb_raw), _ptr(argmax)))
 
 
+def kc_autotune(h, lo, hi):
+    """Returns (samples per thread, nodes per launch, ms per batch) chosen."""
+    st, ch, ms = C.c_int32(), C.c_int32(), C.c_float()
+    _check(h, _lib.kc_autotune(h, _ptr(lo), _ptr(hi), lo.shape[0], C.byref(st), C.byref(ch), C.byref(ms)))
+    return st.value, ch.value, ms.value
+
+
+def kc_lower_bounds_noalloc(X, N, ld, D, K, lo, hi, lb, lb_raw=None, argmax=None, stream=None):
+    """X: device float32 tensor holding X[a*ld + s]; lo, hi (B, K, D) device."""
+    B = lo.shape[0]
+    st = _lib.kc_lower_bounds_noalloc(_ptr(X), int(N), int(ld), int(D), int(K), _ptr(lo), _ptr(hi), B, _ptr(lb),
+                                      _ptr(lb_raw), _ptr(argmax), _stream_ptr(stream))
+    if st != 0:
+        raise KCError(st, "kc_lower_bounds_noalloc failed")
+
+
 def kc_upper_bound(h, centers, ub, worst=None):
     _check(h, _lib.kc_upper_bound(h, _ptr(centers), centers.shape[0], _ptr(ub), _ptr(worst)))
 
@@ -211,6 +239,88 @@ def kc_solve(h, tol=-1.0, opts=None):
     if st not in (0, 4, 5):
         _check(h, st)
     return r, st
+
+
+def _mcheck(m, st):
+    if st != 0:
+        raise KCError(st, _lib.kc_mlp_last_error(m).decode() if m else "kc_mlp_create failed")
+
+
+def kc_mlp_create(params, stream=None):
+    p = np.ascontiguousarray(params, dtype=np.float32) if not _is_torch(params) else params
+    m = C.c_void_p()
+    _mcheck(None, _lib.kc_mlp_create(_ptr(p), _stream_ptr(stream), C.byref(m)))
+    return m
+
+
+def kc_mlp_destroy(m):
+    _lib.kc_mlp_destroy(m)
+
+
+def kc_mlp_get_params(m, out):
+    _mcheck(m, _lib.kc_mlp_get_params(m, _ptr(out)))
+
+
+def kc_mlp_forward(m, feats, out):
+    _mcheck(m, _lib.kc_mlp_forward(m, _ptr(feats), feats.shape[0], _ptr(out)))
+
+
+def kc_mlp_grad(m, feats, targets, masks, loss_out, grad_out):
+    _mcheck(m, _lib.kc_mlp_grad(m, _ptr(feats), _ptr(targets), _ptr(masks), feats.shape[0], _ptr(loss_out),
+                                _ptr(grad_out)))
+
+
+def kc_mlp_train(m, feats, targets, masks, epochs, batch, lr, seed, loss_out=None):
+    _mcheck(m, _lib.kc_mlp_train(m, _ptr(feats), _ptr(targets), _ptr(masks), feats.shape[0], int(epochs),
+                                 int(batch), float(lr), int(seed), _ptr(loss_out)))
+
+
+def kc_set_scorer(h, m):
+    _check(h, _lib.kc_set_scorer(h, m))
+
+
+class Scorer:
+    """The learned node scorer (12 -> 64 -> 64 -> 2, bf16 weights)."""
+
+    NPARAM = 5122
+
+    def __init__(self, params, stream=None):
+        self.m = kc_mlp_create(np.ascontiguousarray(params, dtype=np.float32), stream)
+
+    def close(self):
+        if self.m:
+            kc_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        out = np.empty(self.NPARAM, np.float32)
+        kc_mlp_get_params(self.m, out)
+        return out
+
+    def forward(self, feats):
+        feats = np.ascontiguousarray(feats, dtype=np.float32)
+        out = np.empty((feats.shape[0], 2), np.float32)
+        kc_mlp_forward(self.m, feats, out)
+        return out
+
+    def grad(self, feats, targets, masks):
+        loss = np.zeros(1, np.float32)
+        g = np.empty(self.NPARAM, np.float32)
+        kc_mlp_grad(self.m, np.ascontiguousarray(feats, np.float32), np.ascontiguousarray(targets, np.float32),
+                    np.ascontiguousarray(masks, np.float32), loss, g)
+        return float(loss[0]), g
+
+    def train(self, feats, targets, masks, epochs=20, batch=256, lr=1e-3, seed=0):
+        loss = np.zeros(1, np.float32)
+        kc_mlp_train(self.m, np.ascontiguousarray(feats, np.float32), np.ascontiguousarray(targets, np.float32),
+                     np.ascontiguousarray(masks, np.float32), epochs, batch, lr, seed, loss)
+        return float(loss[0])
 
 
 # ------------------------------------------------------------- convenience
@@ -302,6 +412,10 @@ class KCenter:
         n_act = self._alloc(lo, (1,), "i64")
         kc_sample_reduction(self.h, lo, hi, beta_glob, alpha, active, reps, n_act)
         return active, int(n_act[0])
+
+    def set_scorer(self, scorer):
+        kc_set_scorer(self.h, scorer.m if scorer is not None else None)
+        self._scorer = scorer
 
     def solve(self, tol=1e-12, **kw):
         o = kc_solve_defaults()

@@ -247,6 +247,27 @@ kc_status kc_lower_bounds(kc_ctx *c, const void *lo, const void *hi, int32_t B, 
     return sg.finish();
 }
 
+kc_status kc_autotune(kc_ctx *c, const void *lo, const void *hi, int32_t B, int32_t *st_out, int32_t *chunk_out,
+                      float *ms_out)
+{
+    if (!c) return KC_EINVAL;
+    if (B <= 0 || !lo || !hi) return set_err(c, KC_EINVAL, "kc_autotune: empty node batch");
+    const size_t box = (size_t)B * c->K * c->D * c->esize;
+    Stager sg(c);
+    const int ilo = sg.add(lo, box, true), ihi = sg.add(hi, box, true);
+    KC_TRY(sg.begin());
+    KC_TRY(ensure(c, c->stage_out, (size_t)B * 8 + 2 * (size_t)kMaxD * 8 + 512));
+    int st = 0, ch = 0;
+    float ms = 0.f;
+    KC_TRY(autotune_lower_bounds(c, sg.dev(ilo), sg.dev(ihi), B,
+                                 reinterpret_cast<double *>(static_cast<char *>(c->stage_out.p) + 2 * (size_t)kMaxD * 8 + 256),
+                                 &st, &ch, &ms));
+    if (st_out) *st_out = st;
+    if (chunk_out) *chunk_out = ch;
+    if (ms_out) *ms_out = ms;
+    return KC_OK;
+}
+
 static kc_status check_centers(kc_ctx *c, const int64_t *centers, size_t count)
 {
     std::vector<int64_t> h(count);

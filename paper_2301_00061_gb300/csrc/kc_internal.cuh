@@ -37,6 +37,8 @@ struct VisitScratch {
 
 }  // namespace kc
 
+struct kc_mlp;
+
 struct kc_ctx {
     int dev = 0;
     int num_sms = 0;
@@ -54,13 +56,14 @@ struct kc_ctx {
     kc::DevBuf stage_out;        // device-side outputs destined for host
     kc::DevBuf work;             // per-call work arrays
     kc::VisitScratch vs;         // tightening workspace
+    kc_mlp *scorer = nullptr;    // learned node scorer used by kc_solve with order = 1
     void *pinned = nullptr;      // pinned host staging
     size_t pinned_bytes = 0;
     int64_t launches = 0;
     std::string err;
     // autotuned launch shapes, keyed by kernel family (see kc_tune.cu)
     int lb_st = 0;               // samples per thread of the float lower-bound kernel
-    int lb_ctas_per_sm = 0;
+    int lb_chunk = 0;            // node chunk of the float lower-bound kernel (0: largest that fits)
 };
 
 namespace kc {
@@ -155,6 +158,12 @@ kc_status launch_lower_bounds(kc_ctx *c, const void *lo, const void *hi, int B, 
                               double *lb_raw, int64_t *argmax);
 kc_status launch_lower_bounds_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int B,
                                    double *lb, double *lb_raw, int64_t *arg, int st_override);
+kc_status launch_lower_bounds_cfg(kc_ctx *c, const View &v, const void *lo, const void *hi, int B, double *lb,
+                                  double *lb_raw, int64_t *arg, int st_override, int chunk_override);
+kc_status launch_lower_bounds_refine(kc_ctx *c, const View &v, const void *lo, const void *hi, int B,
+                                     const double *raw_host, double *lb_out, double *lb_exact_out, int64_t *arg);
+kc_status autotune_lower_bounds(kc_ctx *c, const void *lo, const void *hi, int B, double *lb_scratch, int *st_out,
+                                int *chunk_out, float *ms_out);
 
 // Objective (Eq. 1) of S center sets given by device indices [S][K] ->
 // device values [S] (double, exact serial-double value) and argmax [S].
@@ -256,5 +265,8 @@ struct Stager {
     }
 };
 
+
+// Scores B nodes: device features [B][12] -> device outputs [B][2].
+kc_status mlp_forward_device(kc_mlp *m, const float *feats, int B, float *out, cudaStream_t stream);
 
 }  // namespace kc

@@ -62,13 +62,18 @@ struct Node {
     int64_t id;
     int64_t parent;
     int depth;
+    double pkey = 0.0;       // the parent's bound
+    int64_t group = 0;       // its ancestor at depth 8 (itself above that depth)
+    float prio = 0.f;        // learned priority (ties of equal keys: smaller first)
 };
 
 template <typename T>
 struct NodeCmp {
     bool operator()(const Node<T> &a, const Node<T> &b) const
     {
-        return a.key > b.key || (a.key == b.key && a.id > b.id);
+        if (a.key != b.key) return a.key > b.key;
+        if (a.prio != b.prio) return a.prio > b.prio;
+        return a.id > b.id;
     }
 };
 
@@ -85,8 +90,62 @@ double sqdist_host(const std::vector<double> &x, const std::vector<double> &y)
 }
 
 struct SolveBufs {
-    DevBuf boxes, outs, sets, mask, counts, xbuf[2], idbuf[2];
+    DevBuf boxes, outs, sets, mask, counts, xbuf[2], idbuf[2], extra;
 };
+
+// Coordinates of B samples (by id) -> out [B][D] in the data type.
+template <typename T>
+__global__ void gather_points_kernel(const T *__restrict__ X, int64_t ld, int D, const int64_t *__restrict__ ids, int B,
+                                     T *__restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * D; i += gridDim.x * blockDim.x) {
+        const int b = i / D, a = i % D;
+        const int64_t id = ids[b];
+        out[i] = id >= 0 ? X[(size_t)a * ld + id] : T(0);
+    }
+}
+
+// Branching rule 0 (Section 3.3): the max-range variable (smallest k*D+a on ties).
+template <typename T>
+int rule_max_range(const T *lo, const T *hi, int KD)
+{
+    int bi = -1;
+    double br = 0.0;
+    for (int i = 0; i < KD; ++i) {
+        const double r = (double)hi[i] - (double)lo[i];
+        if (r > br) { br = r; bi = i; }
+    }
+    return bi;
+}
+
+// Branching rule 1: the box nearest to the sample x attaining the node's lower
+// bound, on the attribute (with positive range) where x lies farthest outside
+// it.  -1 when x is inside every nearest box or no such attribute exists.
+template <typename T>
+int rule_argmax_gap(const T *lo, const T *hi, const T *x, int K, int D)
+{
+    int kb = -1;
+    double best = 0.0;
+    for (int k = 0; k < K; ++k) {
+        double acc = 0.0;
+        for (int a = 0; a < D; ++a) {
+            const double xv = (double)x[a], l = (double)lo[k * D + a], h = (double)hi[k * D + a];
+            const double d = xv < l ? l - xv : (xv > h ? xv - h : 0.0);
+            acc += d * d;
+        }
+        if (kb < 0 || acc < best) { best = acc; kb = k; }
+    }
+    if (kb < 0 || !(best > 0.0)) return -1;
+    int ab = -1;
+    double g = 0.0;
+    for (int a = 0; a < D; ++a) {
+        const double xv = (double)x[a], l = (double)lo[kb * D + a], h = (double)hi[kb * D + a];
+        if (!(h > l)) continue;
+        const double d = xv < l ? l - xv : (xv > h ? xv - h : 0.0);
+        if (d > g) { g = d; ab = a; }
+    }
+    return ab < 0 ? -1 : kb * D + ab;
+}
 
 template <typename T>
 kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
@@ -156,6 +215,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         KC_CUDA(c, cudaMemcpyAsync(seeds_dev, inc.data(), K * 8, cudaMemcpyHostToDevice, c->stream));
     }
     res->seeds_found = seeds_found;
+    const std::vector<int64_t> inc_seeds = inc;
 
     // ---- open nodes: a binary heap on (key, id)
     std::vector<Node<T>> heap;
@@ -167,12 +227,16 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         for (int k = 0; k < K; ++k)
             for (int a = 0; a < D; ++a) { r.lo[k * D + a] = root_lo[a]; r.hi[k * D + a] = root_hi[a]; }
         r.key = 0.0;
+        r.pkey = 0.0;
         r.id = 0;
         r.parent = -1;
         r.depth = 0;
         heap.push_back(std::move(r));
     }
     int64_t next_id = 1;
+    std::vector<double> range0(D);
+    for (int a = 0; a < D; ++a) range0[a] = std::max((double)root_hi[a] - (double)root_lo[a], 1e-300);
+    kc_mlp *scorer = (o.order == 1) ? c->scorer : nullptr;
 
     const int Bmax = o.batch > 0 ? o.batch : 256;
     // device batch buffers
@@ -205,13 +269,69 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     int64_t *h_sets = reinterpret_cast<int64_t *>(po + o_sets);
     double *h_val = reinterpret_cast<double *>(po + o_val);
 
+    // per-batch extras: argmax ids, counts, argmax coordinates, scorer I/O, label boxes
+    const size_t e_arg = 0, e_cnt = e_arg + (size_t)Bmax * 8, e_pts = e_cnt + (size_t)Bmax * K * 8;
+    const size_t e_feat = e_pts + (((size_t)Bmax * D * sizeof(T) + 255) & ~(size_t)255);
+    const size_t e_out = e_feat + (size_t)Bmax * 12 * 4, e_lbox = e_out + (size_t)Bmax * 2 * 4 + 256;
+    const size_t e_llb = e_lbox + 2 * (size_t)4 * Bmax * KD * sizeof(T), e_raw = e_llb + (size_t)4 * Bmax * 8;
+    const size_t e_ref = e_raw + (size_t)Bmax * 8, extra_bytes = e_ref + (size_t)Bmax * 8 + 256;
+    KC_TRY(ensure(c, sb.extra, extra_bytes));
+    char *xb = static_cast<char *>(sb.extra.p);
+    int64_t *d_arg = reinterpret_cast<int64_t *>(xb + e_arg);
+    int64_t *d_cnt = reinterpret_cast<int64_t *>(xb + e_cnt);
+    T *d_pts = reinterpret_cast<T *>(xb + e_pts);
+    float *d_feat = reinterpret_cast<float *>(xb + e_feat);
+    float *d_out = reinterpret_cast<float *>(xb + e_out);
+    T *d_llo = reinterpret_cast<T *>(xb + e_lbox);
+    T *d_lhi = d_llo + (size_t)4 * Bmax * KD;
+    double *d_llb = reinterpret_cast<double *>(xb + e_llb);
+    double *d_raw = reinterpret_cast<double *>(xb + e_raw);
+    double *d_ref = reinterpret_cast<double *>(xb + e_ref);
+    std::vector<int64_t> h_arg(Bmax), h_cnt((size_t)Bmax * K);
+    std::vector<T> h_pts((size_t)Bmax * D);
+    std::vector<float> h_feat((size_t)Bmax * 12), h_out((size_t)Bmax * 2);
+    std::vector<T> h_llo((size_t)4 * Bmax * KD), h_lhi((size_t)4 * Bmax * KD);
+    std::vector<double> h_llb((size_t)4 * Bmax), h_ub(Bmax);
+
+    std::vector<double> h_raw(Bmax), h_ref(Bmax);
+    // Float data: a bound whose float value cannot decide the prune (its
+    // certified value is below the threshold, the float value plus its error
+    // bound is not) is re-evaluated in double over the same samples (the
+    // ambiguous band of the rounding margin).
+    const double g32 = gamma_n(f32_roundings(D), kU32);
+    std::vector<int> amb;
+    std::vector<double> amb_raw;
+    auto ambiguous = [&](double key, double raw) {
+        const double thr = alpha - tol * alpha;
+        return c->dt == KC_F32 && key < thr && raw * (1.0 + g32) * (1.0 + 1e-9) >= thr;
+    };
+    // refined certified bounds of the boxes src[which[i]] -> h_ref[i]
+    auto refine_nodes = [&](const View &vw, const T *src_lo, const T *src_hi, const double *raw) -> kc_status {
+        const int n = (int)amb.size();
+        amb_raw.resize(n);
+        for (int i = 0; i < n; ++i) {
+            std::memcpy(&h_llo[(size_t)i * KD], src_lo + (size_t)amb[i] * KD, KD * sizeof(T));
+            std::memcpy(&h_lhi[(size_t)i * KD], src_hi + (size_t)amb[i] * KD, KD * sizeof(T));
+            amb_raw[i] = raw[amb[i]];
+        }
+        KC_CUDA(c, cudaMemcpyAsync(d_llo, h_llo.data(), (size_t)n * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+        KC_CUDA(c, cudaMemcpyAsync(d_lhi, h_lhi.data(), (size_t)n * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+        KC_TRY(launch_lower_bounds_refine(c, vw, d_llo, d_lhi, n, amb_raw.data(), d_ref, nullptr, nullptr));
+        KC_CUDA(c, cudaMemcpyAsync(h_ref.data(), d_ref, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaStreamSynchronize(c->stream));
+        return KC_OK;
+    };
+    int64_t refined = 0;
+
     View cur = full_view(c);
     int ping = 0;
-    int64_t visits = 0, batches = 0;
+    int64_t visits = 0, batches = 0, created = 1;
     kc_status status = KC_OK;
     std::vector<Node<T>> batch;
     std::vector<int> live;
     FILE *log = o.log_path ? fopen(o.log_path, "w") : nullptr;
+    double prof[5] = {0, 0, 0, 0, 0};
+    double tA = 0;
 
     auto prune_threshold = [&]() { return alpha - tol * alpha; };
 
@@ -244,29 +364,45 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         KC_CUDA(c, cudaMemcpyAsync(d_lo, h_lo, (size_t)B * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
         KC_CUDA(c, cudaMemcpyAsync(d_hi, h_hi, (size_t)B * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
 
-        // 2. bound + tighten
+        const int Bp = B;
+        if (o.verbose) { KC_CUDA(c, cudaStreamSynchronize(c->stream)); tA = now_s(); }
+
+        // 2b. tighten the survivors
         if (o.use_bt) {
-            KC_TRY(launch_tighten_view(c, cur, d_lo, d_hi, B, alpha, seeds_dev, o.ball_cap, d_lo2, d_hi2, nullptr,
-                                       d_cand, d_lb, nullptr, nullptr, d_st, &c->vs));
+            KC_TRY(launch_tighten_view(c, cur, d_lo, d_hi, Bp, alpha, seeds_dev, o.ball_cap, d_lo2, d_hi2, d_cnt,
+                                       d_cand, d_lb, d_raw, d_arg, d_st, &c->vs));
         } else {
-            KC_TRY(launch_tighten_view(c, cur, d_lo, d_hi, B, __builtin_huge_val(), nullptr, 1, d_lo2, d_hi2, nullptr,
-                                       d_cand, d_lb, nullptr, nullptr, d_st, &c->vs));
+            KC_TRY(launch_tighten_view(c, cur, d_lo, d_hi, Bp, __builtin_huge_val(), nullptr, 1, d_lo2, d_hi2, d_cnt,
+                                       d_cand, d_lb, d_raw, d_arg, d_st, &c->vs));
         }
-        KC_CUDA(c, cudaMemcpyAsync(h_lo2, d_lo2, (size_t)B * KD * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
-        KC_CUDA(c, cudaMemcpyAsync(h_hi2, d_hi2, (size_t)B * KD * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
-        KC_CUDA(c, cudaMemcpyAsync(h_cand, d_cand, (size_t)B * K * 8, cudaMemcpyDeviceToHost, c->stream));
-        KC_CUDA(c, cudaMemcpyAsync(h_lb, d_lb, (size_t)B * 8, cudaMemcpyDeviceToHost, c->stream));
-        KC_CUDA(c, cudaMemcpyAsync(h_st, d_st, (size_t)B, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaMemcpyAsync(h_raw.data(), d_raw, (size_t)Bp * 8, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaMemcpyAsync(h_arg.data(), d_arg, (size_t)Bp * 8, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaMemcpyAsync(h_cnt.data(), d_cnt, (size_t)Bp * K * 8, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaMemcpyAsync(h_lo2, d_lo2, (size_t)Bp * KD * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaMemcpyAsync(h_hi2, d_hi2, (size_t)Bp * KD * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaMemcpyAsync(h_cand, d_cand, (size_t)Bp * K * 8, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaMemcpyAsync(h_lb, d_lb, (size_t)Bp * 8, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaMemcpyAsync(h_st, d_st, (size_t)Bp, cudaMemcpyDeviceToHost, c->stream));
         KC_CUDA(c, cudaStreamSynchronize(c->stream));
-        visits += B;
+        if (o.verbose) { prof[1] += now_s() - tA; tA = now_s(); }
+        visits += Bp;
         ++batches;
 
         // 3. upper bounds of the live nodes' candidates
         live.clear();
-        for (int b = 0; b < B; ++b) {
-            const double lb = std::max(h_lb[b], batch[b].key);
-            batch[b].key = lb;
-            if (h_st[b] == 1 || lb >= prune_threshold()) continue;
+        amb.clear();
+        for (int b = 0; b < Bp; ++b) {
+            h_ub[b] = __builtin_huge_val();
+            batch[b].key = std::max(h_lb[b], batch[b].key);
+            if (h_st[b] != 1 && ambiguous(batch[b].key, h_raw[b])) amb.push_back(b);
+        }
+        if (!amb.empty()) {
+            KC_TRY(refine_nodes(cur, h_lo, h_hi, h_raw.data()));
+            for (size_t i = 0; i < amb.size(); ++i) batch[amb[i]].key = std::max(batch[amb[i]].key, h_ref[i]);
+            refined += (int64_t)amb.size();
+        }
+        for (int b = 0; b < Bp; ++b) {
+            if (h_st[b] == 1 || batch[b].key >= prune_threshold()) continue;
             live.push_back(b);
         }
         if (!live.empty()) {
@@ -277,19 +413,24 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             KC_TRY(launch_objective(c, cur, d_sets, S, K, alpha, d_val, nullptr));
             KC_CUDA(c, cudaMemcpyAsync(h_val, d_val, (size_t)S * 8, cudaMemcpyDeviceToHost, c->stream));
             KC_CUDA(c, cudaStreamSynchronize(c->stream));
+            for (int i = 0; i < S; ++i) h_ub[live[i]] = h_val[i];
             for (int i = 0; i < S; ++i)
                 if (h_val[i] < alpha) {
                     alpha = h_val[i];
                     for (int k = 0; k < K; ++k) inc[k] = h_sets[(size_t)i * K + k];
                 }
         }
+        if (o.verbose) { prof[2] += now_s() - tA; tA = now_s(); }
 
-        // 4. prune, close leaves, branch
+        // 4. prune, close leaves, choose the branching variable, branch
+        std::vector<int> br;          // batch indices of the nodes to branch
+        std::vector<Node<T>> kids;
+        std::vector<int> rule0;       // their max-range variable
         for (int b : live) {
             Node<T> &nd = batch[b];
             if (nd.key >= prune_threshold()) continue;
             T *lo = h_lo2 + (size_t)b * KD, *hi = h_hi2 + (size_t)b * KD;
-            bool leaf = h_st[b] == 2;
+            const bool leaf = h_st[b] == 2;
             if (use_sb && !leaf) {
                 // symmetry breaking mu^1_1 <= ... <= mu^K_1 (Section 4.1.3)
                 for (int k = 1; k < K; ++k)
@@ -301,29 +442,136 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                     if (lo[k * D] > hi[k * D]) empty = true;
                 if (empty) continue;
             }
-            if (log)
-                fprintf(log, "{\"id\":%lld,\"parent\":%lld,\"depth\":%d,\"lb\":%.17g,\"alpha\":%.17g,\"status\":%d}\n",
-                        (long long)nd.id, (long long)nd.parent, nd.depth, nd.key, alpha, (int)h_st[b]);
             if (leaf) continue;
-            int bi = -1;
-            double br = 0.0;
-            for (int i = 0; i < KD; ++i) {
-                const double r = (double)hi[i] - (double)lo[i];
-                if (r > br) { br = r; bi = i; }
-            }
+            const int bi = rule_max_range<T>(lo, hi, KD);
             if (bi < 0) {
                 // every box became a point after symmetry breaking: visit again
                 Node<T> again;
                 again.lo.assign(lo, lo + KD);
                 again.hi.assign(hi, hi + KD);
                 again.key = nd.key;
+                again.pkey = nd.key;
                 again.id = next_id++;
                 again.parent = nd.id;
                 again.depth = nd.depth + 1;
+                again.group = nd.group;
                 heap.push_back(std::move(again));
                 std::push_heap(heap.begin(), heap.end(), cmp);
                 continue;
             }
+            br.push_back(b);
+            rule0.push_back(bi);
+        }
+        const int NB = (int)br.size();
+        std::vector<int> rule1(NB, -1), choice(rule0);
+        std::vector<float> prio(NB, 0.f);
+        std::vector<int8_t> lab(NB, 0), lab_mask(NB, 0);
+        const bool want_feat = scorer != nullptr || log != nullptr;
+        if (NB > 0 && (want_feat || (log && o.log_labels))) {
+            // coordinates of each node's lower-bound sample, for rule 1
+            std::vector<int64_t> ids(NB);
+            for (int i = 0; i < NB; ++i) ids[i] = h_arg[br[i]];
+            KC_CUDA(c, cudaMemcpyAsync(d_sets, ids.data(), (size_t)NB * 8, cudaMemcpyHostToDevice, c->stream));
+            gather_points_kernel<T><<<(NB * D + 255) / 256, 256, 0, c->stream>>>(
+                static_cast<const T *>(c->X), c->ldx, D, d_sets, NB, d_pts);
+            KC_TRY(after_launch(c, "gather points"));
+            KC_CUDA(c, cudaMemcpyAsync(h_pts.data(), d_pts, (size_t)NB * D * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+            KC_CUDA(c, cudaStreamSynchronize(c->stream));
+            for (int i = 0; i < NB; ++i) {
+                const int b = br[i];
+                rule1[i] = rule_argmax_gap<T>(h_lo2 + (size_t)b * KD, h_hi2 + (size_t)b * KD, &h_pts[(size_t)i * D], K, D);
+                // node features (the scorer's 12 inputs)
+                const Node<T> &nd = batch[b];
+                const T *lo = h_lo2 + (size_t)b * KD, *hi = h_hi2 + (size_t)b * KD;
+                float *f = &h_feat[(size_t)i * 12];
+                double cnt = 0.0, lmean = 0.0, lmax = -1e300, lmin = 1e300, zero = 0.0;
+                for (int k = 0; k < K; ++k) cnt += (double)h_cnt[(size_t)b * K + k];
+                for (int k = 0; k < K; ++k)
+                    for (int a2 = 0; a2 < D; ++a2) {
+                        const double r = (double)hi[k * D + a2] - (double)lo[k * D + a2];
+                        const double lr = std::log2(r / range0[a2] + 9.094947017729282e-13) / 40.0;
+                        lmean += lr;
+                        lmax = std::max(lmax, lr);
+                        lmin = std::min(lmin, lr);
+                        if (!(r > 0)) zero += 1.0;
+                    }
+                lmean /= KD;
+                const double al = alpha > 0 ? alpha : 1.0;
+                f[0] = (float)std::min(2.0, nd.key / al);
+                f[1] = (float)std::max(-1.0, std::min(1.0, (alpha - nd.key) / al));
+                f[2] = (float)(std::log2(1.0 + nd.depth) / 8.0);
+                f[3] = (float)(std::log10(1.0 + cnt) / std::log10(1.0 + (double)K * c->N));
+                f[4] = (float)(std::log10(1.0 + (double)cur.n) / std::log10(1.0 + (double)c->N));
+                f[5] = (float)lmean;
+                f[6] = (float)lmax;
+                f[7] = (float)lmin;
+                f[8] = (float)(zero / KD);
+                f[9] = seeds_found ? 1.f : 0.f;
+                f[10] = std::isfinite(h_ub[b]) ? (float)std::max(-1.0, std::min(1.0, (h_ub[b] - alpha) / al)) : 1.f;
+                f[11] = (float)std::max(0.0, std::min(1.0, (nd.key - nd.pkey) / al));
+            }
+            if (scorer) {
+                KC_CUDA(c, cudaMemcpyAsync(d_feat, h_feat.data(), (size_t)NB * 12 * 4, cudaMemcpyHostToDevice, c->stream));
+                KC_TRY(mlp_forward_device(scorer, d_feat, NB, d_out, c->stream));
+                c->launches += 1;
+                KC_CUDA(c, cudaMemcpyAsync(h_out.data(), d_out, (size_t)NB * 2 * 4, cudaMemcpyDeviceToHost, c->stream));
+                KC_CUDA(c, cudaStreamSynchronize(c->stream));
+                for (int i = 0; i < NB; ++i) {
+                    prio[i] = h_out[(size_t)i * 2];
+                    if (h_out[(size_t)i * 2 + 1] > 0.f && rule1[i] >= 0) choice[i] = rule1[i];
+                }
+            }
+            if (log && o.log_labels) {
+                // strong-branching labels: the smaller child bound under each rule
+                int nl = 0;
+                std::vector<int> li;
+                for (int i = 0; i < NB; ++i) {
+                    if (rule1[i] < 0 || rule1[i] == rule0[i]) continue;
+                    const int b = br[i];
+                    const T *lo = h_lo2 + (size_t)b * KD, *hi = h_hi2 + (size_t)b * KD;
+                    for (int r = 0; r < 2; ++r) {
+                        const int v = r == 0 ? rule0[i] : rule1[i];
+                        T m, succ;
+                        split_point<T>(lo[v], hi[v], &m, &succ);
+                        for (int side = 0; side < 2; ++side) {
+                            T *cl = &h_llo[(size_t)nl * KD], *ch = &h_lhi[(size_t)nl * KD];
+                            std::memcpy(cl, lo, KD * sizeof(T));
+                            std::memcpy(ch, hi, KD * sizeof(T));
+                            if (side == 0) ch[v] = m;
+                            else cl[v] = succ;
+                            ++nl;
+                        }
+                    }
+                    li.push_back(i);
+                }
+                if (nl > 0) {
+                    KC_CUDA(c, cudaMemcpyAsync(d_llo, h_llo.data(), (size_t)nl * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+                    KC_CUDA(c, cudaMemcpyAsync(d_lhi, h_lhi.data(), (size_t)nl * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+                    KC_TRY(launch_lower_bounds_view(c, cur, d_llo, d_lhi, nl, d_llb, nullptr, nullptr, 0));
+                    KC_CUDA(c, cudaMemcpyAsync(h_llb.data(), d_llb, (size_t)nl * 8, cudaMemcpyDeviceToHost, c->stream));
+                    KC_CUDA(c, cudaStreamSynchronize(c->stream));
+                    for (size_t q = 0; q < li.size(); ++q) {
+                        const double r0 = std::min(h_llb[4 * q], h_llb[4 * q + 1]);
+                        const double r1 = std::min(h_llb[4 * q + 2], h_llb[4 * q + 3]);
+                        lab[li[q]] = r1 > r0 ? 1 : 0;
+                        lab_mask[li[q]] = 1;
+                    }
+                }
+            }
+        }
+        for (int i = 0; i < NB; ++i) {
+            const int b = br[i];
+            Node<T> &nd = batch[b];
+            const T *lo = h_lo2 + (size_t)b * KD, *hi = h_hi2 + (size_t)b * KD;
+            if (log) {
+                fprintf(log, "{\"id\":%lld,\"parent\":%lld,\"depth\":%d,\"lb\":%.17g,\"alpha\":%.17g,\"rule\":%d,"
+                             "\"rule0\":%d,\"rule1\":%d,\"label\":%d,\"label_mask\":%d,\"feat\":[",
+                        (long long)nd.id, (long long)nd.parent, nd.depth, nd.key, alpha, choice[i] == rule0[i] ? 0 : 1,
+                        rule0[i], rule1[i], (int)lab[i], (int)lab_mask[i]);
+                for (int q = 0; q < 12; ++q) fprintf(log, q ? ",%.8g" : "%.8g", (double)h_feat[(size_t)i * 12 + q]);
+                fprintf(log, "]}\n");
+            }
+            const int bi = choice[i];
             T m, succ;
             split_point<T>(lo[bi], hi[bi], &m, &succ);
             for (int side = 0; side < 2; ++side) {
@@ -333,29 +581,98 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 if (side == 0) ch.hi[bi] = m;
                 else ch.lo[bi] = succ;
                 ch.key = nd.key;
+                ch.pkey = nd.key;
+                ch.prio = prio[i];
                 ch.id = next_id++;
                 ch.parent = nd.id;
                 ch.depth = nd.depth + 1;
+                ch.group = ch.depth <= 8 ? ch.id : nd.group;
+                kids.push_back(std::move(ch));
+            }
+        }
+        // bound the children as they are created (Algorithm 1, Bounding); only
+        // those below the incumbent enter the open set
+        for (size_t k0 = 0; k0 < kids.size(); k0 += (size_t)Bmax) {
+            const int nk = (int)std::min(kids.size() - k0, (size_t)Bmax);
+            for (int q = 0; q < nk; ++q) {
+                std::memcpy(h_lo + (size_t)q * KD, kids[k0 + q].lo.data(), KD * sizeof(T));
+                std::memcpy(h_hi + (size_t)q * KD, kids[k0 + q].hi.data(), KD * sizeof(T));
+            }
+            KC_CUDA(c, cudaMemcpyAsync(d_lo, h_lo, (size_t)nk * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+            KC_CUDA(c, cudaMemcpyAsync(d_hi, h_hi, (size_t)nk * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+            KC_TRY(launch_lower_bounds_view(c, cur, d_lo, d_hi, nk, d_lb, d_raw, nullptr, 0));
+            KC_CUDA(c, cudaMemcpyAsync(h_lb, d_lb, (size_t)nk * 8, cudaMemcpyDeviceToHost, c->stream));
+            KC_CUDA(c, cudaMemcpyAsync(h_raw.data(), d_raw, (size_t)nk * 8, cudaMemcpyDeviceToHost, c->stream));
+            KC_CUDA(c, cudaStreamSynchronize(c->stream));
+            amb.clear();
+            for (int q = 0; q < nk; ++q) {
+                kids[k0 + q].key = std::max(kids[k0 + q].key, h_lb[q]);
+                if (ambiguous(kids[k0 + q].key, h_raw[q])) amb.push_back(q);
+            }
+            if (!amb.empty()) {
+                KC_TRY(refine_nodes(cur, h_lo, h_hi, h_raw.data()));
+                for (size_t i = 0; i < amb.size(); ++i)
+                    kids[k0 + amb[i]].key = std::max(kids[k0 + amb[i]].key, h_ref[i]);
+                refined += (int64_t)amb.size();
+            }
+            for (int q = 0; q < nk; ++q) {
+                Node<T> &ch = kids[k0 + q];
+                ++created;
+                if (ch.key >= prune_threshold()) continue;
                 heap.push_back(std::move(ch));
                 std::push_heap(heap.begin(), heap.end(), cmp);
             }
         }
+        kids.clear();
 
+        if (o.verbose) { prof[3] += now_s() - tA; tA = now_s(); }
         // 5. sample reduction against the hull of the open nodes (Algorithm 5)
         if (o.i_sr > 0 && batches % o.i_sr == 0 && !heap.empty() && heap.front().key < prune_threshold()) {
-            std::vector<T> hlo(KD), hhi(KD);
-            for (int i = 0; i < KD; ++i) { hlo[i] = heap[0].lo[i]; hhi[i] = heap[0].hi[i]; }
-            for (const auto &nd : heap)
-                for (int i = 0; i < KD; ++i) {
-                    hlo[i] = std::min(hlo[i], nd.lo[i]);
-                    hhi[i] = std::max(hhi[i], nd.hi[i]);
+            // one hull box per group of open nodes (a group = the descendants of
+            // one node at depth 8): every node's box lies inside its group's
+            // hull, so redundancy against the hulls implies it against the nodes
+            std::vector<int64_t> gid;
+            std::vector<T> hlo, hhi;
+            {
+                std::vector<std::pair<int64_t, int>> order;
+                order.reserve(heap.size());
+                for (int i = 0; i < (int)heap.size(); ++i) order.push_back({heap[i].group, i});
+                std::sort(order.begin(), order.end());
+                for (size_t q = 0; q < order.size(); ++q) {
+                    const Node<T> &nd = heap[order[q].second];
+                    if (q == 0 || order[q].first != order[q - 1].first) {
+                        gid.push_back(order[q].first);
+                        hlo.insert(hlo.end(), nd.lo.begin(), nd.lo.end());
+                        hhi.insert(hhi.end(), nd.hi.begin(), nd.hi.end());
+                    } else {
+                        T *gl = &hlo[hlo.size() - KD], *gh = &hhi[hhi.size() - KD];
+                        for (int i = 0; i < KD; ++i) {
+                            gl[i] = std::min(gl[i], nd.lo[i]);
+                            gh[i] = std::max(gh[i], nd.hi[i]);
+                        }
+                    }
                 }
+            }
+            int G = (int)gid.size();
+            if (G > Bmax) {
+                // too many groups for the batch buffers: merge neighbours pairwise
+                const int f = (G + Bmax - 1) / Bmax;
+                int w = 0;
+                for (int g = 0; g < G; g += f, ++w) {
+                    for (int i = 0; i < KD; ++i) { hlo[(size_t)w * KD + i] = hlo[(size_t)g * KD + i]; hhi[(size_t)w * KD + i] = hhi[(size_t)g * KD + i]; }
+                    for (int g2 = g + 1; g2 < std::min(G, g + f); ++g2)
+                        for (int i = 0; i < KD; ++i) {
+                            hlo[(size_t)w * KD + i] = std::min(hlo[(size_t)w * KD + i], hlo[(size_t)g2 * KD + i]);
+                            hhi[(size_t)w * KD + i] = std::max(hhi[(size_t)w * KD + i], hhi[(size_t)g2 * KD + i]);
+                        }
+                }
+                G = w;
+            }
             const double beta_glob = heap.front().key;
-            // hull boxes and the seed representatives go after the batch boxes
-            std::memcpy(h_lo, hlo.data(), KD * sizeof(T));
-            std::memcpy(h_hi, hhi.data(), KD * sizeof(T));
-            KC_CUDA(c, cudaMemcpyAsync(d_lo, h_lo, KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-            KC_CUDA(c, cudaMemcpyAsync(d_hi, h_hi, KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+            std::memcpy(h_lo, hlo.data(), (size_t)G * KD * sizeof(T));
+            std::memcpy(h_hi, hhi.data(), (size_t)G * KD * sizeof(T));
+            KC_CUDA(c, cudaMemcpyAsync(d_lo, h_lo, (size_t)G * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+            KC_CUDA(c, cudaMemcpyAsync(d_hi, h_hi, (size_t)G * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
             const int64_t ncur = cur.n;
             KC_TRY(ensure(c, sb.mask, (size_t)ncur + 256));
             KC_TRY(ensure(c, sb.counts, (size_t)compact_blocks(ncur) * 4 + 4096));
@@ -367,11 +684,17 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             const void *repx = nullptr;
             const int *nreps = nullptr;
             if (seeds_found) {
-                KC_TRY(launch_gather_reps(c, 1, 1, seeds_dev, d_lo2, reinterpret_cast<int *>(d_sets)));
+                // the seeds are the assigned samples known in every node: one
+                // representative per cluster, the same for every group
+                std::vector<int64_t> rp((size_t)G * K);
+                for (int g = 0; g < G; ++g)
+                    for (int k = 0; k < K; ++k) rp[(size_t)g * K + k] = inc_seeds[k];
+                KC_CUDA(c, cudaMemcpyAsync(d_sets, rp.data(), rp.size() * 8, cudaMemcpyHostToDevice, c->stream));
+                KC_TRY(launch_gather_reps(c, G, 1, d_sets, d_lo2, reinterpret_cast<int *>(d_llb)));
                 repx = d_lo2;
-                nreps = reinterpret_cast<const int *>(d_sets);
+                nreps = reinterpret_cast<const int *>(d_llb);
             }
-            KC_TRY(launch_sample_reduction_view(c, cur, d_lo, d_hi, 1, repx, nreps, 1, beta_glob, alpha, mask,
+            KC_TRY(launch_sample_reduction_view(c, cur, d_lo, d_hi, G, repx, nreps, 1, beta_glob, alpha, mask,
                                                 n_keep_dev));
             unsigned long long n_keep = 0;
             KC_CUDA(c, cudaMemcpyAsync(&n_keep, n_keep_dev, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -393,8 +716,22 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 ping = nxt;
             }
         }
+        if (o.verbose) {
+            KC_CUDA(c, cudaStreamSynchronize(c->stream));
+            prof[4] += now_s() - tA;
+            tA = now_s();
+            if (batches % 100 == 0)
+                fprintf(stderr, "[kc_solve] batch %lld visits %lld open %zu alpha %.17g beta %.17g active %lld\n",
+                        (long long)batches, (long long)visits, heap.size(), alpha,
+                        heap.empty() ? alpha : heap.front().key, (long long)cur.n);
+        }
     }
     if (log) fclose(log);
+    if (o.verbose)
+        fprintf(stderr, "[kc_solve] seconds: tighten %.3f, upper bounds %.3f, branch+child bounds %.3f, "
+                        "sample reduction %.3f; batches %lld, visits %lld, created %lld, refined %lld\n",
+                prof[1], prof[2], prof[3], prof[4], (long long)batches, (long long)visits, (long long)created,
+                (long long)refined);
 
     // ---- certificate: the incumbent's objective over all N samples in double
     KC_CUDA(c, cudaMemcpyAsync(T_dev, inc.data(), K * 8, cudaMemcpyHostToDevice, c->stream));
@@ -513,6 +850,13 @@ kc_status kc_sample_reduction(kc_ctx *c, const void *lo, const void *hi, int32_t
     return KC_OK;
 }
 
+kc_status kc_set_scorer(kc_ctx *c, kc_mlp *m)
+{
+    if (!c) return KC_EINVAL;
+    c->scorer = m;
+    return KC_OK;
+}
+
 void kc_solve_defaults(kc_solve_opts *o)
 {
     if (!o) return;
@@ -534,7 +878,8 @@ kc_status kc_solve(kc_ctx *c, double tol, const kc_solve_opts *opt, kc_result *o
     if (tol >= 0) o.tol = tol;
     if (!(o.tol >= 0.0) || o.tol >= 1.0) return set_err(c, KC_EINVAL, "kc_solve: tol must be in [0, 1)");
     if (o.batch < 0 || o.batch > 4096) return set_err(c, KC_EINVAL, "kc_solve: batch must be in [0, 4096]");
-    if (o.order != 0) return set_err(c, KC_EINVAL, "kc_solve: learned ordering needs scorer weights");
+    if (o.order != 0 && o.order != 1) return set_err(c, KC_EINVAL, "kc_solve: order must be 0 or 1");
+    if (o.order == 1 && !c->scorer) return set_err(c, KC_EINVAL, "kc_solve: order = 1 needs kc_set_scorer");
     std::memset(out, 0, sizeof(*out));
     if (c->dt == KC_F32) return solve_impl<float>(c, o, out);
     return solve_impl<double>(c, o, out);

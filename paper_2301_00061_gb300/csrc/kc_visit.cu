@@ -7,8 +7,9 @@
 // register accumulators, then reduces them across the warp once per (node,
 // tile) and merges them into global accumulators with atomics.  Extremes that
 // must also name a sample (the representatives) are (value, position) keys:
-// packed into 64 bits for float data, two 64-bit words merged by a 128-bit
-// compare-and-swap for double data.
+// packed into 64 bits and merged with 64-bit atomics for float data; for
+// double data (two words) the kernels run as one CTA whose warps own disjoint
+// nodes, and the owning lane merges them without atomics.
 //
 // Float data take every exclusion only where the float evaluation proves it:
 // a distance d evaluated as d' satisfies d' (1 - g) <= d <= d' / (1 - g), so
@@ -50,18 +51,6 @@ struct K128 {
     unsigned long long hi, lo;
 };
 
-__device__ __forceinline__ K128 cas128(K128 *p, K128 cmp, K128 val)
-{
-    K128 old;
-    asm volatile(
-        "{ .reg .b128 c, v, o; mov.b128 c, {%2, %3}; mov.b128 v, {%4, %5};"
-        " atom.global.cas.b128 o, [%6], c, v; mov.b128 {%0, %1}, o; }"
-        : "=l"(old.lo), "=l"(old.hi)
-        : "l"(cmp.lo), "l"(cmp.hi), "l"(val.lo), "l"(val.hi), "l"(p)
-        : "memory");
-    return old;
-}
-
 template <>
 struct Key<double> {
     using K = K128;
@@ -77,18 +66,14 @@ struct Key<double> {
     __device__ static double vmax(const K &k) { return unord_f64(k.hi); }
     __device__ static double vmin(const K &k) { return unord_f64(~k.hi); }
     __device__ static uint32_t pos(const K &k) { return (uint32_t)(0xFFFFFFFFull - k.lo); }
-    // Lock-free max; every failed exchange means another update succeeded, so
-    // the loop ends; the iteration cap only guards against a broken invariant.
-    __device__ static void atomic_max(K *p, const K &v, unsigned *err)
+    // Double keys do not fit one 64-bit atomic.  The double-data kernels run
+    // as a single CTA in which node b belongs to warp b % 8 alone, so lane 0
+    // of that warp is the only writer of the node's keys: a plain
+    // read-compare-write merge is race-free there.
+    __device__ static void atomic_max(K *p, const K &v, unsigned *)
     {
-        K cur = none();
-        for (int it = 0; it < (1 << 20); ++it) {
-            if (!gt(v, cur)) return;
-            const K old = cas128(p, cur, v);
-            if (old.hi == cur.hi && old.lo == cur.lo) return;
-            cur = old;
-        }
-        atomicOr(err, 2u);
+        const K cur = *p;
+        if (gt(v, cur)) *p = v;
     }
 };
 
@@ -880,6 +865,7 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     const int64_t tilesA = (v.n + tileA - 1) / tileA;
     auto kA = visit_a_kernel<T, KM, DM>;
     KC_TRY(grid_of(c, kA, smemA, tilesA, &gA));
+    if (sizeof(T) == 8) gA = 1;   // single-writer key merge (see Key<double>)
     if (v.n > 0) {
         kA<<<gA, kThreads, smemA, c->stream>>>(static_cast<const T *>(v.X), v.ld, v.n, tileA, lo, hi, B, K_, D, alpha,
                                               mg, lbkey, amax, amin, flags);
@@ -905,6 +891,7 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     int gB = 1;
     auto kB = visit_b_kernel<T, KM, DM, RMX>;
     KC_TRY(grid_of(c, kB, smemB, (v.n + tileB - 1) / tileB, &gB));
+    if (sizeof(T) == 8) gB = 1;   // single-writer key merge (see Key<double>)
     if (v.n > 0) {
         kB<<<gB, kThreads, smemB, c->stream>>>(static_cast<const T *>(v.X), v.ld, v.n, tileB, B, K_, D, RM, blo, bhi,
                                               repx, nreps, have, alpha, mg, cnt, smax, smin, jmax, jmin, cand, flags);
@@ -933,6 +920,12 @@ kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const vo
         return set_err(c, KC_EINVAL, "kc_tighten: supported for D <= 8 and K <= 8 (got D=%d, K=%d)", c->D, c->K);
     const int cap = ball_cap > 0 ? ball_cap : 50;
     if (c->dt == KC_F32) {
+        if (c->K == 3 && c->D == 3)
+            return tighten_impl<float, 3, 3, 7>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
+                                                lb, lb_raw, lbarg, status, vs);
+        if (c->K == 3 && c->D == 4)
+            return tighten_impl<float, 3, 4, 9>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
+                                                lb, lb_raw, lbarg, status, vs);
         if (c->K <= 4 && c->D <= 2)
             return tighten_impl<float, 4, 2, 5>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
                                                 lb, lb_raw, lbarg, status, vs);

@@ -1,0 +1,83 @@
+"""The learned node scorer's CUDA kernels against the FP64 oracle
+(oracle/mlp.py) on the same bfloat16-rounded weights, its training, and the
+solver with learned ordering (the certified optimum must not change)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2301_00061_gb300 import KCenter, Scorer  # noqa: E402
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, 12)).astype(np.float32)
+    T = np.stack([rng.normal(size=n), (rng.uniform(size=n) < 0.4)], 1).astype(np.float32)
+    M = (rng.uniform(size=(n, 2)) < 0.8).astype(np.float32)
+    return X, T, M
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_forward_matches_oracle(seed):
+    theta = mlp.init_params(seed)
+    rng = np.random.default_rng(seed)
+    theta[mlp.NPARAM - 130:] += rng.normal(size=130).astype(np.float32) * 0.1   # non-zero biases too
+    X, _, _ = _data(1000, seed)
+    sc = Scorer(theta)
+    y = sc.forward(X)
+    ref, _ = mlp.forward(theta, X)
+    assert np.max(np.abs(y - ref)) <= 1e-4 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 777])
+def test_gradient_matches_oracle(n):
+    theta = mlp.init_params(3)
+    X, T, M = _data(n, n)
+    sc = Scorer(theta)
+    loss, g = sc.grad(X, T, M)
+    loss_ref, g_ref = mlp.grad(theta, X, T, M)
+    assert abs(loss - loss_ref) <= 1e-5 * max(1.0, abs(loss_ref))
+    scale = np.max(np.abs(g_ref))
+    assert np.max(np.abs(g - g_ref)) <= 2e-4 * scale + 1e-7, np.max(np.abs(g - g_ref)) / scale
+
+
+def test_training_fits_a_teacher():
+    """Targets from a fixed random teacher network: GPU Adam training must cut
+    the loss well below its starting value."""
+    teacher = mlp.init_params(11)
+    X, _, M = _data(4096, 5)
+    y, _ = mlp.forward(teacher, X)
+    T = np.stack([y[:, 0], (y[:, 1] > 0)], 1).astype(np.float32)
+    M[:] = 1.0
+    student = mlp.init_params(12)
+    l0 = mlp.loss(student, X, T, M)
+    sc = Scorer(student)
+    l1 = sc.train(X, T, M, epochs=40, batch=128, lr=3e-3, seed=1)
+    assert l1 < 0.35 * l0, (l0, l1)
+    # the trained parameters reproduce the reported loss in the oracle
+    assert abs(mlp.loss(sc.params(), X, T, M) - l1) <= 1e-3 * max(1.0, l1)
+
+
+def test_learned_order_keeps_the_optimum():
+    """Any scorer (here an untrained one) only changes the order of nodes and
+    the branching variable; every prune still uses the exact bound."""
+    for seed in (0, 1):
+        X = synth.gaussian_mixture(2_500, 2, (0.4, 0.3, 0.3), (1.0,) * 3, (1.0,) * 3, 10.0, seed, dtype=np.float32)
+        theta = mlp.init_params(seed)
+        theta[-1] = 5.0 if seed == 0 else -5.0            # rule logit forced either way
+        kc = KCenter(torch.from_numpy(X).cuda(), 3)
+        sc = Scorer(theta)
+        kc.set_scorer(sc)
+        g1 = kc.solve(tol=1e-12, order=1)
+        g0 = kc.solve(tol=1e-12, order=0)
+        r = oracle.solve(X, 3, tol=1e-12)
+        assert abs(g1["objective"] - r["objective"]) <= 1e-12 * r["objective"]
+        assert abs(g0["objective"] - r["objective"]) <= 1e-12 * r["objective"]
