@@ -371,11 +371,11 @@ static int build_reps(int64_t seed_k, const int64_t *amin_idx, const int64_t *am
  *   over j in J_A^k, r = sqrt(alpha) rounded up, bounds rounded outward.
  *   With seeds, a node whose box k is farther than alpha from seed k holds
  *   no such solution either (infeasible).
- * Step B (Algorithm 3, sample-based, when every J_A^k is non-empty): every
- *   active sample (the sample-based loop of Algorithm 3 has no "unassigned"
- *   guard) is excluded from k when some representative j of k has
- *   ||x_s - x_j||^2 > 4 alpha (Lemma 2); exactly one cluster left assigns it
- *   (J_B), none left makes the node infeasible.
+ * Step B (Algorithm 3, sample-based, when every J_A^k is non-empty): a
+ *   sample not assigned in step A (assigned samples help pre-assign the other
+ *   samples, Section 4.1.1) is excluded from k when some representative j of
+ *   k has ||x_s - x_j||^2 > 4 alpha (Lemma 2); exactly one cluster left
+ *   assigns it (J_B), none left makes the node infeasible.
  * Ball-based BT and "centers on samples" (Algorithm 4): S_+^k = active
  *   samples in M'^k within sqrt(alpha) of every representative of k;
  *   M^k_hat = bbox(S_+^k) cap box-BT over J_B^k.
@@ -482,7 +482,7 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
     for (int64_t s = 0; s < N; ++s) {
         if (!is_active(active, s)) continue;
         const double *x = X + s * D;
-        if (all_have) {
+        if (all_have && asg[s] < 0) {
             int left = 0, kk = -1;
             for (int k = 0; k < K; ++k) {
                 int excl = 0;

@@ -188,6 +188,9 @@ struct Margins {
     float defl, infl, slack;     // float evaluation of a D-term distance
     float alpha_up, four_up;     // alpha and 4 alpha rounded up to float
     float beta_dn;               // beta_glob rounded down to float
+    // single-compare proofs: a float distance d' > t_alpha proves d > alpha,
+    // d' > t_four proves d > 4 alpha (t = RU((RU(target) + slack) / defl * (1 + 1e-6)))
+    float t_alpha, t_four;
 };
 
 // ------------------------------------------------------------ pass A
@@ -264,7 +267,7 @@ visit_a_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, const T
                         bool excl;
                         if constexpr (F32) {
                             v = box_dist_pad<DM>(px, bx[k]);
-                            excl = proved_gt(v, mg.defl, mg.slack, mg.alpha_up);
+                            excl = v > mg.t_alpha;
                         } else {
                             v = box_dist_f64<DM>(reinterpret_cast<const double *>(x), blo[k], bhi[k], D);
                             excl = v > alpha;
@@ -433,22 +436,38 @@ __global__ void finalize_a_kernel(int B, int K, int D, const T *__restrict__ lo,
 }
 
 // ------------------------------------------------------------ pass B
+//
+// Only two kinds of samples need representative distances: samples that the
+// center-based rule left unassigned (the sample-based rule tests them against
+// every representative) and samples inside some box M'^k (the ball test of
+// cluster k).  Each warp first flags its slice of the tile and compacts the
+// flagged samples into a list in shared memory, then processes the list with
+// every lane busy.
+
+constexpr int kSub = 256;   // samples flagged per warp before processing
 
 template <typename T, int KM, int DM, int RMX>
 __global__ void __launch_bounds__(kThreads)
 visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, int K, int D, int RM,
-               const T *__restrict__ blo, const T *__restrict__ bhi, const T *__restrict__ repx,
-               const int *__restrict__ nreps, const int *__restrict__ allhave, double alpha, Margins mg,
-               unsigned long long *__restrict__ cnt, OrdT<T> *__restrict__ smax, OrdT<T> *__restrict__ smin,
-               OrdT<T> *__restrict__ jmax, OrdT<T> *__restrict__ jmin, typename Key<T>::K *__restrict__ cand,
-               unsigned *__restrict__ flags)
+               const T *__restrict__ lo_in, const T *__restrict__ hi_in, const T *__restrict__ blo,
+               const T *__restrict__ bhi, const T *__restrict__ repx, const int *__restrict__ nreps,
+               const int *__restrict__ allhave, double alpha, Margins mg, const int64_t *__restrict__ seeds,
+               const uint32_t *__restrict__ ids, unsigned long long *__restrict__ cnt,
+               OrdT<T> *__restrict__ smax, OrdT<T> *__restrict__ smin, OrdT<T> *__restrict__ jmax,
+               OrdT<T> *__restrict__ jmin, typename Key<T>::K *__restrict__ cand, unsigned *__restrict__ flags)
 {
     using KT = Key<T>;
     using KY = typename KT::K;
     constexpr bool F32 = sizeof(T) == 4;
+    constexpr int DH = (DM + 1) / 2;
+    int64_t seed_id[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) seed_id[k] = (seeds && k < K) ? seeds[k] : -1;
     extern __shared__ __align__(16) unsigned char smem[];
-    T *tx = reinterpret_cast<T *>(smem);                       // [D][tile]
+    T *tx = reinterpret_cast<T *>(smem);                                        // [D][tile]
+    uint32_t *lists = reinterpret_cast<uint32_t *>(tx + (size_t)D * tile);      // [warps][kSub]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *list = lists + warp * kSub;
     const double four_alpha = 4.0 * alpha;
 
     for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
@@ -460,6 +479,9 @@ visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, 
         }
         __syncthreads();
         for (int b = warp; b < B; b += NWV) {
+            // node b: input boxes (center-based status), box-BT boxes, midpoints
+            uint64_t bx[KM][DM];
+            double ilo[KM][DM], ihi[KM][DM];
             T l[KM][DM], h[KM][DM], mid[KM][DM];
             int nr[KM];
 #pragma unroll
@@ -469,6 +491,8 @@ visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, 
                 for (int a = 0; a < DM; ++a) {
                     const bool in = k < K && a < D;
                     const size_t o = ((size_t)b * K + k) * D + a;
+                    if constexpr (F32) bx[k][a] = in ? pk((float)lo_in[o], -(float)hi_in[o]) : pk(0.f, -0.f);
+                    else { ilo[k][a] = in ? (double)lo_in[o] : 0.0; ihi[k][a] = in ? (double)hi_in[o] : 0.0; }
                     l[k][a] = in ? blo[o] : T(0);
                     h[k][a] = in ? bhi[o] : T(0);
                     if constexpr (F32) mid[k][a] = in ? (float)(0.5 * ((double)l[k][a] + (double)h[k][a])) : 0.f;
@@ -489,78 +513,126 @@ visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, 
                 for (int a = 0; a < DM; ++a) { c_smax[k][a] = -INF; c_smin[k][a] = INF; c_jmax[k][a] = -INF; c_jmin[k][a] = INF; }
             }
             bool infeasible = false;
-            for (int j = lane; j < tn; j += 32) {
-                const uint32_t pos = (uint32_t)(base + j);
-                T x[DM];
+            for (int sub = 0; sub < tn; sub += kSub) {
+                const int se = min(tn, sub + kSub);
+                // phase 1: flag the samples that need representative distances
+                int count = 0;
+                for (int j0 = sub; j0 < se; j0 += 32) {
+                    const int j = j0 + lane;
+                    uint32_t fl = 0u;
+                    if (j < se) {
+                        T x[DM];
 #pragma unroll
-                for (int a = 0; a < DM; ++a) x[a] = a < D ? tx[(size_t)a * tile + j] : T(0);
-                uint64_t px[(DM + 1) / 2];
-                if constexpr (F32) {
-#pragma unroll
-                    for (int p = 0; p < (DM + 1) / 2; ++p)
-                        px[p] = pk(x[2 * p], 2 * p + 1 < DM ? x[2 * p + 1] : 0.f);
-                }
-                // distances to every representative; far4: proved > 4 alpha, far1: proved > alpha
-                unsigned long long far4 = 0ull, far1 = 0ull;   // bit k*RMX + r
-#pragma unroll
-                for (int k = 0; k < KM; ++k)
-#pragma unroll
-                    for (int r = 0; r < RMX; ++r)
-                        if (r < nr[k]) {
-                            const T *c = rxb + ((size_t)k * RM + r) * D;
-                            if constexpr (F32) {
-                                uint64_t pc[(DM + 1) / 2];
-#pragma unroll
-                                for (int p = 0; p < (DM + 1) / 2; ++p) {
-                                    const float c0 = 2 * p < D ? c[2 * p] : 0.f;
-                                    const float c1 = 2 * p + 1 < D ? c[2 * p + 1] : 0.f;
-                                    pc[p] = pk(c0, c1);
-                                }
-                                const float d = pt_dist_f32<2 * ((DM + 1) / 2)>(px, pc);
-                                if (proved_gt(d, mg.defl, mg.slack, mg.four_up)) far4 |= 1ull << (k * RMX + r);
-                                if (proved_gt(d, mg.defl, mg.slack, mg.alpha_up)) far1 |= 1ull << (k * RMX + r);
-                            } else {
-                                double cc[DM];
-#pragma unroll
-                                for (int a = 0; a < DM; ++a) cc[a] = a < D ? c[a] : 0.0;
-                                const double d = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), cc, D);
-                                if (d > four_alpha) far4 |= 1ull << (k * RMX + r);
-                                if (d > alpha) far1 |= 1ull << (k * RMX + r);
-                            }
-                        }
-                // sample-based assignment (Algorithm 3, Lemma 2)
-                if (have) {
-                    int left = 0, k1 = -1;
-#pragma unroll
-                    for (int k = 0; k < KM; ++k)
-                        if (k < K) {
-                            const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
-                            if ((far4 & mk) == 0ull) { ++left; k1 = k; }
-                        }
-                    if (left == 0) infeasible = true;
-                    if (left == 1) {
+                        for (int a = 0; a < DM; ++a) x[a] = a < D ? tx[(size_t)a * tile + j] : T(0);
+                        int left = 0;
 #pragma unroll
                         for (int k = 0; k < KM; ++k)
-                            if (k == k1) {
+                            if (k < K) {
+                                bool excl;
+                                if constexpr (F32) {
+                                    uint64_t px[DM];
 #pragma unroll
-                                for (int a = 0; a < DM; ++a) {
-                                    c_jmax[k][a] = x[a] > c_jmax[k][a] ? x[a] : c_jmax[k][a];
-                                    c_jmin[k][a] = x[a] < c_jmin[k][a] ? x[a] : c_jmin[k][a];
+                                    for (int a = 0; a < DM; ++a) px[a] = pk(x[a], -x[a]);
+                                    excl = box_dist_f32<DM>(px, bx[k]) > mg.t_alpha;
+                                } else {
+                                    excl = box_dist_f64<DM>(reinterpret_cast<const double *>(x), ilo[k], ihi[k], D) > alpha;
+                                }
+                                if (!excl) ++left;
+                            }
+                        if (have && left >= 2) {
+                            // the seeds count as assigned in every node
+                            const int64_t id = ids ? (int64_t)ids[base + j] : base + j;
+                            bool is_seed = false;
+#pragma unroll
+                            for (int k = 0; k < KM; ++k)
+                                if (seed_id[k] == id) is_seed = true;
+                            if (!is_seed) fl |= 1u;
+                        }
+#pragma unroll
+                        for (int k = 0; k < KM; ++k)
+                            if (k < K) {
+                                bool inb = true;
+#pragma unroll
+                                for (int a = 0; a < DM; ++a)
+                                    if (a < D && (x[a] < l[k][a] || x[a] > h[k][a])) inb = false;
+                                if (inb) fl |= 2u << k;
+                            }
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, fl != 0u);
+                    if (fl) list[count + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)j | (fl << 16);
+                    count += __popc(bal);
+                }
+                __syncwarp();
+                // phase 2: representative distances of the flagged samples
+                for (int e = lane; e < count; e += 32) {
+                    const uint32_t ent = list[e];
+                    const int j = (int)(ent & 0xFFFFu);
+                    const uint32_t fl = ent >> 16;
+                    const uint32_t pos = (uint32_t)(base + j);
+                    T x[DM];
+#pragma unroll
+                    for (int a = 0; a < DM; ++a) x[a] = a < D ? tx[(size_t)a * tile + j] : T(0);
+                    uint64_t px[DH];
+                    if constexpr (F32) {
+#pragma unroll
+                        for (int p = 0; p < DH; ++p) px[p] = pk(x[2 * p], 2 * p + 1 < DM ? x[2 * p + 1] : 0.f);
+                    }
+                    // distances to the representatives of the clusters that need them
+                    unsigned long long far4 = 0ull, far1 = 0ull;
+#pragma unroll
+                    for (int k = 0; k < KM; ++k) {
+                        const bool need = k < K && ((fl & 1u) || (fl & (2u << k)));
+                        if (!need) continue;
+#pragma unroll
+                        for (int r = 0; r < RMX; ++r)
+                            if (r < nr[k]) {
+                                const T *c = rxb + ((size_t)k * RM + r) * D;
+                                if constexpr (F32) {
+                                    uint64_t pc[DH];
+#pragma unroll
+                                    for (int p = 0; p < DH; ++p)
+                                        pc[p] = pk(2 * p < D ? c[2 * p] : 0.f, 2 * p + 1 < D ? c[2 * p + 1] : 0.f);
+                                    const float d = pt_dist_f32<2 * DH>(px, pc);
+                                    if (d > mg.t_four) far4 |= 1ull << (k * RMX + r);
+                                    if (d > mg.t_alpha) far1 |= 1ull << (k * RMX + r);
+                                } else {
+                                    double cc[DM];
+#pragma unroll
+                                    for (int a = 0; a < DM; ++a) cc[a] = a < D ? c[a] : 0.0;
+                                    const double d = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), cc, D);
+                                    if (d > four_alpha) far4 |= 1ull << (k * RMX + r);
+                                    if (d > alpha) far1 |= 1ull << (k * RMX + r);
                                 }
                             }
                     }
-                }
-                // ball-based tightening and centers on samples (Algorithm 4)
+                    // sample-based assignment of an unassigned sample (Algorithm 3, Lemma 2)
+                    if (fl & 1u) {
+                        int left = 0, k1 = -1;
 #pragma unroll
-                for (int k = 0; k < KM; ++k)
-                    if (k < K) {
-                        bool ok = true;
+                        for (int k = 0; k < KM; ++k)
+                            if (k < K) {
+                                const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
+                                if ((far4 & mk) == 0ull) { ++left; k1 = k; }
+                            }
+                        if (left == 0) infeasible = true;
+                        if (left == 1) {
 #pragma unroll
-                        for (int a = 0; a < DM; ++a)
-                            if (a < D && (x[a] < l[k][a] || x[a] > h[k][a])) ok = false;
-                        const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
-                        if (far1 & mk) ok = false;
-                        if (ok) {
+                            for (int k = 0; k < KM; ++k)
+                                if (k == k1) {
+#pragma unroll
+                                    for (int a = 0; a < DM; ++a) {
+                                        c_jmax[k][a] = x[a] > c_jmax[k][a] ? x[a] : c_jmax[k][a];
+                                        c_jmin[k][a] = x[a] < c_jmin[k][a] ? x[a] : c_jmin[k][a];
+                                    }
+                                }
+                        }
+                    }
+                    // ball-based tightening and centers on samples (Algorithm 4)
+#pragma unroll
+                    for (int k = 0; k < KM; ++k)
+                        if (k < K && (fl & (2u << k))) {
+                            const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
+                            if (far1 & mk) continue;
                             ++c_cnt[k];
 #pragma unroll
                             for (int a = 0; a < DM; ++a) {
@@ -569,17 +641,18 @@ visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, 
                             }
                             T dm;
                             if constexpr (F32) {
-                                uint64_t pm[(DM + 1) / 2];
+                                uint64_t pm[DH];
 #pragma unroll
-                                for (int p = 0; p < (DM + 1) / 2; ++p)
+                                for (int p = 0; p < DH; ++p)
                                     pm[p] = pk(mid[k][2 * p], 2 * p + 1 < DM ? mid[k][2 * p + 1] : 0.f);
-                                dm = pt_dist_f32<2 * ((DM + 1) / 2)>(px, pm);
+                                dm = pt_dist_f32<2 * DH>(px, pm);
                             } else {
                                 dm = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), mid[k], D);
                             }
                             c_cand[k] = kmax<T>(c_cand[k], KT::min_of(dm, pos));
                         }
-                    }
+                }
+                __syncwarp();
             }
             // reduce and merge
 #pragma unroll
@@ -808,6 +881,8 @@ Margins make_margins(kc_ctx *c, double alpha, double beta_glob)
     m.alpha_up = up(alpha);
     m.four_up = up(4.0 * alpha);
     m.beta_dn = dn(beta_glob);
+    m.t_alpha = up(((double)m.alpha_up + (double)m.slack) / (double)m.defl * (1.0 + 1e-6));
+    m.t_four = up(((double)m.four_up + (double)m.slack) / (double)m.defl * (1.0 + 1e-6));
     return m;
 }
 
@@ -887,14 +962,16 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     KC_TRY(after_launch(c, "tighten finalize A"));
     // pass B
     const int tileB = (int)std::max<int64_t>(256, std::min<int64_t>(2048, (32 * 1024) / (D * (int64_t)sizeof(T))) / 32 * 32);
-    const size_t smemB = (size_t)D * tileB * sizeof(T);
+    static_assert(kThreads / 32 * kSub * 4 <= 16 * 1024, "pass B lists");
+    const size_t smemB = (size_t)D * tileB * sizeof(T) + (size_t)NWV * kSub * 4;
     int gB = 1;
     auto kB = visit_b_kernel<T, KM, DM, RMX>;
     KC_TRY(grid_of(c, kB, smemB, (v.n + tileB - 1) / tileB, &gB));
     if (sizeof(T) == 8) gB = 1;   // single-writer key merge (see Key<double>)
     if (v.n > 0) {
-        kB<<<gB, kThreads, smemB, c->stream>>>(static_cast<const T *>(v.X), v.ld, v.n, tileB, B, K_, D, RM, blo, bhi,
-                                              repx, nreps, have, alpha, mg, cnt, smax, smin, jmax, jmin, cand, flags);
+        kB<<<gB, kThreads, smemB, c->stream>>>(static_cast<const T *>(v.X), v.ld, v.n, tileB, B, K_, D, RM, lo, hi, blo,
+                                              bhi, repx, nreps, have, alpha, mg, seeds, v.ids, cnt, smax, smin, jmax, jmin,
+                                              cand, flags);
         KC_TRY(after_launch(c, "tighten pass B"));
     }
     finalize_b_kernel<T><<<(B + 127) / 128, 128, 0, c->stream>>>(B, K_, D, cnt, smax, smin, jmax, jmin, cand, flags,
