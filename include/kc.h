@@ -270,9 +270,11 @@ typedef struct {
     int32_t i_sr;          /* 1: sample reduction every i_sr batches, 0: off */
     int32_t use_bt;        /* 1: assignment + bounds tightening (BB+CF+BT); 0: BB+CF */
     int32_t order;         /* 0: best bound, max-range branching; 1: learned scorer (kc_set_scorer) */
-    int32_t use_graph;     /* 1: replay each batch's kernels as a CUDA graph */
+    int32_t lists;         /* 1: every node keeps its own list of surviving samples (float data, Section
+                              4.2); 0: all nodes of a batch scan one shared sample set */
     int32_t verbose;       /* 0; 1: per-phase timings on stderr */
     int32_t log_labels;    /* 0; 1: the node log also carries strong-branching labels (extra bound passes) */
+    int32_t arena_mb;      /* 0: automatic; device memory (MiB) that holds the per-node lists */
     uint64_t seed;         /* 0: FFT start = seed mod N */
     const char *log_path;  /* NULL, or a file receiving one JSON line per branched node (scorer features) */
 } kc_solve_opts;
@@ -284,11 +286,14 @@ typedef struct {
     int64_t centers[16];   /* K sample indices */
     int64_t nodes;         /* nodes visited */
     int64_t batches;       /* bounding launches */
-    int64_t active_final;  /* samples left after sample reduction */
+    int64_t active_final;  /* samples left after sample reduction (per-node lists: the longest list of
+                              an open node, 0 when none is open) */
     double fft_objective;  /* objective of the root FFT solution */
     double seconds;        /* wall time of the solve */
     int32_t seeds_found;   /* the FFT points were K initial seeds (Section 4.1.1) */
     int32_t status;        /* KC_OK, KC_ETIMEOUT or KC_ELIMIT */
+    int64_t lists_filtered;   /* per-node lists: nodes whose children got a shorter list */
+    int64_t samples_dropped;  /* per-node lists: list entries dropped over the solve */
 } kc_result;
 
 void kc_solve_defaults(kc_solve_opts *opt);

@@ -43,7 +43,8 @@ class SolveOpts(C.Structure):
     _fields_ = [
         ("tol", C.c_double), ("time_limit_s", C.c_double), ("node_limit", C.c_int64),
         ("batch", C.c_int32), ("ball_cap", C.c_int32), ("i_sr", C.c_int32), ("use_bt", C.c_int32),
-        ("order", C.c_int32), ("use_graph", C.c_int32), ("verbose", C.c_int32), ("log_labels", C.c_int32),
+        ("order", C.c_int32), ("lists", C.c_int32), ("verbose", C.c_int32), ("log_labels", C.c_int32),
+        ("arena_mb", C.c_int32),
         ("seed", C.c_uint64),
         ("log_path", C.c_char_p),
     ]
@@ -55,6 +56,7 @@ class Result(C.Structure):
         ("centers", C.c_int64 * 16), ("nodes", C.c_int64), ("batches", C.c_int64),
         ("active_final", C.c_int64), ("fft_objective", C.c_double), ("seconds", C.c_double),
         ("seeds_found", C.c_int32), ("status", C.c_int32),
+        ("lists_filtered", C.c_int64), ("samples_dropped", C.c_int64),
     ]
 
 
@@ -433,4 +435,5 @@ class KCenter:
             "centers": np.array(r.centers[: self.K]), "nodes": r.nodes, "batches": r.batches,
             "active_final": r.active_final, "fft_objective": r.fft_objective, "seconds": r.seconds,
             "seeds_found": bool(r.seeds_found), "status": st,
+            "lists_filtered": r.lists_filtered, "samples_dropped": r.samples_dropped,
         }

@@ -138,4 +138,18 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
+// Work item w of a list batch -> (node, first entry); see ListBatch.
+__device__ __forceinline__ void list_item(const int64_t *__restrict__ tile_prefix, int B, int64_t w, int tile,
+                                          int *b_out, int64_t *start_out)
+{
+    int lo = 0, hi = B;   // largest b with tile_prefix[b] <= w
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tile_prefix[mid] <= w) lo = mid;
+        else hi = mid;
+    }
+    *b_out = lo;
+    *start_out = (int64_t)(w - tile_prefix[lo]) * tile;
+}
+
 }  // namespace kc

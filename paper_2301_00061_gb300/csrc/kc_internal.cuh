@@ -150,6 +150,23 @@ inline View full_view(const kc_ctx *c)
     return v;
 }
 
+// Per-node sample-id lists of a batch of nodes (device arrays).  Nodes that
+// share one list form a group: group g's list is pool[seg_off[g] ..
+// seg_off[g] + seg_n[g]) and its nodes are node_start[g] .. node_start[g + 1]
+// - 1 (node_start NULL: group g is node g alone).  Work item w covers entries
+// [t * list_tile(), (t + 1) * list_tile()) of group g's list, where g is the
+// group with tile_prefix[g] <= w < tile_prefix[g + 1] and t = w - tile_prefix[g];
+// a staged tile serves every node of its group.
+struct ListBatch {
+    const uint32_t *pool = nullptr;
+    const int64_t *seg_off = nullptr;
+    const int64_t *seg_n = nullptr;
+    const int64_t *tile_prefix = nullptr;   // [B + 1]
+    const int *node_start = nullptr;        // [B + 1] or NULL
+    int B = 0;                              // groups
+    int64_t W = 0;                          // tile_prefix[B]
+};
+
 // ----------------------------------------------------------- kernel launchers
 // (implemented in the .cu files; all run on c->stream)
 
@@ -268,5 +285,24 @@ struct Stager {
 
 // Scores B nodes: device features [B][12] -> device outputs [B][2].
 kc_status mlp_forward_device(kc_mlp *m, const float *feats, int B, float *out, cudaStream_t stream);
+
+// ---- per-node sample lists (kc_lists.cu)
+int list_tile();
+kc_status launch_iota(kc_ctx *c, uint32_t *p, int64_t n);
+kc_status launch_copy_segments(kc_ctx *c, const ListBatch &L, uint32_t *dst, const int64_t *dn);
+kc_status launch_seg_lb(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, unsigned long long *keys,
+                        double *lb, double *raw, int64_t *arg);
+kc_status launch_seg_refine(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, const double *raw_host,
+                            float *thr_dev, unsigned long long *vmax, double *out);
+kc_status launch_seg_objective(kc_ctx *c, const ListBatch &L, const int64_t *centers, int B, double alpha_cut,
+                               unsigned long long *keys, unsigned long long *vmax, float *thr, double *val);
+kc_status launch_seg_filter(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B,
+                            const float *beta_dn_dev, double alpha, const void *repx, const int *nreps, int RM,
+                            const int *rmap, uint32_t *out_pool, const int64_t *out_off, unsigned long long *out_n);
+// Tightening of B nodes, each over its own list (float data).
+kc_status launch_tighten_list(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, double alpha,
+                              const int64_t *seeds_dev, int ball_cap, void *lo_out, void *hi_out, int64_t *counts,
+                              int64_t *cand, double *lb, double *lb_raw, int64_t *lbarg, int8_t *status,
+                              VisitScratch *vs);
 
 }  // namespace kc

@@ -23,6 +23,8 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <set>
 #include <vector>
 
 #include "kc_internal.cuh"
@@ -65,6 +67,7 @@ struct Node {
     double pkey = 0.0;       // the parent's bound
     int64_t group = 0;       // its ancestor at depth 8 (itself above that depth)
     float prio = 0.f;        // learned priority (ties of equal keys: smaller first)
+    int list = -1;           // handle of its surviving-sample list (per-node list mode)
 };
 
 template <typename T>
@@ -89,8 +92,107 @@ double sqdist_host(const std::vector<double> &x, const std::vector<double> &y)
     return acc;
 }
 
+// Device arena of per-node sample-id lists (Section 4.2: a sample redundant
+// for both bounds in a node stays redundant in every descendant, so a node's
+// children only need the samples that survive in it).  Lists are immutable
+// and shared by reference: both children of a node hold its filtered list,
+// and a child whose parent could not be filtered (or gained little) holds the
+// parent's list.  Space is managed on the host: best fit over free ranges,
+// coalesced on release.
+struct ListArena {
+    struct Rec {
+        int64_t off = 0, n = 0;
+        int refs = 0;
+    };
+    DevBuf pool;                                   // uint32 sample ids
+    int64_t cap = 0, used = 0, peak = 0;
+    std::map<int64_t, int64_t> by_off;             // free ranges: offset -> length
+    std::set<std::pair<int64_t, int64_t>> by_len;  // (length, offset)
+    std::vector<Rec> recs;
+    std::vector<int> spare;
+
+    uint32_t *ids() const { return static_cast<uint32_t *>(pool.p); }
+    void reset(int64_t capacity)
+    {
+        cap = capacity;
+        used = peak = 0;
+        by_off.clear();
+        by_len.clear();
+        recs.clear();
+        spare.clear();
+        if (cap > 0) put(0, cap);
+    }
+    void put(int64_t off, int64_t len)
+    {
+        by_off[off] = len;
+        by_len.insert({len, off});
+    }
+    void drop(std::map<int64_t, int64_t>::iterator it)
+    {
+        by_len.erase({it->second, it->first});
+        by_off.erase(it);
+    }
+    // offset of n free entries, or -1
+    int64_t alloc(int64_t n)
+    {
+        if (n <= 0) return 0;
+        auto it = by_len.lower_bound({n, INT64_MIN});
+        if (it == by_len.end()) return -1;
+        const int64_t len = it->first, off = it->second;
+        drop(by_off.find(off));
+        if (len > n) put(off + n, len - n);
+        used += n;
+        peak = std::max(peak, used);
+        return off;
+    }
+    void release(int64_t off, int64_t n)
+    {
+        if (n <= 0) return;
+        used -= n;
+        int64_t o = off, l = n;
+        auto nx = by_off.lower_bound(off);
+        if (nx != by_off.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == o) {
+                o = pv->first;
+                l += pv->second;
+                drop(pv);
+            }
+        }
+        nx = by_off.lower_bound(o + l);
+        if (nx != by_off.end() && nx->first == o + l) {
+            l += nx->second;
+            drop(nx);
+        }
+        put(o, l);
+    }
+    int make(int64_t off, int64_t n)
+    {
+        int h;
+        if (!spare.empty()) {
+            h = spare.back();
+            spare.pop_back();
+        } else {
+            h = (int)recs.size();
+            recs.push_back(Rec{});
+        }
+        recs[h] = Rec{off, n, 0};
+        return h;
+    }
+    void ref(int h) { recs[h].refs += 1; }
+    void unref(int h)
+    {
+        if (h < 0) return;
+        if (--recs[h].refs == 0) {
+            release(recs[h].off, recs[h].n);
+            spare.push_back(h);
+        }
+    }
+};
+
 struct SolveBufs {
-    DevBuf boxes, outs, sets, mask, counts, xbuf[2], idbuf[2], extra;
+    DevBuf boxes, outs, sets, mask, counts, xbuf[2], idbuf[2], extra, lists;
+    void *lpin = nullptr;   // pinned mirror of the list-batch descriptors
 };
 
 // Coordinates of B samples (by id) -> out [B][D] in the data type.
@@ -154,10 +256,12 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     const int K = c->K, D = c->D, KD = K * D;
     const double tol = o.tol;
     SolveBufs sb;
+    ListArena arena;
     auto cleanup = [&]() {
         for (DevBuf *b : {&sb.boxes, &sb.outs, &sb.sets, &sb.mask, &sb.counts, &sb.xbuf[0], &sb.xbuf[1], &sb.idbuf[0],
-                          &sb.idbuf[1]})
+                          &sb.idbuf[1], &sb.extra, &sb.lists, &arena.pool})
             if (b->p) cudaFree(b->p);
+        if (sb.lpin) cudaFreeHost(sb.lpin);
     };
     struct Guard {
         std::function<void()> f;
@@ -305,8 +409,91 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         const double thr = alpha - tol * alpha;
         return c->dt == KC_F32 && key < thr && raw * (1.0 + g32) * (1.0 + 1e-9) >= thr;
     };
+    int64_t refined = 0, filtered = 0, dropped = 0;
+
+    // ---- per-node surviving-sample lists (float data)
+    const bool lists = o.lists != 0 && c->dt == KC_F32;
+    const int LT = list_tile();
+    const size_t slot_bytes = ((size_t)3 * (Bmax + 1) * 8 + (size_t)(2 * Bmax + 1) * 4 + 255) & ~(size_t)255;
+    const int kSlots = 6;   // batch, its refinement, upper bounds, filter, children, their refinement
+    const size_t l_keys = (size_t)kSlots * slot_bytes, l_vmax = l_keys + (size_t)Bmax * 8;
+    const size_t l_thr = l_vmax + (size_t)Bmax * 8, l_beta = l_thr + (size_t)Bmax * 4;
+    const size_t l_off = l_beta + (size_t)Bmax * 4, l_n = l_off + (size_t)Bmax * 8;
+    const size_t l_end = l_n + (size_t)Bmax * 8 + 256;
+    unsigned long long *d_keys = nullptr, *d_vmax = nullptr, *d_outn = nullptr;
+    float *d_thr = nullptr, *d_beta = nullptr;
+    int64_t *d_outoff = nullptr;
+    int root_list = -1;
+    if (lists) {
+        KC_TRY(ensure(c, sb.lists, l_end));
+        char *lb = static_cast<char *>(sb.lists.p);
+        d_keys = reinterpret_cast<unsigned long long *>(lb + l_keys);
+        d_vmax = reinterpret_cast<unsigned long long *>(lb + l_vmax);
+        d_thr = reinterpret_cast<float *>(lb + l_thr);
+        d_beta = reinterpret_cast<float *>(lb + l_beta);
+        d_outoff = reinterpret_cast<int64_t *>(lb + l_off);
+        d_outn = reinterpret_cast<unsigned long long *>(lb + l_n);
+        if (cudaMallocHost(&sb.lpin, (size_t)kSlots * slot_bytes) != cudaSuccess) {
+            sb.lpin = nullptr;
+            cudaGetLastError();
+            return set_err(c, KC_ENOMEM, "kc_solve: pinned list descriptors");
+        }
+        size_t fr = 0, tot = 0;
+        KC_CUDA(c, cudaMemGetInfo(&fr, &tot));
+        int64_t cap = o.arena_mb > 0 ? (int64_t)o.arena_mb * (1 << 20) / 4
+                                     : std::min<int64_t>((int64_t)(fr / 2 / 4), 4096 * c->N);
+        cap = std::max<int64_t>(cap, c->N);
+        KC_TRY(ensure(c, arena.pool, (size_t)cap * 4));
+        arena.reset(cap);
+        const int64_t off = arena.alloc(c->N);
+        KC_TRY(launch_iota(c, arena.ids() + off, c->N));
+        root_list = arena.make(off, c->N);
+        arena.ref(root_list);
+        heap.front().list = root_list;
+    }
+    // descriptors of n nodes' lists in slot `slot`: handle_of(i) names node i's
+    // list; rows (or NULL) gives each node's row in per-batch arrays; with
+    // `group`, consecutive nodes holding the same list form one group that
+    // shares each staged tile
+    auto make_lb = [&](int slot, int n, const std::function<int(int)> &handle_of, const int *rows, ListBatch *L,
+                       const int **rows_dev, bool group = false) -> kc_status {
+        char *hp = static_cast<char *>(sb.lpin) + (size_t)slot * slot_bytes;
+        char *dp = static_cast<char *>(sb.lists.p) + (size_t)slot * slot_bytes;
+        int64_t *so = reinterpret_cast<int64_t *>(hp), *sn = so + (Bmax + 1), *tp = sn + (Bmax + 1);
+        int *rm = reinterpret_cast<int *>(tp + (Bmax + 1)), *ns = rm + Bmax;
+        tp[0] = 0;
+        int G = 0, prev = -1;
+        for (int i = 0; i < n; ++i) {
+            const int h = handle_of(i);
+            if (rows) rm[i] = rows[i];
+            if (group && G > 0 && h == prev) continue;
+            const ListArena::Rec &r = arena.recs[h];
+            so[G] = r.off;
+            sn[G] = r.n;
+            tp[G + 1] = tp[G] + (r.n + LT - 1) / LT;
+            ns[G] = i;
+            ++G;
+            prev = h;
+        }
+        ns[G] = n;
+        KC_CUDA(c, cudaMemcpyAsync(dp, hp, slot_bytes, cudaMemcpyHostToDevice, c->stream));
+        const int64_t *sod = reinterpret_cast<const int64_t *>(dp);
+        L->pool = arena.ids();
+        L->seg_off = sod;
+        L->seg_n = sod + (Bmax + 1);
+        L->tile_prefix = sod + 2 * (Bmax + 1);
+        const int *rmd = reinterpret_cast<const int *>(sod + 3 * (Bmax + 1));
+        L->node_start = group ? rmd + Bmax : nullptr;
+        L->B = G;
+        L->W = tp[G];
+        if (rows_dev) *rows_dev = rmd;
+        return KC_OK;
+    };
+    auto list_n = [&](int h) { return h >= 0 ? arena.recs[h].n : (int64_t)0; };
     // refined certified bounds of the boxes src[which[i]] -> h_ref[i]
-    auto refine_nodes = [&](const View &vw, const T *src_lo, const T *src_hi, const double *raw) -> kc_status {
+    // (list mode: over each node's own list, list_of(j) naming box j's list)
+    auto refine_nodes = [&](const View &vw, const T *src_lo, const T *src_hi, const double *raw,
+                            const std::function<int(int)> *list_of, int slot) -> kc_status {
         const int n = (int)amb.size();
         amb_raw.resize(n);
         for (int i = 0; i < n; ++i) {
@@ -316,12 +503,17 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         }
         KC_CUDA(c, cudaMemcpyAsync(d_llo, h_llo.data(), (size_t)n * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
         KC_CUDA(c, cudaMemcpyAsync(d_lhi, h_lhi.data(), (size_t)n * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-        KC_TRY(launch_lower_bounds_refine(c, vw, d_llo, d_lhi, n, amb_raw.data(), d_ref, nullptr, nullptr));
+        if (list_of) {
+            ListBatch L;
+            KC_TRY(make_lb(slot, n, [&](int i) { return (*list_of)(amb[i]); }, nullptr, &L, nullptr));
+            KC_TRY(launch_seg_refine(c, L, d_llo, d_lhi, n, amb_raw.data(), d_thr, d_vmax, d_ref));
+        } else {
+            KC_TRY(launch_lower_bounds_refine(c, vw, d_llo, d_lhi, n, amb_raw.data(), d_ref, nullptr, nullptr));
+        }
         KC_CUDA(c, cudaMemcpyAsync(h_ref.data(), d_ref, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
         KC_CUDA(c, cudaStreamSynchronize(c->stream));
         return KC_OK;
     };
-    int64_t refined = 0;
 
     View cur = full_view(c);
     int ping = 0;
@@ -334,11 +526,16 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     double tA = 0;
 
     auto prune_threshold = [&]() { return alpha - tol * alpha; };
+    auto drop_list = [&](Node<T> &nd) {
+        if (lists) arena.unref(nd.list);
+        nd.list = -1;
+    };
 
     for (;;) {
         // stop test: the smallest key over the open nodes against alpha
-        while (!heap.empty() && heap.front().key >= prune_threshold()) {
+        if (!heap.empty() && heap.front().key >= prune_threshold()) {
             // the heap is ordered: every node is prunable
+            for (Node<T> &nd : heap) drop_list(nd);
             heap.clear();
         }
         if (heap.empty()) break;
@@ -352,10 +549,16 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             std::pop_heap(heap.begin(), heap.end(), cmp);
             Node<T> nd = std::move(heap.back());
             heap.pop_back();
-            if (nd.key >= prune_threshold()) continue;
+            if (nd.key >= prune_threshold()) {
+                drop_list(nd);
+                continue;
+            }
             batch.push_back(std::move(nd));
         }
         if (batch.empty()) continue;
+        // nodes holding the same list are bounded together (one staged tile each)
+        if (lists)
+            std::stable_sort(batch.begin(), batch.end(), [](const Node<T> &a, const Node<T> &b) { return a.list < b.list; });
         const int B = (int)batch.size();
         for (int b = 0; b < B; ++b) {
             std::memcpy(h_lo + (size_t)b * KD, batch[b].lo.data(), KD * sizeof(T));
@@ -368,7 +571,15 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         if (o.verbose) { KC_CUDA(c, cudaStreamSynchronize(c->stream)); tA = now_s(); }
 
         // 2b. tighten the survivors
-        if (o.use_bt) {
+        ListBatch Lb;
+        const std::function<int(int)> batch_list = [&](int b) { return batch[b].list; };
+        if (lists) KC_TRY(make_lb(0, Bp, batch_list, nullptr, &Lb, nullptr, true));
+        if (lists) {
+            const bool bt = o.use_bt != 0;
+            KC_TRY(launch_tighten_list(c, Lb, d_lo, d_hi, Bp, bt ? alpha : __builtin_huge_val(), bt ? seeds_dev : nullptr,
+                                       bt ? o.ball_cap : 1, d_lo2, d_hi2, d_cnt, d_cand, d_lb, d_raw, d_arg, d_st,
+                                       &c->vs));
+        } else if (o.use_bt) {
             KC_TRY(launch_tighten_view(c, cur, d_lo, d_hi, Bp, alpha, seeds_dev, o.ball_cap, d_lo2, d_hi2, d_cnt,
                                        d_cand, d_lb, d_raw, d_arg, d_st, &c->vs));
         } else {
@@ -397,7 +608,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             if (h_st[b] != 1 && ambiguous(batch[b].key, h_raw[b])) amb.push_back(b);
         }
         if (!amb.empty()) {
-            KC_TRY(refine_nodes(cur, h_lo, h_hi, h_raw.data()));
+            KC_TRY(refine_nodes(cur, h_lo, h_hi, h_raw.data(), lists ? &batch_list : nullptr, 1));
             for (size_t i = 0; i < amb.size(); ++i) batch[amb[i]].key = std::max(batch[amb[i]].key, h_ref[i]);
             refined += (int64_t)amb.size();
         }
@@ -410,7 +621,16 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             for (int i = 0; i < S; ++i)
                 for (int k = 0; k < K; ++k) h_sets[(size_t)i * K + k] = h_cand[(size_t)live[i] * K + k];
             KC_CUDA(c, cudaMemcpyAsync(d_sets, h_sets, (size_t)S * K * 8, cudaMemcpyHostToDevice, c->stream));
-            KC_TRY(launch_objective(c, cur, d_sets, S, K, alpha, d_val, nullptr));
+            if (lists) {
+                // over the node's own list: its candidate lies in the node's
+                // boxes, where every dropped sample is nearer to it than the
+                // node's bound, so the maximum is the full-data objective
+                ListBatch Lu;
+                KC_TRY(make_lb(2, S, [&](int i) { return batch[live[i]].list; }, nullptr, &Lu, nullptr));
+                KC_TRY(launch_seg_objective(c, Lu, d_sets, S, alpha, d_keys, d_vmax, d_thr, d_val));
+            } else {
+                KC_TRY(launch_objective(c, cur, d_sets, S, K, alpha, d_val, nullptr));
+            }
             KC_CUDA(c, cudaMemcpyAsync(h_val, d_val, (size_t)S * 8, cudaMemcpyDeviceToHost, c->stream));
             KC_CUDA(c, cudaStreamSynchronize(c->stream));
             for (int i = 0; i < S; ++i) h_ub[live[i]] = h_val[i];
@@ -455,6 +675,8 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 again.parent = nd.id;
                 again.depth = nd.depth + 1;
                 again.group = nd.group;
+                again.list = nd.list;
+                if (lists) arena.ref(again.list);
                 heap.push_back(std::move(again));
                 std::push_heap(heap.begin(), heap.end(), cmp);
                 continue;
@@ -501,7 +723,8 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 f[1] = (float)std::max(-1.0, std::min(1.0, (alpha - nd.key) / al));
                 f[2] = (float)(std::log2(1.0 + nd.depth) / 8.0);
                 f[3] = (float)(std::log10(1.0 + cnt) / std::log10(1.0 + (double)K * c->N));
-                f[4] = (float)(std::log10(1.0 + (double)cur.n) / std::log10(1.0 + (double)c->N));
+                const double nact = lists ? (double)list_n(nd.list) : (double)cur.n;
+                f[4] = (float)(std::log10(1.0 + nact) / std::log10(1.0 + (double)c->N));
                 f[5] = (float)lmean;
                 f[6] = (float)lmax;
                 f[7] = (float)lmin;
@@ -559,6 +782,60 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 }
             }
         }
+        // the children's sample list: the samples of the node's list that are
+        // not redundant for both bounds in its tightened boxes (Section 4.2);
+        // the parent's list when there is no room or little is dropped
+        std::vector<int> kid_list(NB, -1);
+        if (lists && NB > 0 && o.i_sr > 0 && batches % o.i_sr == 0) {
+            std::vector<int> fi, rows;
+            std::vector<int64_t> offs;
+            std::vector<float> bdn;
+            for (int i = 0; i < NB; ++i) {
+                const int b = br[i];
+                kid_list[i] = batch[b].list;
+                const int64_t n = list_n(batch[b].list);
+                if (n < 2 * LT) continue;
+                const int64_t off = arena.alloc(n);
+                if (off < 0) continue;
+                fi.push_back(i);
+                rows.push_back(b);
+                offs.push_back(off);
+                float f = (float)batch[b].key;
+                if ((double)f > batch[b].key) f = nextafterf(f, -1.f);
+                bdn.push_back(f);
+            }
+            const int nf = (int)fi.size();
+            if (nf > 0) {
+                for (int q = 0; q < nf; ++q) {
+                    std::memcpy(&h_llo[(size_t)q * KD], h_lo2 + (size_t)rows[q] * KD, KD * sizeof(T));
+                    std::memcpy(&h_lhi[(size_t)q * KD], h_hi2 + (size_t)rows[q] * KD, KD * sizeof(T));
+                }
+                KC_CUDA(c, cudaMemcpyAsync(d_llo, h_llo.data(), (size_t)nf * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+                KC_CUDA(c, cudaMemcpyAsync(d_lhi, h_lhi.data(), (size_t)nf * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+                KC_CUDA(c, cudaMemcpyAsync(d_beta, bdn.data(), (size_t)nf * 4, cudaMemcpyHostToDevice, c->stream));
+                KC_CUDA(c, cudaMemcpyAsync(d_outoff, offs.data(), (size_t)nf * 8, cudaMemcpyHostToDevice, c->stream));
+                ListBatch Lf;
+                const int *rows_dev = nullptr;
+                KC_TRY(make_lb(3, nf, [&](int q) { return batch[rows[q]].list; }, rows.data(), &Lf, &rows_dev));
+                const bool bt = o.use_bt != 0;
+                KC_TRY(launch_seg_filter(c, Lf, d_llo, d_lhi, nf, d_beta, alpha, bt ? c->vs.repx : nullptr,
+                                         bt ? c->vs.nreps : nullptr, c->vs.RM, rows_dev, arena.ids(), d_outoff, d_outn));
+                std::vector<unsigned long long> kept(nf);
+                KC_CUDA(c, cudaMemcpyAsync(kept.data(), d_outn, (size_t)nf * 8, cudaMemcpyDeviceToHost, c->stream));
+                KC_CUDA(c, cudaStreamSynchronize(c->stream));
+                for (int q = 0; q < nf; ++q) {
+                    const int64_t n = list_n(batch[rows[q]].list), m = (int64_t)kept[q];
+                    if ((double)m > 0.95 * (double)n) {
+                        arena.release(offs[q], n);
+                        continue;
+                    }
+                    arena.release(offs[q] + m, n - m);
+                    kid_list[fi[q]] = arena.make(offs[q], m);
+                    filtered += 1;
+                    dropped += n - m;
+                }
+            }
+        }
         for (int i = 0; i < NB; ++i) {
             const int b = br[i];
             Node<T> &nd = batch[b];
@@ -587,6 +864,8 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 ch.parent = nd.id;
                 ch.depth = nd.depth + 1;
                 ch.group = ch.depth <= 8 ? ch.id : nd.group;
+                ch.list = kid_list[i];
+                if (lists) arena.ref(ch.list);
                 kids.push_back(std::move(ch));
             }
         }
@@ -600,7 +879,14 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             }
             KC_CUDA(c, cudaMemcpyAsync(d_lo, h_lo, (size_t)nk * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
             KC_CUDA(c, cudaMemcpyAsync(d_hi, h_hi, (size_t)nk * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-            KC_TRY(launch_lower_bounds_view(c, cur, d_lo, d_hi, nk, d_lb, d_raw, nullptr, 0));
+            const std::function<int(int)> kid_of = [&](int q) { return kids[k0 + q].list; };
+            if (lists) {
+                ListBatch Lk;
+                KC_TRY(make_lb(4, nk, kid_of, nullptr, &Lk, nullptr, true));
+                KC_TRY(launch_seg_lb(c, Lk, d_lo, d_hi, nk, d_keys, d_lb, d_raw, nullptr));
+            } else {
+                KC_TRY(launch_lower_bounds_view(c, cur, d_lo, d_hi, nk, d_lb, d_raw, nullptr, 0));
+            }
             KC_CUDA(c, cudaMemcpyAsync(h_lb, d_lb, (size_t)nk * 8, cudaMemcpyDeviceToHost, c->stream));
             KC_CUDA(c, cudaMemcpyAsync(h_raw.data(), d_raw, (size_t)nk * 8, cudaMemcpyDeviceToHost, c->stream));
             KC_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -610,7 +896,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 if (ambiguous(kids[k0 + q].key, h_raw[q])) amb.push_back(q);
             }
             if (!amb.empty()) {
-                KC_TRY(refine_nodes(cur, h_lo, h_hi, h_raw.data()));
+                KC_TRY(refine_nodes(cur, h_lo, h_hi, h_raw.data(), lists ? &kid_of : nullptr, 5));
                 for (size_t i = 0; i < amb.size(); ++i)
                     kids[k0 + amb[i]].key = std::max(kids[k0 + amb[i]].key, h_ref[i]);
                 refined += (int64_t)amb.size();
@@ -618,16 +904,20 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             for (int q = 0; q < nk; ++q) {
                 Node<T> &ch = kids[k0 + q];
                 ++created;
-                if (ch.key >= prune_threshold()) continue;
+                if (ch.key >= prune_threshold()) {
+                    drop_list(ch);
+                    continue;
+                }
                 heap.push_back(std::move(ch));
                 std::push_heap(heap.begin(), heap.end(), cmp);
             }
         }
         kids.clear();
+        for (Node<T> &nd : batch) drop_list(nd);
 
         if (o.verbose) { prof[3] += now_s() - tA; tA = now_s(); }
         // 5. sample reduction against the hull of the open nodes (Algorithm 5)
-        if (o.i_sr > 0 && batches % o.i_sr == 0 && !heap.empty() && heap.front().key < prune_threshold()) {
+        if (!lists && o.i_sr > 0 && batches % o.i_sr == 0 && !heap.empty() && heap.front().key < prune_threshold()) {
             // one hull box per group of open nodes (a group = the descendants of
             // one node at depth 8): every node's box lies inside its group's
             // hull, so redundancy against the hulls implies it against the nodes
@@ -723,7 +1013,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             if (batches % 100 == 0)
                 fprintf(stderr, "[kc_solve] batch %lld visits %lld open %zu alpha %.17g beta %.17g active %lld\n",
                         (long long)batches, (long long)visits, heap.size(), alpha,
-                        heap.empty() ? alpha : heap.front().key, (long long)cur.n);
+                        heap.empty() ? alpha : heap.front().key, (long long)(lists ? arena.used : cur.n));
         }
     }
     if (log) fclose(log);
@@ -732,6 +1022,9 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                         "sample reduction %.3f; batches %lld, visits %lld, created %lld, refined %lld\n",
                 prof[1], prof[2], prof[3], prof[4], (long long)batches, (long long)visits, (long long)created,
                 (long long)refined);
+    if (o.verbose && lists)
+        fprintf(stderr, "[kc_solve] lists: %lld filtered, %lld entries dropped, arena peak %lld of %lld entries\n",
+                (long long)filtered, (long long)dropped, (long long)arena.peak, (long long)arena.cap);
 
     // ---- certificate: the incumbent's objective over all N samples in double
     KC_CUDA(c, cudaMemcpyAsync(T_dev, inc.data(), K * 8, cudaMemcpyHostToDevice, c->stream));
@@ -748,9 +1041,17 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     for (int k = 0; k < 16; ++k) res->centers[k] = k < K ? inc[k] : -1;
     res->nodes = visits;
     res->batches = batches;
-    res->active_final = cur.n;
+    if (lists) {
+        int64_t longest = 0;
+        for (const Node<T> &nd : heap) longest = std::max(longest, list_n(nd.list));
+        res->active_final = longest;
+    } else {
+        res->active_final = cur.n;
+    }
     res->seconds = now_s() - t0;
     res->status = status;
+    res->lists_filtered = filtered;
+    res->samples_dropped = dropped;
     return status;
 }
 
@@ -865,7 +1166,7 @@ void kc_solve_defaults(kc_solve_opts *o)
     o->ball_cap = 50;
     o->i_sr = 1;
     o->use_bt = 1;
-    o->use_graph = 1;
+    o->lists = 1;
 }
 
 kc_status kc_solve(kc_ctx *c, double tol, const kc_solve_opts *opt, kc_result *out)
@@ -880,6 +1181,8 @@ kc_status kc_solve(kc_ctx *c, double tol, const kc_solve_opts *opt, kc_result *o
     if (o.batch < 0 || o.batch > 4096) return set_err(c, KC_EINVAL, "kc_solve: batch must be in [0, 4096]");
     if (o.order != 0 && o.order != 1) return set_err(c, KC_EINVAL, "kc_solve: order must be 0 or 1");
     if (o.order == 1 && !c->scorer) return set_err(c, KC_EINVAL, "kc_solve: order = 1 needs kc_set_scorer");
+    if (o.lists != 0 && o.lists != 1) return set_err(c, KC_EINVAL, "kc_solve: lists must be 0 or 1");
+    if (o.arena_mb < 0) return set_err(c, KC_EINVAL, "kc_solve: arena_mb must be >= 0");
     std::memset(out, 0, sizeof(*out));
     if (c->dt == KC_F32) return solve_impl<float>(c, o, out);
     return solve_impl<double>(c, o, out);

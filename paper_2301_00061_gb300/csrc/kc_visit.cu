@@ -194,6 +194,124 @@ struct Margins {
 };
 
 // ------------------------------------------------------------ pass A
+//
+// pass_a_node: one warp's share of one node over a staged tile of samples
+// (j = j0, j0 + step, ... < tn).  Keys name a sample by tids[j] when the tile
+// was gathered from a list of sample ids, else by its position base + j.
+
+template <typename T, int KM, int DM>
+__device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td, int tile, int tn, int j0, int step,
+                                            const uint32_t *tids, int64_t base, const T *__restrict__ lo,
+                                            const T *__restrict__ hi, int b, int K, int D, double alpha,
+                                            const Margins &mg, typename Key<T>::K *__restrict__ lbkey,
+                                            typename Key<T>::K *__restrict__ amax, typename Key<T>::K *__restrict__ amin,
+                                            unsigned *__restrict__ flags)
+{
+    using KT = Key<T>;
+    using KY = typename KT::K;
+    constexpr bool F32 = sizeof(T) == 4;
+    const int lane = threadIdx.x & 31;
+    // node boxes into registers
+    uint64_t bx[KM][DM];
+    double blo[KM][DM], bhi[KM][DM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k)
+#pragma unroll
+        for (int a = 0; a < DM; ++a) {
+            const bool in = k < K && a < D;
+            const size_t o = ((size_t)b * K + k) * D + a;
+            if constexpr (F32) {
+                bx[k][a] = in ? pk((float)lo[o], -(float)hi[o]) : pk(0.f, -0.f);
+            } else {
+                blo[k][a] = in ? (double)lo[o] : 0.0;
+                bhi[k][a] = in ? (double)hi[o] : 0.0;
+            }
+        }
+    KY acc_lb = KT::none();
+    KY acc_max[KM][DM], acc_min[KM][DM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k)
+#pragma unroll
+        for (int a = 0; a < DM; ++a) { acc_max[k][a] = KT::none(); acc_min[k][a] = KT::none(); }
+    bool infeasible = false;
+    for (int j = j0; j < tn; j += step) {
+        const uint32_t pos = tids ? tids[j] : (uint32_t)(base + j);
+        T x[DM];
+        uint64_t px[DM];
+#pragma unroll
+        for (int a = 0; a < DM; ++a) {
+            if constexpr (F32) {
+                px[a] = a < D ? tp[(size_t)a * tile + j] : pk(0.f, -0.f);
+                x[a] = upk(px[a]).x;
+            } else {
+                x[a] = a < D ? td[(size_t)a * tile + j] : 0.0;
+            }
+        }
+        T bmin = T(0);
+        int left = 0, k1 = -1;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            if (k < K) {
+                T v;
+                bool excl;
+                if constexpr (F32) {
+                    v = box_dist_pad<DM>(px, bx[k]);
+                    excl = v > mg.t_alpha;
+                } else {
+                    v = box_dist_f64<DM>(reinterpret_cast<const double *>(x), blo[k], bhi[k], D);
+                    excl = v > alpha;
+                }
+                bmin = (k == 0 || v < bmin) ? v : bmin;
+                if (!excl) { ++left; k1 = k; }
+            }
+        }
+        acc_lb = kmax<T>(acc_lb, KT::max_of(bmin, pos));
+        if (left == 0) infeasible = true;
+        if (left == 1) {
+#pragma unroll
+            for (int k = 0; k < KM; ++k)
+                if (k == k1) {
+#pragma unroll
+                    for (int a = 0; a < DM; ++a)
+                        if (a < D) {
+                            acc_max[k][a] = kmax<T>(acc_max[k][a], KT::max_of(x[a], pos));
+                            acc_min[k][a] = kmax<T>(acc_min[k][a], KT::min_of(x[a], pos));
+                        }
+                }
+        }
+    }
+    // warp reduction, then one atomic per accumulator and warp
+    acc_lb = warp_kmax<T>(acc_lb);
+    if (lane == 0 && !KT::is_none(acc_lb)) KT::atomic_max(&lbkey[b], acc_lb, &flags[b]);
+#pragma unroll
+    for (int k = 0; k < KM; ++k)
+#pragma unroll
+        for (int a = 0; a < DM; ++a)
+            if (k < K && a < D) {
+                const KY m1 = warp_kmax<T>(acc_max[k][a]);
+                const KY m2 = warp_kmax<T>(acc_min[k][a]);
+                const size_t o = ((size_t)b * K + k) * D + a;
+                if (lane == 0 && !KT::is_none(m1)) KT::atomic_max(&amax[o], m1, &flags[b]);
+                if (lane == 0 && !KT::is_none(m2)) KT::atomic_max(&amin[o], m2, &flags[b]);
+            }
+    if (__any_sync(0xffffffffu, infeasible) && lane == 0) atomicOr(&flags[b], 1u);
+}
+
+// Stages samples of a tile in shared memory: float data as (x, -x) pairs,
+// double data as values.  ids: gather by sample id (list mode), else rows
+// base .. base + tn of the view.
+template <typename T>
+__device__ __forceinline__ void stage_tile_a(const T *__restrict__ X, int64_t ld, int D, int tile, int tn, int64_t base,
+                                             const uint32_t *ids, uint64_t *tp, double *td)
+{
+    for (int i = threadIdx.x; i < D * tile; i += kThreads) {
+        const int a = i / tile, j = i - a * tile;
+        T v = T(0);
+        if (j < tn) v = ids ? X[(size_t)a * ld + ids[j]] : X[(size_t)a * ld + base + j];
+        if constexpr (sizeof(T) == 4) tp[i] = pk(v, -v);
+        else td[i] = v;
+    }
+}
 
 template <typename T, int KM, int DM>
 __global__ void __launch_bounds__(kThreads)
@@ -202,111 +320,54 @@ visit_a_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, const T
                typename Key<T>::K *__restrict__ lbkey, typename Key<T>::K *__restrict__ amax,
                typename Key<T>::K *__restrict__ amin, unsigned *__restrict__ flags)
 {
-    using KT = Key<T>;
-    using KY = typename KT::K;
-    constexpr bool F32 = sizeof(T) == 4;
     extern __shared__ __align__(16) unsigned char smem[];
-    // float: (x, -x) pairs [D][tile]; double: x [D][tile]
     uint64_t *tp = reinterpret_cast<uint64_t *>(smem);
     double *td = reinterpret_cast<double *>(smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
     for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
         const int tn = (int)((n - base) < (int64_t)tile ? (n - base) : (int64_t)tile);
         __syncthreads();
-        for (int i = threadIdx.x; i < D * tile; i += kThreads) {
-            const int a = i / tile, j = i - a * tile;
-            const T v = j < tn ? X[(size_t)a * ld + base + j] : T(0);
-            if constexpr (F32) tp[i] = pk(v, -v);
-            else td[i] = v;
-        }
+        stage_tile_a<T>(X, ld, D, tile, tn, base, nullptr, tp, td);
         __syncthreads();
-        for (int b = warp; b < B; b += NWV) {
-            // node boxes into registers
-            uint64_t bx[KM][DM];
-            double blo[KM][DM], bhi[KM][DM];
-#pragma unroll
-            for (int k = 0; k < KM; ++k)
-#pragma unroll
-                for (int a = 0; a < DM; ++a) {
-                    const bool in = k < K && a < D;
-                    const size_t o = ((size_t)b * K + k) * D + a;
-                    if constexpr (F32) {
-                        bx[k][a] = in ? pk((float)lo[o], -(float)hi[o]) : pk(0.f, -0.f);
-                    } else {
-                        blo[k][a] = in ? (double)lo[o] : 0.0;
-                        bhi[k][a] = in ? (double)hi[o] : 0.0;
-                    }
-                }
-            KY acc_lb = KT::none();
-            KY acc_max[KM][DM], acc_min[KM][DM];
-#pragma unroll
-            for (int k = 0; k < KM; ++k)
-#pragma unroll
-                for (int a = 0; a < DM; ++a) { acc_max[k][a] = KT::none(); acc_min[k][a] = KT::none(); }
-            bool infeasible = false;
-            for (int j = lane; j < tn; j += 32) {
-                const uint32_t pos = (uint32_t)(base + j);
-                T x[DM];
-                uint64_t px[DM];
-#pragma unroll
-                for (int a = 0; a < DM; ++a) {
-                    if constexpr (F32) {
-                        px[a] = a < D ? tp[(size_t)a * tile + j] : pk(0.f, -0.f);
-                        x[a] = upk(px[a]).x;
-                    } else {
-                        x[a] = a < D ? td[(size_t)a * tile + j] : 0.0;
-                    }
-                }
-                T bmin = T(0);
-                int left = 0, k1 = -1;
-#pragma unroll
-                for (int k = 0; k < KM; ++k) {
-                    if (k < K) {
-                        T v;
-                        bool excl;
-                        if constexpr (F32) {
-                            v = box_dist_pad<DM>(px, bx[k]);
-                            excl = v > mg.t_alpha;
-                        } else {
-                            v = box_dist_f64<DM>(reinterpret_cast<const double *>(x), blo[k], bhi[k], D);
-                            excl = v > alpha;
-                        }
-                        bmin = (k == 0 || v < bmin) ? v : bmin;
-                        if (!excl) { ++left; k1 = k; }
-                    }
-                }
-                acc_lb = kmax<T>(acc_lb, KT::max_of(bmin, pos));
-                if (left == 0) infeasible = true;
-                if (left == 1) {
-#pragma unroll
-                    for (int k = 0; k < KM; ++k)
-                        if (k == k1) {
-#pragma unroll
-                            for (int a = 0; a < DM; ++a)
-                                if (a < D) {
-                                    acc_max[k][a] = kmax<T>(acc_max[k][a], KT::max_of(x[a], pos));
-                                    acc_min[k][a] = kmax<T>(acc_min[k][a], KT::min_of(x[a], pos));
-                                }
-                        }
-                }
-            }
-            // warp reduction, then one atomic per accumulator and warp
-            acc_lb = warp_kmax<T>(acc_lb);
-            if (lane == 0 && !KT::is_none(acc_lb)) KT::atomic_max(&lbkey[b], acc_lb, &flags[b]);
-#pragma unroll
-            for (int k = 0; k < KM; ++k)
-#pragma unroll
-                for (int a = 0; a < DM; ++a)
-                    if (k < K && a < D) {
-                        const KY m1 = warp_kmax<T>(acc_max[k][a]);
-                        const KY m2 = warp_kmax<T>(acc_min[k][a]);
-                        const size_t o = ((size_t)b * K + k) * D + a;
-                        if (lane == 0 && !KT::is_none(m1)) KT::atomic_max(&amax[o], m1, &flags[b]);
-                        if (lane == 0 && !KT::is_none(m2)) KT::atomic_max(&amin[o], m2, &flags[b]);
-                    }
-            if (__any_sync(0xffffffffu, infeasible) && lane == 0) atomicOr(&flags[b], 1u);
-        }
+        for (int b = warp; b < B; b += NWV)
+            pass_a_node<T, KM, DM>(tp, td, tile, tn, lane, 32, nullptr, base, lo, hi, b, K, D, alpha, mg, lbkey, amax,
+                                   amin, flags);
+    }
+}
+
+// List mode: work item w = one tile of a group's sample-id list (see
+// ListBatch); the CTA evaluates every node of the group on the staged tile.
+template <typename T, int KM, int DM>
+__global__ void __launch_bounds__(kThreads)
+visit_a_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile,
+                    const T *__restrict__ lo, const T *__restrict__ hi, int K, int D, double alpha, Margins mg,
+                    typename Key<T>::K *__restrict__ lbkey, typename Key<T>::K *__restrict__ amax,
+                    typename Key<T>::K *__restrict__ amin, unsigned *__restrict__ flags)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *tp = reinterpret_cast<uint64_t *>(smem);
+    double *td = reinterpret_cast<double *>(smem);
+    uint32_t *tids = reinterpret_cast<uint32_t *>(smem + (size_t)D * tile * 8);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
+        int b;
+        int64_t st;
+        list_item(L.tile_prefix, L.B, w, tile, &b, &st);
+        const int64_t nb = L.seg_n[b];
+        const int tn = (int)((nb - st) < (int64_t)tile ? (nb - st) : (int64_t)tile);
+        __syncthreads();
+        for (int j = threadIdx.x; j < tn; j += kThreads) tids[j] = L.pool[L.seg_off[b] + st + j];
+        __syncthreads();
+        stage_tile_a<T>(X, ld, D, tile, tn, 0, tids, tp, td);
+        __syncthreads();
+        // the group's nodes share the tile: min(G, warps) teams of warps, team
+        // t takes nodes n0 + t, n0 + t + teams, ... over the whole tile
+        const int n0 = L.node_start ? L.node_start[b] : b, n1 = L.node_start ? L.node_start[b + 1] : b + 1;
+        const int teams = (n1 - n0) < NWV ? (n1 - n0) : NWV, wpt = NWV / teams, team = warp / wpt;
+        if (team < teams)
+            for (int nd = n0 + team; nd < n1; nd += teams)
+                pass_a_node<T, KM, DM>(tp, td, tile, tn, (warp % wpt) * 32 + lane, wpt * 32, tids, 0, lo, hi, nd, K, D,
+                                       alpha, mg, lbkey, amax, amin, flags);
     }
 }
 
@@ -447,6 +508,235 @@ __global__ void finalize_a_kernel(int B, int K, int D, const T *__restrict__ lo,
 constexpr int kSub = 256;   // samples flagged per warp before processing
 
 template <typename T, int KM, int DM, int RMX>
+__device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int jstart, int wstep, const uint32_t *tids,
+                                            const uint32_t *__restrict__ ids, int64_t base, uint32_t *list, int b,
+                                            int K, int D, int RM, const T *__restrict__ lo_in,
+                                            const T *__restrict__ hi_in, const T *__restrict__ blo,
+                                            const T *__restrict__ bhi, const T *__restrict__ repx,
+                                            const int *__restrict__ nreps, const int *__restrict__ allhave,
+                                            double alpha, const Margins &mg, const int64_t *seed_id,
+                                            unsigned long long *__restrict__ cnt, OrdT<T> *__restrict__ smax,
+                                            OrdT<T> *__restrict__ smin, OrdT<T> *__restrict__ jmax,
+                                            OrdT<T> *__restrict__ jmin, typename Key<T>::K *__restrict__ cand,
+                                            unsigned *__restrict__ flags)
+{
+    using KT = Key<T>;
+    using KY = typename KT::K;
+    constexpr bool F32 = sizeof(T) == 4;
+    constexpr int DH = (DM + 1) / 2;
+    const int lane = threadIdx.x & 31;
+    const double four_alpha = 4.0 * alpha;
+    // node b: input boxes (center-based status), box-BT boxes, midpoints
+    uint64_t bx[KM][DM];
+    double ilo[KM][DM], ihi[KM][DM];
+    T l[KM][DM], h[KM][DM], mid[KM][DM];
+    int nr[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        nr[k] = k < K ? nreps[(size_t)b * K + k] : 0;
+#pragma unroll
+        for (int a = 0; a < DM; ++a) {
+            const bool in = k < K && a < D;
+            const size_t o = ((size_t)b * K + k) * D + a;
+            if constexpr (F32) bx[k][a] = in ? pk((float)lo_in[o], -(float)hi_in[o]) : pk(0.f, -0.f);
+            else { ilo[k][a] = in ? (double)lo_in[o] : 0.0; ihi[k][a] = in ? (double)hi_in[o] : 0.0; }
+            l[k][a] = in ? blo[o] : T(0);
+            h[k][a] = in ? bhi[o] : T(0);
+            if constexpr (F32) mid[k][a] = in ? (float)(0.5 * ((double)l[k][a] + (double)h[k][a])) : 0.f;
+            else mid[k][a] = in ? 0.5 * (l[k][a] + h[k][a]) : 0.0;
+        }
+    }
+    const bool have = allhave[b] != 0;
+    const T *rxb = repx + (size_t)b * K * RM * D;
+    unsigned long long c_cnt[KM];
+    T c_smax[KM][DM], c_smin[KM][DM], c_jmax[KM][DM], c_jmin[KM][DM];
+    KY c_cand[KM];
+    const T INF = F32 ? (T)__int_as_float(0x7f800000) : (T)__longlong_as_double(0x7ff0000000000000ll);
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        c_cnt[k] = 0;
+        c_cand[k] = KT::none();
+#pragma unroll
+        for (int a = 0; a < DM; ++a) { c_smax[k][a] = -INF; c_smin[k][a] = INF; c_jmax[k][a] = -INF; c_jmin[k][a] = INF; }
+    }
+    bool infeasible = false;
+    for (int r0 = jstart; r0 < tn; r0 += 8 * wstep) {
+        // phase 1: flag the samples that need representative distances
+        int count = 0;
+        for (int g = 0; g < 8; ++g) {
+            const int jb = r0 + g * wstep;
+            if (jb >= tn) break;   // uniform across the warp
+            const int j = jb + lane;
+            uint32_t fl = 0u;
+            if (j < tn) {
+                T x[DM];
+#pragma unroll
+                for (int a = 0; a < DM; ++a) x[a] = a < D ? tx[(size_t)a * tile + j] : T(0);
+                int left = 0;
+#pragma unroll
+                for (int k = 0; k < KM; ++k)
+                    if (k < K) {
+                        bool excl;
+                        if constexpr (F32) {
+                            uint64_t px[DM];
+#pragma unroll
+                            for (int a = 0; a < DM; ++a) px[a] = pk(x[a], -x[a]);
+                            excl = box_dist_f32<DM>(px, bx[k]) > mg.t_alpha;
+                        } else {
+                            excl = box_dist_f64<DM>(reinterpret_cast<const double *>(x), ilo[k], ihi[k], D) > alpha;
+                        }
+                        if (!excl) ++left;
+                    }
+                if (have && left >= 2) {
+                    // the seeds count as assigned in every node
+                    const int64_t id = tids ? (int64_t)tids[j] : (ids ? (int64_t)ids[base + j] : base + j);
+                    bool is_seed = false;
+#pragma unroll
+                    for (int k = 0; k < KM; ++k)
+                        if (seed_id[k] == id) is_seed = true;
+                    if (!is_seed) fl |= 1u;
+                }
+#pragma unroll
+                for (int k = 0; k < KM; ++k)
+                    if (k < K) {
+                        bool inb = true;
+#pragma unroll
+                        for (int a = 0; a < DM; ++a)
+                            if (a < D && (x[a] < l[k][a] || x[a] > h[k][a])) inb = false;
+                        if (inb) fl |= 2u << k;
+                    }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, fl != 0u);
+            if (fl) list[count + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)j | (fl << 16);
+            count += __popc(bal);
+        }
+        __syncwarp();
+        // phase 2: representative distances of the flagged samples
+        for (int e = lane; e < count; e += 32) {
+            const uint32_t ent = list[e];
+            const int j = (int)(ent & 0xFFFFu);
+            const uint32_t fl = ent >> 16;
+            const uint32_t pos = tids ? tids[j] : (uint32_t)(base + j);
+            T x[DM];
+#pragma unroll
+            for (int a = 0; a < DM; ++a) x[a] = a < D ? tx[(size_t)a * tile + j] : T(0);
+            uint64_t px[DH];
+            if constexpr (F32) {
+#pragma unroll
+                for (int p = 0; p < DH; ++p) px[p] = pk(x[2 * p], 2 * p + 1 < DM ? x[2 * p + 1] : 0.f);
+            }
+            // distances to the representatives of the clusters that need them
+            unsigned long long far4 = 0ull, far1 = 0ull;
+#pragma unroll
+            for (int k = 0; k < KM; ++k) {
+                const bool need = k < K && ((fl & 1u) || (fl & (2u << k)));
+                if (!need) continue;
+#pragma unroll
+                for (int r = 0; r < RMX; ++r)
+                    if (r < nr[k]) {
+                        const T *c = rxb + ((size_t)k * RM + r) * D;
+                        if constexpr (F32) {
+                            uint64_t pc[DH];
+#pragma unroll
+                            for (int p = 0; p < DH; ++p)
+                                pc[p] = pk(2 * p < D ? c[2 * p] : 0.f, 2 * p + 1 < D ? c[2 * p + 1] : 0.f);
+                            const float d = pt_dist_f32<2 * DH>(px, pc);
+                            if (d > mg.t_four) far4 |= 1ull << (k * RMX + r);
+                            if (d > mg.t_alpha) far1 |= 1ull << (k * RMX + r);
+                        } else {
+                            double cc[DM];
+#pragma unroll
+                            for (int a = 0; a < DM; ++a) cc[a] = a < D ? c[a] : 0.0;
+                            const double d = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), cc, D);
+                            if (d > four_alpha) far4 |= 1ull << (k * RMX + r);
+                            if (d > alpha) far1 |= 1ull << (k * RMX + r);
+                        }
+                    }
+            }
+            // sample-based assignment of an unassigned sample (Algorithm 3, Lemma 2)
+            if (fl & 1u) {
+                int left = 0, k1 = -1;
+#pragma unroll
+                for (int k = 0; k < KM; ++k)
+                    if (k < K) {
+                        const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
+                        if ((far4 & mk) == 0ull) { ++left; k1 = k; }
+                    }
+                if (left == 0) infeasible = true;
+                if (left == 1) {
+#pragma unroll
+                    for (int k = 0; k < KM; ++k)
+                        if (k == k1) {
+#pragma unroll
+                            for (int a = 0; a < DM; ++a) {
+                                c_jmax[k][a] = x[a] > c_jmax[k][a] ? x[a] : c_jmax[k][a];
+                                c_jmin[k][a] = x[a] < c_jmin[k][a] ? x[a] : c_jmin[k][a];
+                            }
+                        }
+                }
+            }
+            // ball-based tightening and centers on samples (Algorithm 4)
+#pragma unroll
+            for (int k = 0; k < KM; ++k)
+                if (k < K && (fl & (2u << k))) {
+                    const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
+                    if (far1 & mk) continue;
+                    ++c_cnt[k];
+#pragma unroll
+                    for (int a = 0; a < DM; ++a) {
+                        c_smax[k][a] = x[a] > c_smax[k][a] ? x[a] : c_smax[k][a];
+                        c_smin[k][a] = x[a] < c_smin[k][a] ? x[a] : c_smin[k][a];
+                    }
+                    T dm;
+                    if constexpr (F32) {
+                        uint64_t pm[DH];
+#pragma unroll
+                        for (int p = 0; p < DH; ++p)
+                            pm[p] = pk(mid[k][2 * p], 2 * p + 1 < DM ? mid[k][2 * p + 1] : 0.f);
+                        dm = pt_dist_f32<2 * DH>(px, pm);
+                    } else {
+                        dm = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), mid[k], D);
+                    }
+                    c_cand[k] = kmax<T>(c_cand[k], KT::min_of(dm, pos));
+                }
+        }
+        __syncwarp();
+    }
+    // reduce and merge
+#pragma unroll
+    for (int k = 0; k < KM; ++k)
+        if (k < K) {
+            unsigned long long cn = c_cnt[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(0xffffffffu, cn, o);
+            const KY cd = warp_kmax<T>(c_cand[k]);
+            const size_t ok_ = (size_t)b * K + k;
+            if (lane == 0 && cn) atomicAdd(&cnt[ok_], cn);
+            if (lane == 0 && !KT::is_none(cd)) KT::atomic_max(&cand[ok_], cd, &flags[b]);
+#pragma unroll
+            for (int a = 0; a < DM; ++a)
+                if (a < D) {
+                    T v1 = c_smax[k][a], v2 = c_smin[k][a], v3 = c_jmax[k][a], v4 = c_jmin[k][a];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        v1 = fmax(v1, __shfl_xor_sync(0xffffffffu, v1, o));
+                        v2 = fmin(v2, __shfl_xor_sync(0xffffffffu, v2, o));
+                        v3 = fmax(v3, __shfl_xor_sync(0xffffffffu, v3, o));
+                        v4 = fmin(v4, __shfl_xor_sync(0xffffffffu, v4, o));
+                    }
+                    const size_t o = ok_ * D + a;
+                    if (lane == 0) {
+                        if (v1 != -INF) atomic_max_val(&smax[o], v1);
+                        if (v2 != INF) atomic_min_val(&smin[o], v2);
+                        if (v3 != -INF) atomic_max_val(&jmax[o], v3);
+                        if (v4 != INF) atomic_min_val(&jmin[o], v4);
+                    }
+                }
+        }
+    if (__any_sync(0xffffffffu, infeasible) && lane == 0) atomicOr(&flags[b], 1u);
+}
+
+template <typename T, int KM, int DM, int RMX>
 __global__ void __launch_bounds__(kThreads)
 visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, int K, int D, int RM,
                const T *__restrict__ lo_in, const T *__restrict__ hi_in, const T *__restrict__ blo,
@@ -456,20 +746,14 @@ visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, 
                OrdT<T> *__restrict__ smax, OrdT<T> *__restrict__ smin, OrdT<T> *__restrict__ jmax,
                OrdT<T> *__restrict__ jmin, typename Key<T>::K *__restrict__ cand, unsigned *__restrict__ flags)
 {
-    using KT = Key<T>;
-    using KY = typename KT::K;
-    constexpr bool F32 = sizeof(T) == 4;
-    constexpr int DH = (DM + 1) / 2;
     int64_t seed_id[KM];
 #pragma unroll
     for (int k = 0; k < KM; ++k) seed_id[k] = (seeds && k < K) ? seeds[k] : -1;
     extern __shared__ __align__(16) unsigned char smem[];
     T *tx = reinterpret_cast<T *>(smem);                                        // [D][tile]
     uint32_t *lists = reinterpret_cast<uint32_t *>(tx + (size_t)D * tile);      // [warps][kSub]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
     uint32_t *list = lists + warp * kSub;
-    const double four_alpha = 4.0 * alpha;
-
     for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
         const int tn = (int)((n - base) < (int64_t)tile ? (n - base) : (int64_t)tile);
         __syncthreads();
@@ -478,215 +762,55 @@ visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, 
             tx[i] = j < tn ? X[(size_t)a * ld + base + j] : T(0);
         }
         __syncthreads();
-        for (int b = warp; b < B; b += NWV) {
-            // node b: input boxes (center-based status), box-BT boxes, midpoints
-            uint64_t bx[KM][DM];
-            double ilo[KM][DM], ihi[KM][DM];
-            T l[KM][DM], h[KM][DM], mid[KM][DM];
-            int nr[KM];
+        for (int b = warp; b < B; b += NWV)
+            pass_b_node<T, KM, DM, RMX>(tx, tile, tn, 0, 32, nullptr, ids, base, list, b, K, D, RM, lo_in, hi_in, blo,
+                                        bhi, repx, nreps, allhave, alpha, mg, seed_id, cnt, smax, smin, jmax, jmin,
+                                        cand, flags);
+    }
+}
+
+// List mode of pass B (see visit_a_list_kernel).
+template <typename T, int KM, int DM, int RMX>
+__global__ void __launch_bounds__(kThreads)
+visit_b_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile, int K,
+                    int D, int RM, const T *__restrict__ lo_in, const T *__restrict__ hi_in, const T *__restrict__ blo,
+                    const T *__restrict__ bhi, const T *__restrict__ repx, const int *__restrict__ nreps,
+                    const int *__restrict__ allhave, double alpha, Margins mg, const int64_t *__restrict__ seeds,
+                    unsigned long long *__restrict__ cnt, OrdT<T> *__restrict__ smax, OrdT<T> *__restrict__ smin,
+                    OrdT<T> *__restrict__ jmax, OrdT<T> *__restrict__ jmin, typename Key<T>::K *__restrict__ cand,
+                    unsigned *__restrict__ flags)
+{
+    int64_t seed_id[KM];
 #pragma unroll
-            for (int k = 0; k < KM; ++k) {
-                nr[k] = k < K ? nreps[(size_t)b * K + k] : 0;
-#pragma unroll
-                for (int a = 0; a < DM; ++a) {
-                    const bool in = k < K && a < D;
-                    const size_t o = ((size_t)b * K + k) * D + a;
-                    if constexpr (F32) bx[k][a] = in ? pk((float)lo_in[o], -(float)hi_in[o]) : pk(0.f, -0.f);
-                    else { ilo[k][a] = in ? (double)lo_in[o] : 0.0; ihi[k][a] = in ? (double)hi_in[o] : 0.0; }
-                    l[k][a] = in ? blo[o] : T(0);
-                    h[k][a] = in ? bhi[o] : T(0);
-                    if constexpr (F32) mid[k][a] = in ? (float)(0.5 * ((double)l[k][a] + (double)h[k][a])) : 0.f;
-                    else mid[k][a] = in ? 0.5 * (l[k][a] + h[k][a]) : 0.0;
-                }
-            }
-            const bool have = allhave[b] != 0;
-            const T *rxb = repx + (size_t)b * K * RM * D;
-            unsigned long long c_cnt[KM];
-            T c_smax[KM][DM], c_smin[KM][DM], c_jmax[KM][DM], c_jmin[KM][DM];
-            KY c_cand[KM];
-            const T INF = F32 ? (T)__int_as_float(0x7f800000) : (T)__longlong_as_double(0x7ff0000000000000ll);
-#pragma unroll
-            for (int k = 0; k < KM; ++k) {
-                c_cnt[k] = 0;
-                c_cand[k] = KT::none();
-#pragma unroll
-                for (int a = 0; a < DM; ++a) { c_smax[k][a] = -INF; c_smin[k][a] = INF; c_jmax[k][a] = -INF; c_jmin[k][a] = INF; }
-            }
-            bool infeasible = false;
-            for (int sub = 0; sub < tn; sub += kSub) {
-                const int se = min(tn, sub + kSub);
-                // phase 1: flag the samples that need representative distances
-                int count = 0;
-                for (int j0 = sub; j0 < se; j0 += 32) {
-                    const int j = j0 + lane;
-                    uint32_t fl = 0u;
-                    if (j < se) {
-                        T x[DM];
-#pragma unroll
-                        for (int a = 0; a < DM; ++a) x[a] = a < D ? tx[(size_t)a * tile + j] : T(0);
-                        int left = 0;
-#pragma unroll
-                        for (int k = 0; k < KM; ++k)
-                            if (k < K) {
-                                bool excl;
-                                if constexpr (F32) {
-                                    uint64_t px[DM];
-#pragma unroll
-                                    for (int a = 0; a < DM; ++a) px[a] = pk(x[a], -x[a]);
-                                    excl = box_dist_f32<DM>(px, bx[k]) > mg.t_alpha;
-                                } else {
-                                    excl = box_dist_f64<DM>(reinterpret_cast<const double *>(x), ilo[k], ihi[k], D) > alpha;
-                                }
-                                if (!excl) ++left;
-                            }
-                        if (have && left >= 2) {
-                            // the seeds count as assigned in every node
-                            const int64_t id = ids ? (int64_t)ids[base + j] : base + j;
-                            bool is_seed = false;
-#pragma unroll
-                            for (int k = 0; k < KM; ++k)
-                                if (seed_id[k] == id) is_seed = true;
-                            if (!is_seed) fl |= 1u;
-                        }
-#pragma unroll
-                        for (int k = 0; k < KM; ++k)
-                            if (k < K) {
-                                bool inb = true;
-#pragma unroll
-                                for (int a = 0; a < DM; ++a)
-                                    if (a < D && (x[a] < l[k][a] || x[a] > h[k][a])) inb = false;
-                                if (inb) fl |= 2u << k;
-                            }
-                    }
-                    const unsigned bal = __ballot_sync(0xffffffffu, fl != 0u);
-                    if (fl) list[count + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)j | (fl << 16);
-                    count += __popc(bal);
-                }
-                __syncwarp();
-                // phase 2: representative distances of the flagged samples
-                for (int e = lane; e < count; e += 32) {
-                    const uint32_t ent = list[e];
-                    const int j = (int)(ent & 0xFFFFu);
-                    const uint32_t fl = ent >> 16;
-                    const uint32_t pos = (uint32_t)(base + j);
-                    T x[DM];
-#pragma unroll
-                    for (int a = 0; a < DM; ++a) x[a] = a < D ? tx[(size_t)a * tile + j] : T(0);
-                    uint64_t px[DH];
-                    if constexpr (F32) {
-#pragma unroll
-                        for (int p = 0; p < DH; ++p) px[p] = pk(x[2 * p], 2 * p + 1 < DM ? x[2 * p + 1] : 0.f);
-                    }
-                    // distances to the representatives of the clusters that need them
-                    unsigned long long far4 = 0ull, far1 = 0ull;
-#pragma unroll
-                    for (int k = 0; k < KM; ++k) {
-                        const bool need = k < K && ((fl & 1u) || (fl & (2u << k)));
-                        if (!need) continue;
-#pragma unroll
-                        for (int r = 0; r < RMX; ++r)
-                            if (r < nr[k]) {
-                                const T *c = rxb + ((size_t)k * RM + r) * D;
-                                if constexpr (F32) {
-                                    uint64_t pc[DH];
-#pragma unroll
-                                    for (int p = 0; p < DH; ++p)
-                                        pc[p] = pk(2 * p < D ? c[2 * p] : 0.f, 2 * p + 1 < D ? c[2 * p + 1] : 0.f);
-                                    const float d = pt_dist_f32<2 * DH>(px, pc);
-                                    if (d > mg.t_four) far4 |= 1ull << (k * RMX + r);
-                                    if (d > mg.t_alpha) far1 |= 1ull << (k * RMX + r);
-                                } else {
-                                    double cc[DM];
-#pragma unroll
-                                    for (int a = 0; a < DM; ++a) cc[a] = a < D ? c[a] : 0.0;
-                                    const double d = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), cc, D);
-                                    if (d > four_alpha) far4 |= 1ull << (k * RMX + r);
-                                    if (d > alpha) far1 |= 1ull << (k * RMX + r);
-                                }
-                            }
-                    }
-                    // sample-based assignment of an unassigned sample (Algorithm 3, Lemma 2)
-                    if (fl & 1u) {
-                        int left = 0, k1 = -1;
-#pragma unroll
-                        for (int k = 0; k < KM; ++k)
-                            if (k < K) {
-                                const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
-                                if ((far4 & mk) == 0ull) { ++left; k1 = k; }
-                            }
-                        if (left == 0) infeasible = true;
-                        if (left == 1) {
-#pragma unroll
-                            for (int k = 0; k < KM; ++k)
-                                if (k == k1) {
-#pragma unroll
-                                    for (int a = 0; a < DM; ++a) {
-                                        c_jmax[k][a] = x[a] > c_jmax[k][a] ? x[a] : c_jmax[k][a];
-                                        c_jmin[k][a] = x[a] < c_jmin[k][a] ? x[a] : c_jmin[k][a];
-                                    }
-                                }
-                        }
-                    }
-                    // ball-based tightening and centers on samples (Algorithm 4)
-#pragma unroll
-                    for (int k = 0; k < KM; ++k)
-                        if (k < K && (fl & (2u << k))) {
-                            const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
-                            if (far1 & mk) continue;
-                            ++c_cnt[k];
-#pragma unroll
-                            for (int a = 0; a < DM; ++a) {
-                                c_smax[k][a] = x[a] > c_smax[k][a] ? x[a] : c_smax[k][a];
-                                c_smin[k][a] = x[a] < c_smin[k][a] ? x[a] : c_smin[k][a];
-                            }
-                            T dm;
-                            if constexpr (F32) {
-                                uint64_t pm[DH];
-#pragma unroll
-                                for (int p = 0; p < DH; ++p)
-                                    pm[p] = pk(mid[k][2 * p], 2 * p + 1 < DM ? mid[k][2 * p + 1] : 0.f);
-                                dm = pt_dist_f32<2 * DH>(px, pm);
-                            } else {
-                                dm = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), mid[k], D);
-                            }
-                            c_cand[k] = kmax<T>(c_cand[k], KT::min_of(dm, pos));
-                        }
-                }
-                __syncwarp();
-            }
-            // reduce and merge
-#pragma unroll
-            for (int k = 0; k < KM; ++k)
-                if (k < K) {
-                    unsigned long long cn = c_cnt[k];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(0xffffffffu, cn, o);
-                    const KY cd = warp_kmax<T>(c_cand[k]);
-                    const size_t ok_ = (size_t)b * K + k;
-                    if (lane == 0 && cn) atomicAdd(&cnt[ok_], cn);
-                    if (lane == 0 && !KT::is_none(cd)) KT::atomic_max(&cand[ok_], cd, &flags[b]);
-#pragma unroll
-                    for (int a = 0; a < DM; ++a)
-                        if (a < D) {
-                            T v1 = c_smax[k][a], v2 = c_smin[k][a], v3 = c_jmax[k][a], v4 = c_jmin[k][a];
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) {
-                                v1 = fmax(v1, __shfl_xor_sync(0xffffffffu, v1, o));
-                                v2 = fmin(v2, __shfl_xor_sync(0xffffffffu, v2, o));
-                                v3 = fmax(v3, __shfl_xor_sync(0xffffffffu, v3, o));
-                                v4 = fmin(v4, __shfl_xor_sync(0xffffffffu, v4, o));
-                            }
-                            const size_t o = ok_ * D + a;
-                            if (lane == 0) {
-                                if (v1 != -INF) atomic_max_val(&smax[o], v1);
-                                if (v2 != INF) atomic_min_val(&smin[o], v2);
-                                if (v3 != -INF) atomic_max_val(&jmax[o], v3);
-                                if (v4 != INF) atomic_min_val(&jmin[o], v4);
-                            }
-                        }
-                }
-            if (__any_sync(0xffffffffu, infeasible) && lane == 0) atomicOr(&flags[b], 1u);
+    for (int k = 0; k < KM; ++k) seed_id[k] = (seeds && k < K) ? seeds[k] : -1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *tx = reinterpret_cast<T *>(smem);
+    uint32_t *lists = reinterpret_cast<uint32_t *>(tx + (size_t)D * tile);
+    uint32_t *tids = lists + NWV * kSub;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *list = lists + warp * kSub;
+    for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
+        int b;
+        int64_t st;
+        list_item(L.tile_prefix, L.B, w, tile, &b, &st);
+        const int64_t nb = L.seg_n[b];
+        const int tn = (int)((nb - st) < (int64_t)tile ? (nb - st) : (int64_t)tile);
+        __syncthreads();
+        for (int j = threadIdx.x; j < tn; j += kThreads) tids[j] = L.pool[L.seg_off[b] + st + j];
+        __syncthreads();
+        for (int i = threadIdx.x; i < D * tile; i += kThreads) {
+            const int a = i / tile, j = i - a * tile;
+            tx[i] = j < tn ? X[(size_t)a * ld + tids[j]] : T(0);
         }
+        __syncthreads();
+        const int n0 = L.node_start ? L.node_start[b] : b, n1 = L.node_start ? L.node_start[b + 1] : b + 1;
+        const int teams = (n1 - n0) < NWV ? (n1 - n0) : NWV, wpt = NWV / teams, team = warp / wpt;
+        if (team < teams)
+            for (int nd = n0 + team; nd < n1; nd += teams)
+                pass_b_node<T, KM, DM, RMX>(tx, tile, tn, (warp % wpt) * 32, wpt * 32, tids, nullptr, 0, list, nd, K, D,
+                                            RM, lo_in, hi_in, blo, bhi, repx, nreps, allhave, alpha, mg, seed_id, cnt,
+                                            smax, smin, jmax, jmin, cand, flags);
+        (void)lane;
     }
 }
 
@@ -891,7 +1015,8 @@ int reps_cap(int D, int cap) { return std::min(cap, std::min(kMaxReps, 2 * D + 1
 template <typename T, int KM, int DM, int RMX>
 kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi_, int B, double alpha,
                        const int64_t *seeds, int cap, void *lo_out_, void *hi_out_, int64_t *counts, int64_t *cand_out,
-                       double *lb, double *lb_raw, int64_t *lbarg, int8_t *status, VisitScratch *vs)
+                       double *lb, double *lb_raw, int64_t *lbarg, int8_t *status, VisitScratch *vs,
+                       const ListBatch *L = nullptr)
 {
     using KY = typename Key<T>::K;
     const int K_ = c->K, D = c->D;
@@ -939,16 +1064,30 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     int gA = 1;
     const int64_t tilesA = (v.n + tileA - 1) / tileA;
     auto kA = visit_a_kernel<T, KM, DM>;
-    KC_TRY(grid_of(c, kA, smemA, tilesA, &gA));
-    if (sizeof(T) == 8) gA = 1;   // single-writer key merge (see Key<double>)
-    if (v.n > 0) {
-        kA<<<gA, kThreads, smemA, c->stream>>>(static_cast<const T *>(v.X), v.ld, v.n, tileA, lo, hi, B, K_, D, alpha,
-                                              mg, lbkey, amax, amin, flags);
-        KC_TRY(after_launch(c, "tighten pass A"));
+    if (L) {
+        // list mode: one node per work item, tile = list_tile() gathered ids
+        const int lt = list_tile();
+        const size_t smem = (size_t)D * lt * 8 + (size_t)lt * 4;
+        auto kAL = visit_a_list_kernel<T, KM, DM>;
+        int g = 1;
+        KC_TRY(grid_of(c, kAL, smem, std::max<int64_t>(1, L->W), &g));
+        if (L->W > 0) {
+            kAL<<<g, kThreads, smem, c->stream>>>(static_cast<const T *>(c->X), c->ldx, *L, lt, lo, hi, K_, D, alpha,
+                                                  mg, lbkey, amax, amin, flags);
+            KC_TRY(after_launch(c, "tighten pass A (lists)"));
+        }
+    } else {
+        KC_TRY(grid_of(c, kA, smemA, tilesA, &gA));
+        if (sizeof(T) == 8) gA = 1;   // single-writer key merge (see Key<double>)
+        if (v.n > 0) {
+            kA<<<gA, kThreads, smemA, c->stream>>>(static_cast<const T *>(v.X), v.ld, v.n, tileA, lo, hi, B, K_, D,
+                                                  alpha, mg, lbkey, amax, amin, flags);
+            KC_TRY(after_launch(c, "tighten pass A"));
+        }
     }
     FinA fa;
     fa.seeds = seeds;
-    fa.ids = v.ids;
+    fa.ids = L ? nullptr : v.ids;   // list-mode keys already hold sample ids
     fa.r_up = r_up;
     fa.alpha = alpha;
     fa.defl = deflate_factor(c->dt, D);
@@ -966,6 +1105,19 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     const size_t smemB = (size_t)D * tileB * sizeof(T) + (size_t)NWV * kSub * 4;
     int gB = 1;
     auto kB = visit_b_kernel<T, KM, DM, RMX>;
+    if (L) {
+        const int lt = list_tile();
+        const size_t smem = (size_t)D * lt * sizeof(T) + (size_t)NWV * kSub * 4 + (size_t)lt * 4;
+        auto kBL = visit_b_list_kernel<T, KM, DM, RMX>;
+        int g = 1;
+        KC_TRY(grid_of(c, kBL, smem, std::max<int64_t>(1, L->W), &g));
+        if (L->W > 0) {
+            kBL<<<g, kThreads, smem, c->stream>>>(static_cast<const T *>(c->X), c->ldx, *L, lt, K_, D, RM, lo, hi, blo,
+                                                  bhi, repx, nreps, have, alpha, mg, seeds, cnt, smax, smin, jmax, jmin,
+                                                  cand, flags);
+            KC_TRY(after_launch(c, "tighten pass B (lists)"));
+        }
+    } else {
     KC_TRY(grid_of(c, kB, smemB, (v.n + tileB - 1) / tileB, &gB));
     if (sizeof(T) == 8) gB = 1;   // single-writer key merge (see Key<double>)
     if (v.n > 0) {
@@ -974,8 +1126,9 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
                                               cand, flags);
         KC_TRY(after_launch(c, "tighten pass B"));
     }
+    }
     finalize_b_kernel<T><<<(B + 127) / 128, 128, 0, c->stream>>>(B, K_, D, cnt, smax, smin, jmax, jmin, cand, flags,
-                                                                v.ids, r_up, static_cast<T *>(lo_out_),
+                                                                L ? nullptr : v.ids, r_up, static_cast<T *>(lo_out_),
                                                                 static_cast<T *>(hi_out_), counts, cand_out, status);
     KC_TRY(after_launch(c, "tighten finalize B"));
     vs->reps = reps;
@@ -1021,6 +1174,33 @@ kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const vo
         return tighten_impl<double, 4, 4, 9>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
                                              lb_raw, lbarg, status, vs);
     return set_err(c, KC_EINVAL, "kc_tighten: double data supported for K <= 4, D <= 4 (K=%d, D=%d)", c->K, c->D);
+}
+
+kc_status launch_tighten_list(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, double alpha,
+                              const int64_t *seeds_dev, int ball_cap, void *lo_out, void *hi_out, int64_t *counts,
+                              int64_t *cand, double *lb, double *lb_raw, int64_t *lbarg, int8_t *status,
+                              VisitScratch *vs)
+{
+    if (B <= 0) return KC_OK;
+    if (c->dt != KC_F32) return set_err(c, KC_EINTERNAL, "list-mode tightening is for float data");
+    const int cap = ball_cap > 0 ? ball_cap : 50;
+    const View v = full_view(c);
+    if (c->K == 3 && c->D == 3)
+        return tighten_impl<float, 3, 3, 7>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
+                                            lb_raw, lbarg, status, vs, &L);
+    if (c->K == 3 && c->D == 4)
+        return tighten_impl<float, 3, 4, 9>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
+                                            lb_raw, lbarg, status, vs, &L);
+    if (c->K <= 4 && c->D <= 2)
+        return tighten_impl<float, 4, 2, 5>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
+                                            lb_raw, lbarg, status, vs, &L);
+    if (c->K <= 4 && c->D <= 4)
+        return tighten_impl<float, 4, 4, 9>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
+                                            lb_raw, lbarg, status, vs, &L);
+    if (c->K <= 2 && c->D <= 8)
+        return tighten_impl<float, 2, 8, 17>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
+                                             lb_raw, lbarg, status, vs, &L);
+    return set_err(c, KC_EINVAL, "kc_tighten: float data supported for K <= 4 with D <= 4, or K <= 2 with D <= 8");
 }
 
 kc_status launch_sample_reduction_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int M,

@@ -182,8 +182,10 @@ def test_solve_small_workload_f64(n):
     g, r = _solve_both(X, 3)
     assert g["status"] == 0
     assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"]
-    # the stop rule is (UB - LB) / UB <= 1e-12, evaluated in double
-    assert g["lower_bound"] <= g["objective"] and g["gap"] <= 1e-12 * (1 + 1e-6)
+    # the stop rule is UB - LB <= 1e-12 UB; the reported LB is UB (1 - 1e-12)
+    # rounded to double (error <= 2^-53 UB, 1 - 1e-12 itself off by <= 2^-53)
+    # and the reported gap is rounded again: gap <= 1e-12 + 4 * 2^-53.
+    assert g["lower_bound"] <= g["objective"] and g["gap"] <= 1e-12 + 4 * 2.0**-53
     assert oracle.objective(X, g["centers"])[0] == g["objective"]
     if n == 60:
         assert abs(g["objective"] - oracle.bruteforce(X, 3)[0]) <= 1e-12 * g["objective"]
@@ -195,6 +197,42 @@ def test_solve_f32_small(k):
     g, r = _solve_both(X, k)
     assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
     assert oracle.objective(X, g["centers"])[0] == g["objective"]
+
+
+@pytest.mark.parametrize("lists", [0, 1])
+@pytest.mark.parametrize("recipe", ["blobs2", "batched4", "outliers2"])
+def test_solve_f32_lists_and_shared_set(recipe, lists):
+    """Per-node surviving-sample lists (Section 4.2) and the shared compacted
+    set reach the oracle's optimum; list mode really drops samples."""
+    if recipe == "blobs2":
+        X, k = _blobs(4_000, 2, 3, seed=21, dtype=np.float32), 3
+    elif recipe == "batched4":
+        X, k = synth.make_workload("batched_solve", n=2_500)[0], 3
+    else:
+        X, k = synth.make_workload("learned_order", n=3_000)[0], 4
+    g, r = _solve_both(X, k, lists=lists)
+    assert g["status"] == 0
+    assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
+    assert oracle.objective(X, g["centers"])[0] == g["objective"]
+    if lists:
+        assert g["lists_filtered"] > 0 and g["samples_dropped"] > 0
+    else:
+        assert g["lists_filtered"] == 0
+
+
+def test_solve_lists_with_a_full_arena():
+    """With the list arena barely larger than the root list most children
+    inherit their parent's list; the certificate is unchanged."""
+    X = _blobs(240_000, 2, 3, seed=23, dtype=np.float32)
+    kc = KCenter(_t(X), 3)
+    tight = kc.solve(tol=1e-12, lists=1, arena_mb=1)
+    roomy = kc.solve(tol=1e-12, lists=1)
+    shared = kc.solve(tol=1e-12, lists=0)
+    assert tight["status"] == roomy["status"] == shared["status"] == 0
+    z = shared["objective"]
+    assert tight["objective"] == roomy["objective"] == z
+    assert oracle.objective(X, tight["centers"])[0] == z
+    assert tight["samples_dropped"] < roomy["samples_dropped"]
 
 
 def test_solve_plain_bb_and_no_sample_reduction():
