@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--n", type=int, default=None, help="override N (testing only)")
+    p.add_argument("--solve-n", type=int, default=1_000_000,
+                   help="N of the batched-solve workload timed to a certified optimum (0: skip)")
+    p.add_argument("--solve-time-limit", type=float, default=120.0)
     return p.parse_args()
 
 
@@ -259,6 +262,31 @@ def main():
                 "peak_basis": f"FP32 pipe: {sms} SMs x 128 lanes x {f_mhz:.0f} MHz (median SM clock sampled)",
                 "hbm_gbs": n * w.d * 4 / (ms * 1e-3) / 1e9}
 
+    # ---- time to a certified optimum (kc_solve, tol 1e-12) on the
+    # batched-solve recipe, data resident in HBM; every rank solves its own
+    # instance (seeded by rank), the slowest rank counts
+    solve = None
+    if args.solve_n > 0:
+        Xs, ws_ = synth.make_workload("batched_solve", n=args.solve_n, seed=2 + rank)
+        Xsd = torch.from_numpy(Xs).to(dev)
+        kc = kcm.KCenter(Xsd, ws_.k)
+        torch.cuda.synchronize()
+        barrier()
+        r = kc.solve(tol=1e-12, time_limit_s=args.solve_time_limit)
+        torch.cuda.synchronize()
+        secs = r["seconds"]
+        if ws > 1:
+            t = torch.tensor([secs], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            secs = float(t[0])
+        solve = {"workload": f"batched_solve: N={args.solve_n:,} D={ws_.d} K={ws_.k} float32, weights .6/.3/.1",
+                 "metric": "time to certified optimum (tol 1e-12)", "seconds": secs,
+                 "certified": r["status"] == 0, "objective": r["objective"], "lower_bound": r["lower_bound"],
+                 "gap": r["gap"], "nodes": int(r["nodes"]), "batches": int(r["batches"]),
+                 "lists_filtered": int(r["lists_filtered"])}
+        kc.close()
+        del Xsd
+
     cfg = config_dict(n, w)
     cfg["autotuned"] = {"samples_per_thread": tuned_st, "nodes_per_launch": tuned_chunk}
     line = {
@@ -267,6 +295,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
         "clocks": ck, "e2e": e2e, "gpu_launches": int(launches) * ws, "roofline": roofline,
     }
+    if solve is not None:
+        line["solve"] = solve
     if rank == 0 and not args.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(X, lo, hi, 200_000)
         line["cpu_baseline"] = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
