@@ -729,7 +729,13 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 f[6] = (float)lmax;
                 f[7] = (float)lmin;
                 f[8] = (float)(zero / KD);
-                f[9] = seeds_found ? 1.f : 0.f;
+                // range of rule 1's variable against the largest range (0 when rule 1 has none)
+                {
+                    const int v0 = rule0[i], v1 = rule1[i];
+                    const double r0 = (double)hi[v0] - (double)lo[v0];
+                    const double r1 = v1 >= 0 ? (double)hi[v1] - (double)lo[v1] : 0.0;
+                    f[9] = v1 >= 0 && r0 > 0 ? (float)(std::log2(r1 / r0 + 9.094947017729282e-13) / -40.0) : 1.f;
+                }
                 f[10] = std::isfinite(h_ub[b]) ? (float)std::max(-1.0, std::min(1.0, (h_ub[b] - alpha) / al)) : 1.f;
                 f[11] = (float)std::max(0.0, std::min(1.0, (nd.key - nd.pkey) / al));
             }
@@ -745,7 +751,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 }
             }
             if (log && o.log_labels) {
-                // strong-branching labels: the smaller child bound under each rule
+                // strong-branching labels: both children bounded under each rule
                 int nl = 0;
                 std::vector<int> li;
                 for (int i = 0; i < NB; ++i) {
@@ -773,11 +779,13 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                     KC_TRY(launch_lower_bounds_view(c, cur, d_llo, d_lhi, nl, d_llb, nullptr, nullptr, 0));
                     KC_CUDA(c, cudaMemcpyAsync(h_llb.data(), d_llb, (size_t)nl * 8, cudaMemcpyDeviceToHost, c->stream));
                     KC_CUDA(c, cudaStreamSynchronize(c->stream));
+                    // the rule whose children gain more bound on average; no
+                    // label where the two are within 1e-9 alpha
                     for (size_t q = 0; q < li.size(); ++q) {
-                        const double r0 = std::min(h_llb[4 * q], h_llb[4 * q + 1]);
-                        const double r1 = std::min(h_llb[4 * q + 2], h_llb[4 * q + 3]);
+                        const double r0 = 0.5 * (h_llb[4 * q] + h_llb[4 * q + 1]);
+                        const double r1 = 0.5 * (h_llb[4 * q + 2] + h_llb[4 * q + 3]);
                         lab[li[q]] = r1 > r0 ? 1 : 0;
-                        lab_mask[li[q]] = 1;
+                        lab_mask[li[q]] = std::fabs(r1 - r0) > 1e-9 * alpha ? 1 : 0;
                     }
                 }
             }

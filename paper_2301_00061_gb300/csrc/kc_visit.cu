@@ -91,11 +91,7 @@ __device__ __forceinline__ typename Key<T>::K warp_kmax(typename Key<T>::K v)
     return v;
 }
 
-// ordered-integer min/max of values (no position)
-__device__ __forceinline__ void atomic_max_val(unsigned *p, float v) { atomicMax(p, ord_f32(v)); }
-__device__ __forceinline__ void atomic_min_val(unsigned *p, float v) { atomicMin(p, ord_f32(v)); }
-__device__ __forceinline__ void atomic_max_val(unsigned long long *p, double v) { atomicMax(p, ord_f64(v)); }
-__device__ __forceinline__ void atomic_min_val(unsigned long long *p, double v) { atomicMin(p, ord_f64(v)); }
+// values as order-preserving unsigned integers (no position)
 template <typename T>
 using OrdT = typename std::conditional<sizeof(T) == 4, unsigned, unsigned long long>::type;
 __device__ __forceinline__ float from_ord(unsigned u) { return unord_f32(u); }
@@ -338,7 +334,7 @@ visit_a_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, const T
 // List mode: work item w = one tile of a group's sample-id list (see
 // ListBatch); the CTA evaluates every node of the group on the staged tile.
 template <typename T, int KM, int DM>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 visit_a_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile,
                     const T *__restrict__ lo, const T *__restrict__ hi, int K, int D, double alpha, Margins mg,
                     typename Key<T>::K *__restrict__ lbkey, typename Key<T>::K *__restrict__ amax,
@@ -507,58 +503,71 @@ __global__ void finalize_a_kernel(int B, int K, int D, const T *__restrict__ lo,
 
 constexpr int kSub = 256;   // samples flagged per warp before processing
 
+// Per-warp shared-memory state of pass B for one node: the node's boxes
+// (read by every lane, so kept once per warp instead of once per thread) and
+// the warp's running bounding boxes, merged into global memory at the end.
+template <typename T, int KM, int DM>
+struct PBSlot {
+    uint64_t bx[KM][DM];                 // float data: packed (lo, -hi) of the input boxes
+    T ilo[KM][DM], ihi[KM][DM];          // double data: input boxes
+    T l[KM][DM], h[KM][DM], mid[KM][DM]; // box-BT boxes and their midpoints
+    OrdT<T> smax[KM][DM], smin[KM][DM];  // bbox of S_+ (ordered integers)
+    OrdT<T> jmax[KM][DM], jmin[KM][DM];  // bbox of the sample-based assigned samples
+};
+
+__device__ __forceinline__ unsigned to_ord(float v) { return ord_f32(v); }
+__device__ __forceinline__ unsigned long long to_ord(double v) { return ord_f64(v); }
+
 template <typename T, int KM, int DM, int RMX>
 __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int jstart, int wstep, const uint32_t *tids,
-                                            const uint32_t *__restrict__ ids, int64_t base, uint32_t *list, int b,
-                                            int K, int D, int RM, const T *__restrict__ lo_in,
-                                            const T *__restrict__ hi_in, const T *__restrict__ blo,
-                                            const T *__restrict__ bhi, const T *__restrict__ repx,
-                                            const int *__restrict__ nreps, const int *__restrict__ allhave,
-                                            double alpha, const Margins &mg, const int64_t *seed_id,
-                                            unsigned long long *__restrict__ cnt, OrdT<T> *__restrict__ smax,
-                                            OrdT<T> *__restrict__ smin, OrdT<T> *__restrict__ jmax,
-                                            OrdT<T> *__restrict__ jmin, typename Key<T>::K *__restrict__ cand,
-                                            unsigned *__restrict__ flags)
+                                            const uint32_t *__restrict__ ids, int64_t base, uint32_t *list,
+                                            PBSlot<T, KM, DM> *ws, int b, int K, int D, int RM,
+                                            const T *__restrict__ lo_in, const T *__restrict__ hi_in,
+                                            const T *__restrict__ blo, const T *__restrict__ bhi,
+                                            const T *__restrict__ repx, const int *__restrict__ nreps,
+                                            const int *__restrict__ allhave, double alpha, const Margins &mg,
+                                            const int64_t *seed_id, unsigned long long *__restrict__ cnt,
+                                            OrdT<T> *__restrict__ smax, OrdT<T> *__restrict__ smin,
+                                            OrdT<T> *__restrict__ jmax, OrdT<T> *__restrict__ jmin,
+                                            typename Key<T>::K *__restrict__ cand, unsigned *__restrict__ flags)
 {
     using KT = Key<T>;
     using KY = typename KT::K;
+    using OT = OrdT<T>;
     constexpr bool F32 = sizeof(T) == 4;
     constexpr int DH = (DM + 1) / 2;
     const int lane = threadIdx.x & 31;
     const double four_alpha = 4.0 * alpha;
     // node b: input boxes (center-based status), box-BT boxes, midpoints
-    uint64_t bx[KM][DM];
-    double ilo[KM][DM], ihi[KM][DM];
-    T l[KM][DM], h[KM][DM], mid[KM][DM];
+    for (int i = lane; i < KM * DM; i += 32) {
+        const int k = i / DM, a = i % DM;
+        const bool in = k < K && a < D;
+        const size_t o = ((size_t)b * K + k) * D + a;
+        if constexpr (F32) ws->bx[k][a] = in ? pk((float)lo_in[o], -(float)hi_in[o]) : pk(0.f, -0.f);
+        else { ws->ilo[k][a] = in ? lo_in[o] : T(0); ws->ihi[k][a] = in ? hi_in[o] : T(0); }
+        const T lv = in ? blo[o] : T(0), hv = in ? bhi[o] : T(0);
+        ws->l[k][a] = lv;
+        ws->h[k][a] = hv;
+        if constexpr (F32) ws->mid[k][a] = (float)(0.5 * ((double)lv + (double)hv));
+        else ws->mid[k][a] = 0.5 * (lv + hv);
+        ws->smax[k][a] = (OT)0;
+        ws->smin[k][a] = ~(OT)0;
+        ws->jmax[k][a] = (OT)0;
+        ws->jmin[k][a] = ~(OT)0;
+    }
     int nr[KM];
 #pragma unroll
-    for (int k = 0; k < KM; ++k) {
-        nr[k] = k < K ? nreps[(size_t)b * K + k] : 0;
-#pragma unroll
-        for (int a = 0; a < DM; ++a) {
-            const bool in = k < K && a < D;
-            const size_t o = ((size_t)b * K + k) * D + a;
-            if constexpr (F32) bx[k][a] = in ? pk((float)lo_in[o], -(float)hi_in[o]) : pk(0.f, -0.f);
-            else { ilo[k][a] = in ? (double)lo_in[o] : 0.0; ihi[k][a] = in ? (double)hi_in[o] : 0.0; }
-            l[k][a] = in ? blo[o] : T(0);
-            h[k][a] = in ? bhi[o] : T(0);
-            if constexpr (F32) mid[k][a] = in ? (float)(0.5 * ((double)l[k][a] + (double)h[k][a])) : 0.f;
-            else mid[k][a] = in ? 0.5 * (l[k][a] + h[k][a]) : 0.0;
-        }
-    }
+    for (int k = 0; k < KM; ++k) nr[k] = k < K ? nreps[(size_t)b * K + k] : 0;
     const bool have = allhave[b] != 0;
     const T *rxb = repx + (size_t)b * K * RM * D;
     unsigned long long c_cnt[KM];
-    T c_smax[KM][DM], c_smin[KM][DM], c_jmax[KM][DM], c_jmin[KM][DM];
     KY c_cand[KM];
-    const T INF = F32 ? (T)__int_as_float(0x7f800000) : (T)__longlong_as_double(0x7ff0000000000000ll);
 #pragma unroll
     for (int k = 0; k < KM; ++k) {
         c_cnt[k] = 0;
         c_cand[k] = KT::none();
-#pragma unroll
-        for (int a = 0; a < DM; ++a) { c_smax[k][a] = -INF; c_smin[k][a] = INF; c_jmax[k][a] = -INF; c_jmin[k][a] = INF; }
     }
+    __syncwarp();
     bool infeasible = false;
     for (int r0 = jstart; r0 < tn; r0 += 8 * wstep) {
         // phase 1: flag the samples that need representative distances
@@ -581,9 +590,11 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
                             uint64_t px[DM];
 #pragma unroll
                             for (int a = 0; a < DM; ++a) px[a] = pk(x[a], -x[a]);
-                            excl = box_dist_f32<DM>(px, bx[k]) > mg.t_alpha;
+                            excl = box_dist_f32<DM>(px, ws->bx[k]) > mg.t_alpha;
                         } else {
-                            excl = box_dist_f64<DM>(reinterpret_cast<const double *>(x), ilo[k], ihi[k], D) > alpha;
+                            excl = box_dist_f64<DM>(reinterpret_cast<const double *>(x),
+                                                    reinterpret_cast<const double *>(ws->ilo[k]),
+                                                    reinterpret_cast<const double *>(ws->ihi[k]), D) > alpha;
                         }
                         if (!excl) ++left;
                     }
@@ -602,7 +613,7 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
                         bool inb = true;
 #pragma unroll
                         for (int a = 0; a < DM; ++a)
-                            if (a < D && (x[a] < l[k][a] || x[a] > h[k][a])) inb = false;
+                            if (a < D && (x[a] < ws->l[k][a] || x[a] > ws->h[k][a])) inb = false;
                         if (inb) fl |= 2u << k;
                     }
             }
@@ -663,17 +674,12 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
                         if ((far4 & mk) == 0ull) { ++left; k1 = k; }
                     }
                 if (left == 0) infeasible = true;
-                if (left == 1) {
-#pragma unroll
-                    for (int k = 0; k < KM; ++k)
-                        if (k == k1) {
-#pragma unroll
-                            for (int a = 0; a < DM; ++a) {
-                                c_jmax[k][a] = x[a] > c_jmax[k][a] ? x[a] : c_jmax[k][a];
-                                c_jmin[k][a] = x[a] < c_jmin[k][a] ? x[a] : c_jmin[k][a];
-                            }
-                        }
-                }
+                if (left == 1)
+                    for (int a = 0; a < D; ++a) {
+                        const OT v = to_ord(x[a]);
+                        atomicMax(&ws->jmax[k1][a], v);
+                        atomicMin(&ws->jmin[k1][a], v);
+                    }
             }
             // ball-based tightening and centers on samples (Algorithm 4)
 #pragma unroll
@@ -682,20 +688,21 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
                     const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
                     if (far1 & mk) continue;
                     ++c_cnt[k];
-#pragma unroll
-                    for (int a = 0; a < DM; ++a) {
-                        c_smax[k][a] = x[a] > c_smax[k][a] ? x[a] : c_smax[k][a];
-                        c_smin[k][a] = x[a] < c_smin[k][a] ? x[a] : c_smin[k][a];
+                    for (int a = 0; a < D; ++a) {
+                        const OT v = to_ord(x[a]);
+                        atomicMax(&ws->smax[k][a], v);
+                        atomicMin(&ws->smin[k][a], v);
                     }
                     T dm;
                     if constexpr (F32) {
                         uint64_t pm[DH];
 #pragma unroll
                         for (int p = 0; p < DH; ++p)
-                            pm[p] = pk(mid[k][2 * p], 2 * p + 1 < DM ? mid[k][2 * p + 1] : 0.f);
+                            pm[p] = pk(ws->mid[k][2 * p], 2 * p + 1 < DM ? ws->mid[k][2 * p + 1] : 0.f);
                         dm = pt_dist_f32<2 * DH>(px, pm);
                     } else {
-                        dm = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), mid[k], D);
+                        dm = pt_dist_f64<DM>(reinterpret_cast<const double *>(x),
+                                             reinterpret_cast<const double *>(ws->mid[k]), D);
                     }
                     c_cand[k] = kmax<T>(c_cand[k], KT::min_of(dm, pos));
                 }
@@ -713,26 +720,17 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
             const size_t ok_ = (size_t)b * K + k;
             if (lane == 0 && cn) atomicAdd(&cnt[ok_], cn);
             if (lane == 0 && !KT::is_none(cd)) KT::atomic_max(&cand[ok_], cd, &flags[b]);
-#pragma unroll
-            for (int a = 0; a < DM; ++a)
-                if (a < D) {
-                    T v1 = c_smax[k][a], v2 = c_smin[k][a], v3 = c_jmax[k][a], v4 = c_jmin[k][a];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        v1 = fmax(v1, __shfl_xor_sync(0xffffffffu, v1, o));
-                        v2 = fmin(v2, __shfl_xor_sync(0xffffffffu, v2, o));
-                        v3 = fmax(v3, __shfl_xor_sync(0xffffffffu, v3, o));
-                        v4 = fmin(v4, __shfl_xor_sync(0xffffffffu, v4, o));
-                    }
-                    const size_t o = ok_ * D + a;
-                    if (lane == 0) {
-                        if (v1 != -INF) atomic_max_val(&smax[o], v1);
-                        if (v2 != INF) atomic_min_val(&smin[o], v2);
-                        if (v3 != -INF) atomic_max_val(&jmax[o], v3);
-                        if (v4 != INF) atomic_min_val(&jmin[o], v4);
-                    }
-                }
         }
+    __syncwarp();
+    for (int i = lane; i < K * D; i += 32) {
+        const int k = i / D, a = i % D;
+        const size_t o = ((size_t)b * K + k) * D + a;
+        if (ws->smax[k][a] != (OT)0) atomicMax(&smax[o], ws->smax[k][a]);
+        if (ws->smin[k][a] != ~(OT)0) atomicMin(&smin[o], ws->smin[k][a]);
+        if (ws->jmax[k][a] != (OT)0) atomicMax(&jmax[o], ws->jmax[k][a]);
+        if (ws->jmin[k][a] != ~(OT)0) atomicMin(&jmin[o], ws->jmin[k][a]);
+    }
+    __syncwarp();   // the slot is rewritten by the warp's next node
     if (__any_sync(0xffffffffu, infeasible) && lane == 0) atomicOr(&flags[b], 1u);
 }
 
@@ -752,6 +750,7 @@ visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, 
     extern __shared__ __align__(16) unsigned char smem[];
     T *tx = reinterpret_cast<T *>(smem);                                        // [D][tile]
     uint32_t *lists = reinterpret_cast<uint32_t *>(tx + (size_t)D * tile);      // [warps][kSub]
+    auto *slots = reinterpret_cast<PBSlot<T, KM, DM> *>(lists + NWV * kSub);   // [warps]
     const int warp = threadIdx.x >> 5;
     uint32_t *list = lists + warp * kSub;
     for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
@@ -763,15 +762,15 @@ visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, 
         }
         __syncthreads();
         for (int b = warp; b < B; b += NWV)
-            pass_b_node<T, KM, DM, RMX>(tx, tile, tn, 0, 32, nullptr, ids, base, list, b, K, D, RM, lo_in, hi_in, blo,
-                                        bhi, repx, nreps, allhave, alpha, mg, seed_id, cnt, smax, smin, jmax, jmin,
-                                        cand, flags);
+            pass_b_node<T, KM, DM, RMX>(tx, tile, tn, 0, 32, nullptr, ids, base, list, slots + warp, b, K, D, RM,
+                                        lo_in, hi_in, blo, bhi, repx, nreps, allhave, alpha, mg, seed_id, cnt, smax,
+                                        smin, jmax, jmin, cand, flags);
     }
 }
 
 // List mode of pass B (see visit_a_list_kernel).
 template <typename T, int KM, int DM, int RMX>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 visit_b_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile, int K,
                     int D, int RM, const T *__restrict__ lo_in, const T *__restrict__ hi_in, const T *__restrict__ blo,
                     const T *__restrict__ bhi, const T *__restrict__ repx, const int *__restrict__ nreps,
@@ -784,9 +783,10 @@ visit_b_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile, 
 #pragma unroll
     for (int k = 0; k < KM; ++k) seed_id[k] = (seeds && k < K) ? seeds[k] : -1;
     extern __shared__ __align__(16) unsigned char smem[];
-    T *tx = reinterpret_cast<T *>(smem);
-    uint32_t *lists = reinterpret_cast<uint32_t *>(tx + (size_t)D * tile);
-    uint32_t *tids = lists + NWV * kSub;
+    T *tx = reinterpret_cast<T *>(smem);                                        // [D][tile]
+    uint32_t *lists = reinterpret_cast<uint32_t *>(tx + (size_t)D * tile);      // [warps][kSub]
+    auto *slots = reinterpret_cast<PBSlot<T, KM, DM> *>(lists + NWV * kSub);   // [warps]
+    uint32_t *tids = reinterpret_cast<uint32_t *>(slots + NWV);                 // [tile]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *list = lists + warp * kSub;
     for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
@@ -807,9 +807,9 @@ visit_b_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile, 
         const int teams = (n1 - n0) < NWV ? (n1 - n0) : NWV, wpt = NWV / teams, team = warp / wpt;
         if (team < teams)
             for (int nd = n0 + team; nd < n1; nd += teams)
-                pass_b_node<T, KM, DM, RMX>(tx, tile, tn, (warp % wpt) * 32, wpt * 32, tids, nullptr, 0, list, nd, K, D,
-                                            RM, lo_in, hi_in, blo, bhi, repx, nreps, allhave, alpha, mg, seed_id, cnt,
-                                            smax, smin, jmax, jmin, cand, flags);
+                pass_b_node<T, KM, DM, RMX>(tx, tile, tn, (warp % wpt) * 32, wpt * 32, tids, nullptr, 0, list,
+                                            slots + warp, nd, K, D, RM, lo_in, hi_in, blo, bhi, repx, nreps, allhave,
+                                            alpha, mg, seed_id, cnt, smax, smin, jmax, jmin, cand, flags);
         (void)lane;
     }
 }
@@ -1102,12 +1102,13 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     // pass B
     const int tileB = (int)std::max<int64_t>(256, std::min<int64_t>(2048, (32 * 1024) / (D * (int64_t)sizeof(T))) / 32 * 32);
     static_assert(kThreads / 32 * kSub * 4 <= 16 * 1024, "pass B lists");
-    const size_t smemB = (size_t)D * tileB * sizeof(T) + (size_t)NWV * kSub * 4;
+    const size_t slotB = (size_t)NWV * sizeof(PBSlot<T, KM, DM>);
+    const size_t smemB = (size_t)D * tileB * sizeof(T) + (size_t)NWV * kSub * 4 + slotB;
     int gB = 1;
     auto kB = visit_b_kernel<T, KM, DM, RMX>;
     if (L) {
         const int lt = list_tile();
-        const size_t smem = (size_t)D * lt * sizeof(T) + (size_t)NWV * kSub * 4 + (size_t)lt * 4;
+        const size_t smem = (size_t)D * lt * sizeof(T) + (size_t)NWV * kSub * 4 + slotB + (size_t)lt * 4;
         auto kBL = visit_b_list_kernel<T, KM, DM, RMX>;
         int g = 1;
         KC_TRY(grid_of(c, kBL, smem, std::max<int64_t>(1, L->W), &g));

@@ -3,8 +3,8 @@
 The solver writes one JSON line per branched node when given a ``log_path``
 (features, parent link, the branching rules' variables and, with
 ``log_labels``, a strong-branching label: 1 when the rule "split the nearest box
-where the bound-attaining sample lies farthest outside" gives a larger smaller
-child bound than max-range).  This module turns such logs into a training set
+where the bound-attaining sample lies farthest outside" gives its two children
+a larger mean lower bound than max-range, unmasked only where the two differ).  This module turns such logs into a training set
 -- priority target log2(1 + number of branched descendants) / 10, rule target
 the label -- and trains the scorer on the GPU with the library's kernels.
 
