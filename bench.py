@@ -53,6 +53,18 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(x, ws):
+    """The largest value of x over all ranks (the slowest replica's time);
+    a plain CPU all-reduce on the process group's gloo backend."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -217,10 +229,7 @@ def main():
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     launches = kcm.kc_launch_count(h) - launches0
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
+    ms = max_over_ranks(ms, ws)
     evals_per_step = B_NODES * n
     value = evals_per_step * ws / (ms * 1e-3)
 
@@ -240,10 +249,7 @@ def main():
         kcm.kc_destroy(h2)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t[0])
+    e2e_s = max_over_ranks(e2e_s, ws)
     e2e = {"value": evals_per_step * ws / e2e_s, "unit": "evals/s",
            "h2d_bytes_per_step": int(X.nbytes + lo.nbytes + hi.nbytes),
            "d2h_bytes_per_step": int(lbh.numel() * 8 + argh.numel() * 8),
@@ -257,8 +263,14 @@ def main():
     ops_per_eval = 3 * w.k * w.d
     achieved = ops_per_eval * evals_per_step / (ms * 1e-3) / 1e12
     peak = sms * 128 * f_mhz * 1e6 / 1e12
+    # DRAM traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    # from an ncu capture of this kernel at N = 5e6 with 4 samples per thread and
+    # 256 nodes per launch: reads scale with N, the per-CTA partials do not.
+    traffic = None
+    if (tuned_st, tuned_chunk) == (4, B_NODES) and w.d == 8 and w.k == 5:
+        traffic = 160_141_568 * (n / 5e6) + 3_646_720
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": traffic,
                 "peak_basis": f"FP32 pipe: {sms} SMs x 128 lanes x {f_mhz:.0f} MHz (median SM clock sampled)",
                 "hbm_gbs": n * w.d * 4 / (ms * 1e-3) / 1e9}
 
@@ -275,10 +287,7 @@ def main():
         r = kc.solve(tol=1e-12, time_limit_s=args.solve_time_limit)
         torch.cuda.synchronize()
         secs = r["seconds"]
-        if ws > 1:
-            t = torch.tensor([secs], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            secs = float(t[0])
+        secs = max_over_ranks(secs, ws)
         solve = {"workload": f"batched_solve: N={args.solve_n:,} D={ws_.d} K={ws_.k} float32, weights .6/.3/.1",
                  "metric": "time to certified optimum (tol 1e-12)", "seconds": secs,
                  "certified": r["status"] == 0, "objective": r["objective"], "lower_bound": r["lower_bound"],

@@ -132,6 +132,8 @@ def main(argv=None):
     X, T, M = generate(inst, node_limit=a.node_limit)
     p, loss = train_scorer(X, T, M, epochs=a.epochs)
     save(p, a.out, {"samples": int(len(X)), "instances": a.instances, "epochs": a.epochs, "loss": loss,
+                    "node_limit": a.node_limit,
+                    "command": "python -m paper_2301_00061_gb300.scorer train " + " ".join(argv or sys.argv[1:]),
                     "label_rate": float(T[M[:, 1] > 0, 1].mean()) if (M[:, 1] > 0).any() else None})
     print(json.dumps({"samples": int(len(X)), "loss": loss, "out": a.out}))
 
