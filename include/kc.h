@@ -231,15 +231,17 @@ kc_status kc_sample_reduction(kc_ctx *ctx, const void *lo, const void *hi, int32
 /*
  * The learned node scorer: a 12 -> 64 -> 64 -> 2 perceptron with ReLU
  * activations, bfloat16 weight matrices and float32 biases, activations and
- * accumulation.  Output 0 ranks open nodes, output 1 is the logit of the
- * branching rule (> 0: split the box that is nearest to the sample attaining
- * the node's lower bound, on the attribute where that sample lies farthest
- * outside it; otherwise the max-range rule of Section 3.3).  The paper has no
+ * accumulation.  Output r predicts the cost (log2 of the number of branched
+ * nodes in the subtree, / 10) of branching a node with rule r: rule 0 is the
+ * max-range rule of Section 3.3, rule 1 splits the box nearest to the sample
+ * attaining the node's lower bound, on the attribute where that sample lies
+ * farthest outside it.  The solver takes the cheaper rule and orders equal
+ * lower bounds by the smaller predicted cost.  The paper has no
  * learned component: the exact lower bound still decides every prune, so the
  * certified optimum cannot change.  Parameters are one float vector of 5122
  * values [W1 64x12, b1 64, W2 64x64, b2 64, W3 2x64, b3 2] (row major);
- * training minimizes the mean of m0 (y0 - t0)^2 / 2 + m1 (softplus(y1) - t1 y1)
- * with Adam.  Arrays may be host or device memory.
+ * training minimizes the mean of m0 (y0 - t0)^2 / 2 + m1 (y1 - t1)^2 / 2 with
+ * Adam.  Arrays may be host or device memory.
  */
 typedef struct kc_mlp kc_mlp;
 kc_status kc_mlp_create(const float *params, void *stream, kc_mlp **out);
@@ -273,7 +275,9 @@ typedef struct {
     int32_t lists;         /* 1: every node keeps its own list of surviving samples (float data, Section
                               4.2); 0: all nodes of a batch scan one shared sample set */
     int32_t verbose;       /* 0; 1: per-phase timings on stderr */
-    int32_t log_labels;    /* 0; 1: the node log also carries strong-branching labels (extra bound passes) */
+    int32_t explore;       /* 0; p in (0, 100]: on p % of the nodes where the two branching rules
+                              differ, take a random one (seeded by seed and node id): training
+                              data for the scorer, with log_path */
     int32_t arena_mb;      /* 0: automatic; device memory (MiB) that holds the per-node lists */
     uint64_t seed;         /* 0: FFT start = seed mod N */
     const char *log_path;  /* NULL, or a file receiving one JSON line per branched node (scorer features) */

@@ -6,8 +6,8 @@ Definition (the same one the CUDA kernels implement):
   z1 = W1 x + b1, h1 = relu(z1)      W1: 64 x 12
   z2 = W2 h1 + b2, h2 = relu(z2)     W2: 64 x 64
   y  = W3 h2 + b3                    W3: 2 x 64
-  y[0] is the node priority (regression), y[1] the branching-rule logit.
-  Per-sample loss: m0 * (y0 - t0)^2 / 2 + m1 * (softplus(y1) - t1 * y1);
+  y[r] is the predicted cost of branching a node with rule r (regression).
+  Per-sample loss: m0 * (y0 - t0)^2 / 2 + m1 * (y1 - t1)^2 / 2;
   the batch loss is the mean over samples.
 The forward and backward passes use the weight matrices rounded to bfloat16
 (round to nearest, ties to even); biases stay in float32.  The parameter vector
@@ -83,19 +83,11 @@ def forward(theta, X, bf16=True):
     return y, (X, z1, h1, z2, h2)
 
 
-def softplus(v):
-    return np.logaddexp(0.0, v)
-
-
-def sigmoid(v):
-    return 0.5 * (1.0 + np.tanh(0.5 * v))
-
-
 def loss(theta, X, T, M, bf16=True):
     y, _ = forward(theta, X, bf16)
     T = np.asarray(T, dtype=np.float64)
     M = np.asarray(M, dtype=np.float64)
-    per = M[:, 0] * 0.5 * (y[:, 0] - T[:, 0]) ** 2 + M[:, 1] * (softplus(y[:, 1]) - T[:, 1] * y[:, 1])
+    per = M[:, 0] * 0.5 * (y[:, 0] - T[:, 0]) ** 2 + M[:, 1] * 0.5 * (y[:, 1] - T[:, 1]) ** 2
     return per.mean()
 
 
@@ -109,7 +101,7 @@ def grad(theta, X, T, M, bf16=True):
     M = np.asarray(M, dtype=np.float64)
     dy = np.empty_like(y)
     dy[:, 0] = M[:, 0] * (y[:, 0] - T[:, 0])
-    dy[:, 1] = M[:, 1] * (sigmoid(y[:, 1]) - T[:, 1])
+    dy[:, 1] = M[:, 1] * (y[:, 1] - T[:, 1])
     dy /= n
     g = {}
     g["W3"] = dy.T @ h2
@@ -122,7 +114,7 @@ def grad(theta, X, T, M, bf16=True):
     dz1 = dh1 * (z1 > 0)
     g["W1"] = dz1.T @ X
     g["b1"] = dz1.sum(0)
-    per = M[:, 0] * 0.5 * (y[:, 0] - T[:, 0]) ** 2 + M[:, 1] * (softplus(y[:, 1]) - T[:, 1] * y[:, 1])
+    per = M[:, 0] * 0.5 * (y[:, 0] - T[:, 0]) ** 2 + M[:, 1] * 0.5 * (y[:, 1] - T[:, 1]) ** 2
     return per.mean(), pack(g)
 
 

@@ -43,7 +43,7 @@ class SolveOpts(C.Structure):
     _fields_ = [
         ("tol", C.c_double), ("time_limit_s", C.c_double), ("node_limit", C.c_int64),
         ("batch", C.c_int32), ("ball_cap", C.c_int32), ("i_sr", C.c_int32), ("use_bt", C.c_int32),
-        ("order", C.c_int32), ("lists", C.c_int32), ("verbose", C.c_int32), ("log_labels", C.c_int32),
+        ("order", C.c_int32), ("lists", C.c_int32), ("verbose", C.c_int32), ("explore", C.c_int32),
         ("arena_mb", C.c_int32),
         ("seed", C.c_uint64),
         ("log_path", C.c_char_p),

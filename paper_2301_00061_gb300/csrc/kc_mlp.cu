@@ -1,12 +1,12 @@
 // kc_mlp.cu -- the learned node scorer: a 12 -> 64 -> 64 -> 2 ReLU perceptron
 // with bfloat16 weight matrices and float32 biases, activations and
-// accumulation.  Output 0 is a node priority, output 1 the logit of the
-// branching rule.  Inference (one warp per node), training (a fused forward +
+// accumulation.  Output r is the predicted cost (log2 of the subtree size / 10)
+// of branching a node with rule r.  Inference (one warp per node), training (a fused forward +
 // backward kernel over chunks of 32 samples staged in shared memory, gradient
 // sums merged with atomics, then Adam) -- all hand-written.
 //
-// Loss per sample: m0 (y0 - t0)^2 / 2 + m1 (softplus(y1) - t1 y1), averaged
-// over the batch.  Parameter vector: [W1 64x12, b1 64, W2 64x64, b2 64,
+// Loss per sample: m0 (y0 - t0)^2 / 2 + m1 (y1 - t1)^2 / 2, averaged over the
+// batch.  Parameter vector: [W1 64x12, b1 64, W2 64x64, b2 64,
 // W3 2x64, b3 2] (row major), 5122 floats.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -83,8 +83,6 @@ __global__ void mlp_forward_kernel(Weights W, const float *__restrict__ feats, i
     }
 }
 
-__device__ __forceinline__ float softplusf(float v) { return v > 20.f ? v : log1pf(expf(v)); }
-__device__ __forceinline__ float sigmoidf(float v) { return 1.f / (1.f + expf(-v)); }
 
 // Gradient of the mean loss over the n samples idx[0..n) (idx NULL: 0..n-1),
 // added into grad[NPARAM]; the loss added into *loss.
@@ -124,11 +122,11 @@ mlp_grad_kernel(Weights W, const float *__restrict__ feats, const float *__restr
             warp_forward(W, x, z1a, z1b, z2a, z2b, y0, y1);
             const float t0 = targets[(size_t)s * 2], t1 = targets[(size_t)s * 2 + 1];
             const float m0 = masks[(size_t)s * 2], m1 = masks[(size_t)s * 2 + 1];
-            const float dy0 = m0 * (y0 - t0) * inv_n, dy1 = m1 * (sigmoidf(y1) - t1) * inv_n;
+            const float dy0 = m0 * (y0 - t0) * inv_n, dy1 = m1 * (y1 - t1) * inv_n;
             if (lane == 0) {
                 dys[j * 2] = dy0;
                 dys[j * 2 + 1] = dy1;
-                const float l = m0 * 0.5f * (y0 - t0) * (y0 - t0) + m1 * (softplusf(y1) - t1 * y1);
+                const float l = m0 * 0.5f * (y0 - t0) * (y0 - t0) + m1 * 0.5f * (y1 - t1) * (y1 - t1);
                 atomicAdd(loss, l * inv_n);
             }
             h1s[j * NH + lane] = fmaxf(z1a, 0.f);

@@ -395,7 +395,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     std::vector<T> h_pts((size_t)Bmax * D);
     std::vector<float> h_feat((size_t)Bmax * 12), h_out((size_t)Bmax * 2);
     std::vector<T> h_llo((size_t)4 * Bmax * KD), h_lhi((size_t)4 * Bmax * KD);
-    std::vector<double> h_llb((size_t)4 * Bmax), h_ub(Bmax);
+    std::vector<double> h_ub(Bmax);
 
     std::vector<double> h_raw(Bmax), h_ref(Bmax);
     // Float data: a bound whose float value cannot decide the prune (its
@@ -687,9 +687,8 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         const int NB = (int)br.size();
         std::vector<int> rule1(NB, -1), choice(rule0);
         std::vector<float> prio(NB, 0.f);
-        std::vector<int8_t> lab(NB, 0), lab_mask(NB, 0);
         const bool want_feat = scorer != nullptr || log != nullptr;
-        if (NB > 0 && (want_feat || (log && o.log_labels))) {
+        if (NB > 0 && want_feat) {
             // coordinates of each node's lower-bound sample, for rule 1
             std::vector<int64_t> ids(NB);
             for (int i = 0; i < NB; ++i) ids[i] = h_arg[br[i]];
@@ -745,48 +744,25 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 c->launches += 1;
                 KC_CUDA(c, cudaMemcpyAsync(h_out.data(), d_out, (size_t)NB * 2 * 4, cudaMemcpyDeviceToHost, c->stream));
                 KC_CUDA(c, cudaStreamSynchronize(c->stream));
+                // output r: predicted cost of branching with rule r; take the cheaper
                 for (int i = 0; i < NB; ++i) {
-                    prio[i] = h_out[(size_t)i * 2];
-                    if (h_out[(size_t)i * 2 + 1] > 0.f && rule1[i] >= 0) choice[i] = rule1[i];
+                    const float c0 = h_out[(size_t)i * 2], c1 = h_out[(size_t)i * 2 + 1];
+                    const bool take1 = rule1[i] >= 0 && c1 < c0;
+                    if (take1) choice[i] = rule1[i];
+                    prio[i] = take1 ? c1 : c0;
                 }
             }
-            if (log && o.log_labels) {
-                // strong-branching labels: both children bounded under each rule
-                int nl = 0;
-                std::vector<int> li;
+            if (o.explore > 0) {
+                // training data: on explore % of the nodes where the two rules
+                // differ, a uniformly random rule, drawn from the seed and the node
+                // id (splitmix64 finalizer)
                 for (int i = 0; i < NB; ++i) {
                     if (rule1[i] < 0 || rule1[i] == rule0[i]) continue;
-                    const int b = br[i];
-                    const T *lo = h_lo2 + (size_t)b * KD, *hi = h_hi2 + (size_t)b * KD;
-                    for (int r = 0; r < 2; ++r) {
-                        const int v = r == 0 ? rule0[i] : rule1[i];
-                        T m, succ;
-                        split_point<T>(lo[v], hi[v], &m, &succ);
-                        for (int side = 0; side < 2; ++side) {
-                            T *cl = &h_llo[(size_t)nl * KD], *ch = &h_lhi[(size_t)nl * KD];
-                            std::memcpy(cl, lo, KD * sizeof(T));
-                            std::memcpy(ch, hi, KD * sizeof(T));
-                            if (side == 0) ch[v] = m;
-                            else cl[v] = succ;
-                            ++nl;
-                        }
-                    }
-                    li.push_back(i);
-                }
-                if (nl > 0) {
-                    KC_CUDA(c, cudaMemcpyAsync(d_llo, h_llo.data(), (size_t)nl * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-                    KC_CUDA(c, cudaMemcpyAsync(d_lhi, h_lhi.data(), (size_t)nl * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-                    KC_TRY(launch_lower_bounds_view(c, cur, d_llo, d_lhi, nl, d_llb, nullptr, nullptr, 0));
-                    KC_CUDA(c, cudaMemcpyAsync(h_llb.data(), d_llb, (size_t)nl * 8, cudaMemcpyDeviceToHost, c->stream));
-                    KC_CUDA(c, cudaStreamSynchronize(c->stream));
-                    // the rule whose children gain more bound on average; no
-                    // label where the two are within 1e-9 alpha
-                    for (size_t q = 0; q < li.size(); ++q) {
-                        const double r0 = 0.5 * (h_llb[4 * q] + h_llb[4 * q + 1]);
-                        const double r1 = 0.5 * (h_llb[4 * q + 2] + h_llb[4 * q + 3]);
-                        lab[li[q]] = r1 > r0 ? 1 : 0;
-                        lab_mask[li[q]] = std::fabs(r1 - r0) > 1e-9 * alpha ? 1 : 0;
-                    }
+                    uint64_t z = o.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(batch[br[i]].id + 1);
+                    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+                    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+                    z ^= z >> 31;
+                    if ((z & 0xFFFFFFFFull) % 100 < (uint64_t)o.explore) choice[i] = (z >> 63) ? rule1[i] : rule0[i];
                 }
             }
         }
@@ -850,9 +826,9 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             const T *lo = h_lo2 + (size_t)b * KD, *hi = h_hi2 + (size_t)b * KD;
             if (log) {
                 fprintf(log, "{\"id\":%lld,\"parent\":%lld,\"depth\":%d,\"lb\":%.17g,\"alpha\":%.17g,\"rule\":%d,"
-                             "\"rule0\":%d,\"rule1\":%d,\"label\":%d,\"label_mask\":%d,\"feat\":[",
+                             "\"rule0\":%d,\"rule1\":%d,\"feat\":[",
                         (long long)nd.id, (long long)nd.parent, nd.depth, nd.key, alpha, choice[i] == rule0[i] ? 0 : 1,
-                        rule0[i], rule1[i], (int)lab[i], (int)lab_mask[i]);
+                        rule0[i], rule1[i]);
                 for (int q = 0; q < 12; ++q) fprintf(log, q ? ",%.8g" : "%.8g", (double)h_feat[(size_t)i * 12 + q]);
                 fprintf(log, "]}\n");
             }
@@ -1191,6 +1167,7 @@ kc_status kc_solve(kc_ctx *c, double tol, const kc_solve_opts *opt, kc_result *o
     if (o.order == 1 && !c->scorer) return set_err(c, KC_EINVAL, "kc_solve: order = 1 needs kc_set_scorer");
     if (o.lists != 0 && o.lists != 1) return set_err(c, KC_EINVAL, "kc_solve: lists must be 0 or 1");
     if (o.arena_mb < 0) return set_err(c, KC_EINVAL, "kc_solve: arena_mb must be >= 0");
+    if (o.explore < 0 || o.explore > 100) return set_err(c, KC_EINVAL, "kc_solve: explore must be in [0, 100]");
     std::memset(out, 0, sizeof(*out));
     if (c->dt == KC_F32) return solve_impl<float>(c, o, out);
     return solve_impl<double>(c, o, out);

@@ -1,12 +1,20 @@
 """Training data and training for the learned node scorer.
 
-The solver writes one JSON line per branched node when given a ``log_path``
-(features, parent link, the branching rules' variables and, with
-``log_labels``, a strong-branching label: 1 when the rule "split the nearest box
-where the bound-attaining sample lies farthest outside" gives its two children
-a larger mean lower bound than max-range, unmasked only where the two differ).  This module turns such logs into a training set
--- priority target log2(1 + number of branched descendants) / 10, rule target
-the label -- and trains the scorer on the GPU with the library's kernels.
+The scorer predicts, for a node about to be branched, the cost of branching it
+with each rule: output r = log2(1 + number of branched nodes in the subtree) / 10
+when rule r is applied (rule 0: max-range; rule 1: split the box nearest to the
+sample attaining the node's bound, on the attribute where that sample lies
+farthest outside).  The solver takes the cheaper rule.
+
+Training data come from the solver itself: with ``explore`` set it branches
+that percentage of the nodes with a random one of the two rules (where they
+differ) and, given a ``log_path``, writes one JSON line per branched node
+(features, parent, the rule taken).  A node's subtree size is counted from the
+log and becomes the target of the output of the rule that was taken; where the
+two rules coincide it is the target of both.  Round 1 explores every node under
+max-range; round 2 explores 30 % of the nodes under the round-1 model, and the
+model is retrained on both rounds' data.  Training runs on the GPU with the
+library's kernels.
 
     python -m paper_2301_00061_gb300.scorer train --out weights.json
 """
@@ -41,8 +49,16 @@ def dataset_from_log(records):
         if p in idx:
             size[idx[p]] += size[i]
     X = np.array([r["feat"] for r in records], np.float32)
-    T = np.stack([np.log2(1.0 + size) / 10.0, np.array([r["label"] for r in records], np.float64)], 1)
-    M = np.stack([np.ones(len(records)), np.array([r["label_mask"] for r in records], np.float64)], 1)
+    cost = np.log2(1.0 + size) / 10.0
+    T = np.stack([cost, cost], 1)
+    M = np.zeros((len(records), 2))
+    for i, r in enumerate(records):
+        if r["rule1"] < 0:
+            M[i, 0] = 1.0                      # only max-range applies
+        elif r["rule1"] == r["rule0"]:
+            M[i, :] = 1.0                      # both rules split the same variable
+        else:
+            M[i, r["rule"]] = 1.0
     return X, T.astype(np.float32), M.astype(np.float32)
 
 
@@ -63,18 +79,37 @@ def family_instances(count, seed=100, n_lo=10_000, n_hi=200_000):
     return out
 
 
-def generate(instances, node_limit=20_000, time_limit=60.0, batch=256):
-    """Solve each instance with logging and labels; concatenated dataset."""
+def outlier_instances(count, seed=200, n_lo=10_000, n_hi=200_000):
+    """Seeded training instances shaped like the learned-order workload: four
+    equal blobs in 2-D plus 1 % uniform outliers, K = 4."""
+    import synth
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
+        X = synth.gaussian_mixture(n, 2, (0.25,) * 4, (1.0,) * 4, (1.0,) * 4, 10.0, seed=int(rng.integers(1 << 30)),
+                                   outlier_frac=0.01, dtype=np.float32)
+        out.append((X, 4))
+    return out
+
+
+def generate(instances, node_limit=20_000, time_limit=60.0, batch=256, seed=1, params=None, explore=100):
+    """Solve each instance with exploration and logging; concatenated dataset.
+    With ``params``, the scorer they define picks the rule on the nodes that
+    are not explored (on-policy data); otherwise max-range does."""
     import torch
-    from . import KCenter
+    from . import KCenter, Scorer
+    sc = Scorer(params) if params is not None else None
     feats, targs, masks = [], [], []
-    for X, k in instances:
+    for i, (X, k) in enumerate(instances):
         with tempfile.NamedTemporaryFile(suffix=".jsonl", delete=False) as tf:
             path = tf.name
         try:
             kc = KCenter(torch.from_numpy(X).cuda(), k)
-            kc.solve(tol=1e-12, log_path=path, log_labels=1, node_limit=node_limit, time_limit_s=time_limit,
-                     batch=batch)
+            if sc is not None:
+                kc.set_scorer(sc)
+            kc.solve(tol=1e-12, log_path=path, explore=explore, order=1 if sc is not None else 0, seed=seed + i,
+                     node_limit=node_limit, time_limit_s=time_limit, batch=batch)
             kc.close()
             Xf, T, M = dataset_from_log(read_log(path))
         finally:
@@ -82,6 +117,8 @@ def generate(instances, node_limit=20_000, time_limit=60.0, batch=256):
         feats.append(Xf)
         targs.append(T)
         masks.append(M)
+    if sc is not None:
+        sc.close()
     return np.concatenate(feats), np.concatenate(targs), np.concatenate(masks)
 
 
@@ -123,18 +160,26 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("cmd", choices=["train"])
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
-    ap.add_argument("--instances", type=int, default=12)
-    ap.add_argument("--epochs", type=int, default=40)
-    ap.add_argument("--node-limit", type=int, default=20_000)
+    ap.add_argument("--instances", type=int, default=12, help="batched-solve family instances")
+    ap.add_argument("--outlier-instances", type=int, default=6, help="outlier family instances")
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--node-limit", type=int, default=8_000)
+    ap.add_argument("--rounds", type=int, default=2,
+                    help="1: random-rule data only; 2: then on-policy data from the first model, retrain on both")
+    ap.add_argument("--explore", type=int, default=30, help="percent of random rules in on-policy rounds")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(HERE))
-    inst = family_instances(a.instances)
+    inst = family_instances(a.instances) + outlier_instances(a.outlier_instances)
     X, T, M = generate(inst, node_limit=a.node_limit)
     p, loss = train_scorer(X, T, M, epochs=a.epochs)
-    save(p, a.out, {"samples": int(len(X)), "instances": a.instances, "epochs": a.epochs, "loss": loss,
-                    "node_limit": a.node_limit,
-                    "command": "python -m paper_2301_00061_gb300.scorer train " + " ".join(argv or sys.argv[1:]),
-                    "label_rate": float(T[M[:, 1] > 0, 1].mean()) if (M[:, 1] > 0).any() else None})
+    for r in range(1, a.rounds):
+        X2, T2, M2 = generate(inst, node_limit=a.node_limit, seed=1000 * r + 1, params=p, explore=a.explore)
+        X, T, M = np.concatenate([X, X2]), np.concatenate([T, T2]), np.concatenate([M, M2])
+        p, loss = train_scorer(X, T, M, epochs=a.epochs)
+    save(p, a.out, {"samples": int(len(X)), "instances": a.instances, "outlier_instances": a.outlier_instances,
+                    "epochs": a.epochs, "loss": loss, "node_limit": a.node_limit, "rounds": a.rounds,
+                    "explore": a.explore,
+                    "command": "python -m paper_2301_00061_gb300.scorer train " + " ".join(argv or sys.argv[1:])})
     print(json.dumps({"samples": int(len(X)), "loss": loss, "out": a.out}))
 
 

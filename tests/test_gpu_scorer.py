@@ -55,7 +55,7 @@ def test_training_fits_a_teacher():
     teacher = mlp.init_params(11)
     X, _, M = _data(4096, 5)
     y, _ = mlp.forward(teacher, X)
-    T = np.stack([y[:, 0], (y[:, 1] > 0)], 1).astype(np.float32)
+    T = y.astype(np.float32)
     M[:] = 1.0
     student = mlp.init_params(12)
     l0 = mlp.loss(student, X, T, M)
@@ -67,12 +67,14 @@ def test_training_fits_a_teacher():
 
 
 def test_learned_order_keeps_the_optimum():
-    """Any scorer (here an untrained one) only changes the order of nodes and
-    the branching variable; every prune still uses the exact bound."""
+    """Any scorer only changes the order of nodes and the branching variable;
+    every prune still uses the exact bound.  Here the output layer is zero and
+    its biases make rule 1 (seed 0) or max-range (seed 1) the cheaper rule."""
     for seed in (0, 1):
         X = synth.gaussian_mixture(2_500, 2, (0.4, 0.3, 0.3), (1.0,) * 3, (1.0,) * 3, 10.0, seed, dtype=np.float32)
         theta = mlp.init_params(seed)
-        theta[-1] = 5.0 if seed == 0 else -5.0            # rule logit forced either way
+        theta[-130:] = 0.0
+        theta[-1] = -5.0 if seed == 0 else 5.0            # predicted cost of rule 1
         kc = KCenter(torch.from_numpy(X).cuda(), 3)
         sc = Scorer(theta)
         kc.set_scorer(sc)
@@ -84,12 +86,13 @@ def test_learned_order_keeps_the_optimum():
 
 
 def test_trained_scorer_gains_over_best_bound():
-    """The committed scorer (trained on solver logs of the batched-solve
-    family, seeds 100..) against plain best-bound ordering with max-range
-    branching on held-out instances: eight family instances drawn with seed
-    999, three 3000-sample blob sets whose best-bound trees are large, and the
-    batched-solve recipe at N = 200,000.  Same certified optimum on every
-    instance; fewer nodes in total."""
+    """The committed scorer (trained on exploring solves of the batched-solve
+    family, seeds 100.., and the outlier family, seeds 200..) against plain
+    best-bound ordering with max-range branching on held-out instances: eight
+    family instances drawn with seed 999, three 3000-sample blob sets whose
+    best-bound trees are large, the batched-solve recipe at N = 200,000 and
+    three outlier-family instances drawn with seed 998.  Same certified
+    optimum on every instance; fewer nodes in total."""
     from paper_2301_00061_gb300 import scorer as S
     w = S.load()
     inst = S.family_instances(8, seed=999)
@@ -97,6 +100,7 @@ def test_trained_scorer_gains_over_best_bound():
         inst.append((synth.gaussian_mixture(3_000, 2, (1 / 3,) * 3, (1.0,) * 3, (1.0,) * 3, 10.0, s,
                                             dtype=np.float32), 3))
     inst.append((synth.make_workload("batched_solve", n=200_000)[0], 3))
+    inst += S.outlier_instances(3, seed=998)
     sc = Scorer(w)
     rows, tot = [], {0: 0, 1: 0}
     for X, k in inst:

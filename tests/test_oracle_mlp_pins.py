@@ -48,10 +48,15 @@ def test_special_cases():
     X, T, M = _data(5, 2)
     y, _ = mlp.forward(theta, X)
     assert np.all(y[:, 0] == 0.25) and np.all(y[:, 1] == -1.5)
-    # loss with zero outputs: (t0^2)/2 for the regression head, log(2) - 0 for the logit head
+    # loss with zero outputs: t^2 / 2 for each head; with outputs equal to the
+    # targets (biases set to constant targets): zero
     z = np.zeros(mlp.NPARAM, np.float32)
     L = mlp.loss(z, X, T, np.ones_like(M))
-    assert L == pytest.approx(np.mean(0.5 * T[:, 0] ** 2 + np.log(2.0)), rel=1e-14)
+    assert L == pytest.approx(np.mean(0.5 * T[:, 0] ** 2 + 0.5 * T[:, 1] ** 2), rel=1e-14)
+    Tc = np.tile(np.array([[0.25, -1.5]]), (5, 1))
+    assert mlp.loss(theta, X, Tc, np.ones_like(M)) == 0.0
+    # a masked head contributes nothing
+    assert mlp.loss(z, X, T, np.stack([np.ones(5), np.zeros(5)], 1)) == pytest.approx(np.mean(0.5 * T[:, 0] ** 2))
     # the first Adam step moves every parameter with a non-zero gradient by about lr against it
     g = np.array([3.0, -0.5, 0.0])
     th, m, v = mlp.adam_step(np.zeros(3), np.zeros(3), np.zeros(3), g, 1, lr=0.01)
