@@ -261,19 +261,24 @@ seg_obj_exact(const float *__restrict__ X, int64_t ld, ListBatch L, const float 
 // and for the upper bound (outside every box, or some representative of each
 // box that holds it proved farther than alpha).  Output: appended to the
 // node's region out_pool[out_off[b] ...], count in out_n[b] (unordered tiles).
+// With ckeys, the lower bounds of node b's two children over the surviving
+// samples come out of the same pass: child 0 has hi[cvar[b]] = csplit[2b],
+// child 1 has lo[cvar[b]] = csplit[2b + 1], all other bounds as node b's boxes
+// (packed keys ckeys[2b], ckeys[2b + 1]).
 template <int DMAX>
 __global__ void __launch_bounds__(256)
 seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float *__restrict__ lo,
                const float *__restrict__ hi, int K, int D, const float *__restrict__ beta_dn, float infl, float slack,
                float t_alpha, const float *__restrict__ repx, const int *__restrict__ nreps, int RM,
                const int *__restrict__ rmap, uint32_t *__restrict__ out_pool, const int64_t *__restrict__ out_off,
-               unsigned long long *__restrict__ out_n)
+               unsigned long long *__restrict__ out_n, const int *__restrict__ cvar, const float *__restrict__ csplit,
+               unsigned long long *__restrict__ ckeys)
 {
     // out_pool NULL: count the surviving samples only
     __shared__ uint64_t sbox[kMaxK * DMAX];
     __shared__ float sl[kMaxK * DMAX], sh[kMaxK * DMAX];
     __shared__ unsigned wsum[8];
-    __shared__ unsigned long long base_s;
+    __shared__ unsigned long long base_s, red[8];
     const int Dp = (D + 1) & ~1;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
@@ -292,6 +297,10 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
         __syncthreads();
         const float bth = beta_dn[b];
         const size_t rb = rmap ? (size_t)rmap[b] : (size_t)b;   // row of the node's representatives
+        // the children's split: box ks, attribute as_, at (cm | cs)
+        const int cv = ckeys ? cvar[b] : 0, ks = cv / D, as_ = cv % D;
+        const float cm = ckeys ? csplit[2 * b] : 0.f, cs = ckeys ? csplit[2 * b + 1] : 0.f;
+        unsigned long long best0 = 0ull, best1 = 0ull;
         for (int j0 = 0; j0 < tn; j0 += blockDim.x) {
             const int j = j0 + threadIdx.x;
             bool keep = false;
@@ -342,6 +351,25 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
                     if (!excl) ubred = false;
                 }
                 keep = !(lbred && ubred);
+                if (keep && ckeys) {
+                    // children's bounds over the surviving samples (the closed form
+                    // of Section 3.1 in the same float evaluation as seg_lb_f32)
+                    float other = __int_as_float(0x7f800000);
+                    for (int k = 0; k < K; ++k)
+                        if (k != ks) other = fminf(other, box_dist_rt<DMAX>(px, sbox + k * Dp, Dp));
+                    uint64_t cb[DMAX];
+#pragma unroll
+                    for (int a = 0; a < DMAX; ++a)
+                        cb[a] = a == as_ ? pk(sl[ks * D + as_], -cm) : (a < Dp ? sbox[ks * Dp + a] : pk(0.f, -0.f));
+                    const float d0 = box_dist_rt<DMAX>(px, cb, Dp);
+#pragma unroll
+                    for (int a = 0; a < DMAX; ++a)
+                        if (a == as_) cb[a] = pk(cs, -sh[ks * D + as_]);
+                    const float d1 = box_dist_rt<DMAX>(px, cb, Dp);
+                    const unsigned long long k0 = key_max(fminf(other, d0), id), k1 = key_max(fminf(other, d1), id);
+                    best0 = k0 > best0 ? k0 : best0;
+                    best1 = k1 > best1 ? k1 : best1;
+                }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
             if (lane == 0) wsum[wp] = __popc(bal);
@@ -359,6 +387,14 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
                 out_pool[out_off[b] + (int64_t)p] = id;
             }
             __syncthreads();
+        }
+        if (ckeys) {
+            best0 = block_max_u64(best0, red);
+            best1 = block_max_u64(best1, red);
+            if (threadIdx.x == 0) {
+                if (best0) atomicMax(&ckeys[2 * b], best0);
+                if (best1) atomicMax(&ckeys[2 * b + 1], best1);
+            }
         }
     }
 }
@@ -513,12 +549,14 @@ kc_status launch_seg_objective(kc_ctx *c, const ListBatch &L, const int64_t *cen
 
 kc_status launch_seg_filter(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B,
                             const float *beta_dn_dev, double alpha, const void *repx, const int *nreps, int RM,
-                            const int *rmap, uint32_t *out_pool, const int64_t *out_off, unsigned long long *out_n)
+                            const int *rmap, uint32_t *out_pool, const int64_t *out_off, unsigned long long *out_n,
+                            const int *cvar, const float *csplit, unsigned long long *ckeys, double *child_lb,
+                            double *child_raw)
 {
     if (c->D > kListMaxD) return set_err(c, KC_EINVAL, "list kernels: D <= %d (got %d)", kListMaxD, c->D);
     if (B <= 0) return KC_OK;
     KC_CUDA(c, cudaMemsetAsync(out_n, 0, (size_t)B * 8, c->stream));
-    if (L.W <= 0) return KC_OK;
+    if (ckeys) KC_CUDA(c, cudaMemsetAsync(ckeys, 0, (size_t)2 * B * 8, c->stream));
     const double g = gamma_n(f32_roundings(c->D), kU32);
     float infl = (float)(1.0 / (1.0 - g));
     if ((double)infl < 1.0 / (1.0 - g)) infl = nextafterf(infl, 2.f);
@@ -534,8 +572,15 @@ kc_status launch_seg_filter(kc_ctx *c, const ListBatch &L, const void *lo, const
                                                  static_cast<const float *>(lo), static_cast<const float *>(hi), c->K,
                                                  c->D, beta_dn_dev, infl, slack, t_alpha,
                                                  static_cast<const float *>(repx), nreps, RM, rmap, out_pool, out_off,
-                                                 out_n);
-    return after_launch(c, "list filter");
+                                                 out_n, cvar, csplit, ckeys);
+    KC_TRY(after_launch(c, "list filter"));
+    if (ckeys) {
+        keys_finalize<<<(2 * B + 127) / 128, 128, 0, c->stream>>>(ckeys, 2 * B, deflate_factor(KC_F32, c->D),
+                                                                  underflow_slack(KC_F32, c->D), child_lb, child_raw,
+                                                                  nullptr);
+        KC_TRY(after_launch(c, "list filter: children's bounds"));
+    }
+    return KC_OK;
 }
 
 }  // namespace kc

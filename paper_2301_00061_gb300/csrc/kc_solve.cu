@@ -419,10 +419,15 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     const size_t l_keys = (size_t)kSlots * slot_bytes, l_vmax = l_keys + (size_t)Bmax * 8;
     const size_t l_thr = l_vmax + (size_t)Bmax * 8, l_beta = l_thr + (size_t)Bmax * 4;
     const size_t l_off = l_beta + (size_t)Bmax * 4, l_n = l_off + (size_t)Bmax * 8;
-    const size_t l_end = l_n + (size_t)Bmax * 8 + 256;
-    unsigned long long *d_keys = nullptr, *d_vmax = nullptr, *d_outn = nullptr;
-    float *d_thr = nullptr, *d_beta = nullptr;
+    const size_t l_cvar = l_n + (size_t)Bmax * 8, l_csplit = l_cvar + (size_t)Bmax * 4;
+    const size_t l_ckeys = l_csplit + (size_t)2 * Bmax * 4, l_clb = l_ckeys + (size_t)2 * Bmax * 8;
+    const size_t l_craw = l_clb + (size_t)2 * Bmax * 8;
+    const size_t l_end = l_craw + (size_t)2 * Bmax * 8 + 256;
+    unsigned long long *d_keys = nullptr, *d_vmax = nullptr, *d_outn = nullptr, *d_ckeys = nullptr;
+    float *d_thr = nullptr, *d_beta = nullptr, *d_csplit = nullptr;
     int64_t *d_outoff = nullptr;
+    int *d_cvar = nullptr;
+    double *d_clb = nullptr, *d_craw = nullptr;
     int root_list = -1;
     if (lists) {
         KC_TRY(ensure(c, sb.lists, l_end));
@@ -433,6 +438,11 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         d_beta = reinterpret_cast<float *>(lb + l_beta);
         d_outoff = reinterpret_cast<int64_t *>(lb + l_off);
         d_outn = reinterpret_cast<unsigned long long *>(lb + l_n);
+        d_cvar = reinterpret_cast<int *>(lb + l_cvar);
+        d_csplit = reinterpret_cast<float *>(lb + l_csplit);
+        d_ckeys = reinterpret_cast<unsigned long long *>(lb + l_ckeys);
+        d_clb = reinterpret_cast<double *>(lb + l_clb);
+        d_craw = reinterpret_cast<double *>(lb + l_craw);
         if (cudaMallocHost(&sb.lpin, (size_t)kSlots * slot_bytes) != cudaSuccess) {
             sb.lpin = nullptr;
             cudaGetLastError();
@@ -645,6 +655,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         // 4. prune, close leaves, choose the branching variable, branch
         std::vector<int> br;          // batch indices of the nodes to branch
         std::vector<Node<T>> kids;
+        std::vector<int> kid_fused;   // index into flb/fraw, or -1
         std::vector<int> rule0;       // their max-range variable
         for (int b : live) {
             Node<T> &nd = batch[b];
@@ -769,7 +780,10 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         // the children's sample list: the samples of the node's list that are
         // not redundant for both bounds in its tightened boxes (Section 4.2);
         // the parent's list when there is no room or little is dropped
-        std::vector<int> kid_list(NB, -1);
+        // The filter also bounds the children over the surviving samples
+        // (flb/fraw[2 * row + side]); fused_row[i]: node i's row, or -1.
+        std::vector<int> kid_list(NB, -1), fused_row(NB, -1);
+        std::vector<double> flb, fraw;
         if (lists && NB > 0 && o.i_sr > 0 && batches % o.i_sr == 0) {
             std::vector<int> fi, rows;
             std::vector<int64_t> offs;
@@ -798,15 +812,35 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 KC_CUDA(c, cudaMemcpyAsync(d_lhi, h_lhi.data(), (size_t)nf * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
                 KC_CUDA(c, cudaMemcpyAsync(d_beta, bdn.data(), (size_t)nf * 4, cudaMemcpyHostToDevice, c->stream));
                 KC_CUDA(c, cudaMemcpyAsync(d_outoff, offs.data(), (size_t)nf * 8, cudaMemcpyHostToDevice, c->stream));
+                // the children's split (branching variable and value, as below)
+                std::vector<int> cvar(nf);
+                std::vector<float> csplit((size_t)2 * nf);
+                for (int q = 0; q < nf; ++q) {
+                    const int v = choice[fi[q]];
+                    const T *lq = h_lo2 + (size_t)rows[q] * KD, *hq = h_hi2 + (size_t)rows[q] * KD;
+                    T m, succ;
+                    split_point<T>(lq[v], hq[v], &m, &succ);
+                    cvar[q] = v;
+                    csplit[2 * q] = (float)m;
+                    csplit[2 * q + 1] = (float)succ;
+                }
+                KC_CUDA(c, cudaMemcpyAsync(d_cvar, cvar.data(), (size_t)nf * 4, cudaMemcpyHostToDevice, c->stream));
+                KC_CUDA(c, cudaMemcpyAsync(d_csplit, csplit.data(), (size_t)2 * nf * 4, cudaMemcpyHostToDevice, c->stream));
                 ListBatch Lf;
                 const int *rows_dev = nullptr;
                 KC_TRY(make_lb(3, nf, [&](int q) { return batch[rows[q]].list; }, rows.data(), &Lf, &rows_dev));
                 const bool bt = o.use_bt != 0;
                 KC_TRY(launch_seg_filter(c, Lf, d_llo, d_lhi, nf, d_beta, alpha, bt ? c->vs.repx : nullptr,
-                                         bt ? c->vs.nreps : nullptr, c->vs.RM, rows_dev, arena.ids(), d_outoff, d_outn));
+                                         bt ? c->vs.nreps : nullptr, c->vs.RM, rows_dev, arena.ids(), d_outoff, d_outn,
+                                         d_cvar, d_csplit, d_ckeys, d_clb, d_craw));
                 std::vector<unsigned long long> kept(nf);
+                flb.resize((size_t)2 * nf);
+                fraw.resize((size_t)2 * nf);
                 KC_CUDA(c, cudaMemcpyAsync(kept.data(), d_outn, (size_t)nf * 8, cudaMemcpyDeviceToHost, c->stream));
+                KC_CUDA(c, cudaMemcpyAsync(flb.data(), d_clb, (size_t)2 * nf * 8, cudaMemcpyDeviceToHost, c->stream));
+                KC_CUDA(c, cudaMemcpyAsync(fraw.data(), d_craw, (size_t)2 * nf * 8, cudaMemcpyDeviceToHost, c->stream));
                 KC_CUDA(c, cudaStreamSynchronize(c->stream));
+                for (int q = 0; q < nf; ++q) fused_row[fi[q]] = q;
                 for (int q = 0; q < nf; ++q) {
                     const int64_t n = list_n(batch[rows[q]].list), m = (int64_t)kept[q];
                     if ((double)m > 0.95 * (double)n) {
@@ -851,36 +885,61 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 ch.list = kid_list[i];
                 if (lists) arena.ref(ch.list);
                 kids.push_back(std::move(ch));
+                kid_fused.push_back(fused_row[i] >= 0 ? 2 * fused_row[i] + side : -1);
             }
         }
         // bound the children as they are created (Algorithm 1, Bounding); only
         // those below the incumbent enter the open set
+        std::vector<double> klb((size_t)Bmax), kraw((size_t)Bmax);
         for (size_t k0 = 0; k0 < kids.size(); k0 += (size_t)Bmax) {
             const int nk = (int)std::min(kids.size() - k0, (size_t)Bmax);
             for (int q = 0; q < nk; ++q) {
                 std::memcpy(h_lo + (size_t)q * KD, kids[k0 + q].lo.data(), KD * sizeof(T));
                 std::memcpy(h_hi + (size_t)q * KD, kids[k0 + q].hi.data(), KD * sizeof(T));
             }
-            KC_CUDA(c, cudaMemcpyAsync(d_lo, h_lo, (size_t)nk * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-            KC_CUDA(c, cudaMemcpyAsync(d_hi, h_hi, (size_t)nk * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
             const std::function<int(int)> kid_of = [&](int q) { return kids[k0 + q].list; };
-            if (lists) {
-                ListBatch Lk;
-                KC_TRY(make_lb(4, nk, kid_of, nullptr, &Lk, nullptr, true));
-                KC_TRY(launch_seg_lb(c, Lk, d_lo, d_hi, nk, d_keys, d_lb, d_raw, nullptr));
-            } else {
-                KC_TRY(launch_lower_bounds_view(c, cur, d_lo, d_hi, nk, d_lb, d_raw, nullptr, 0));
+            // children bounded by the filter take its values; the rest are
+            // bounded here over their lists (or the shared set)
+            std::vector<int> sub;
+            for (int q = 0; q < nk; ++q) {
+                const int f = kid_fused[k0 + q];
+                if (f >= 0) {
+                    klb[q] = flb[f];
+                    kraw[q] = fraw[f];
+                } else {
+                    sub.push_back(q);
+                }
             }
-            KC_CUDA(c, cudaMemcpyAsync(h_lb, d_lb, (size_t)nk * 8, cudaMemcpyDeviceToHost, c->stream));
-            KC_CUDA(c, cudaMemcpyAsync(h_raw.data(), d_raw, (size_t)nk * 8, cudaMemcpyDeviceToHost, c->stream));
-            KC_CUDA(c, cudaStreamSynchronize(c->stream));
+            if (!sub.empty()) {
+                const int ns = (int)sub.size();
+                for (int t = 0; t < ns; ++t) {
+                    std::memcpy(&h_llo[(size_t)t * KD], h_lo + (size_t)sub[t] * KD, KD * sizeof(T));
+                    std::memcpy(&h_lhi[(size_t)t * KD], h_hi + (size_t)sub[t] * KD, KD * sizeof(T));
+                }
+                KC_CUDA(c, cudaMemcpyAsync(d_lo, h_llo.data(), (size_t)ns * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+                KC_CUDA(c, cudaMemcpyAsync(d_hi, h_lhi.data(), (size_t)ns * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+                if (lists) {
+                    ListBatch Lk;
+                    KC_TRY(make_lb(4, ns, [&](int t) { return kids[k0 + sub[t]].list; }, nullptr, &Lk, nullptr, true));
+                    KC_TRY(launch_seg_lb(c, Lk, d_lo, d_hi, ns, d_keys, d_lb, d_raw, nullptr));
+                } else {
+                    KC_TRY(launch_lower_bounds_view(c, cur, d_lo, d_hi, ns, d_lb, d_raw, nullptr, 0));
+                }
+                KC_CUDA(c, cudaMemcpyAsync(h_lb, d_lb, (size_t)ns * 8, cudaMemcpyDeviceToHost, c->stream));
+                KC_CUDA(c, cudaMemcpyAsync(h_raw.data(), d_raw, (size_t)ns * 8, cudaMemcpyDeviceToHost, c->stream));
+                KC_CUDA(c, cudaStreamSynchronize(c->stream));
+                for (int t = 0; t < ns; ++t) {
+                    klb[sub[t]] = h_lb[t];
+                    kraw[sub[t]] = h_raw[t];
+                }
+            }
             amb.clear();
             for (int q = 0; q < nk; ++q) {
-                kids[k0 + q].key = std::max(kids[k0 + q].key, h_lb[q]);
-                if (ambiguous(kids[k0 + q].key, h_raw[q])) amb.push_back(q);
+                kids[k0 + q].key = std::max(kids[k0 + q].key, klb[q]);
+                if (ambiguous(kids[k0 + q].key, kraw[q])) amb.push_back(q);
             }
             if (!amb.empty()) {
-                KC_TRY(refine_nodes(cur, h_lo, h_hi, h_raw.data(), lists ? &kid_of : nullptr, 5));
+                KC_TRY(refine_nodes(cur, h_lo, h_hi, kraw.data(), lists ? &kid_of : nullptr, 5));
                 for (size_t i = 0; i < amb.size(); ++i)
                     kids[k0 + amb[i]].key = std::max(kids[k0 + amb[i]].key, h_ref[i]);
                 refined += (int64_t)amb.size();
@@ -897,6 +956,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             }
         }
         kids.clear();
+        kid_fused.clear();
         for (Node<T> &nd : batch) drop_list(nd);
 
         if (o.verbose) { prof[3] += now_s() - tA; tA = now_s(); }
