@@ -755,10 +755,17 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 c->launches += 1;
                 KC_CUDA(c, cudaMemcpyAsync(h_out.data(), d_out, (size_t)NB * 2 * 4, cudaMemcpyDeviceToHost, c->stream));
                 KC_CUDA(c, cudaStreamSynchronize(c->stream));
-                // output r: predicted cost of branching with rule r; take the cheaper
+                // output r: predicted cost of branching with rule r; take the cheaper,
+                // but rule 1 only on a variable whose range is at least 1/16 of the
+                // largest: splitting one short side over and over leaves the other
+                // boxes large, and tightening and list filtering then stall
                 for (int i = 0; i < NB; ++i) {
                     const float c0 = h_out[(size_t)i * 2], c1 = h_out[(size_t)i * 2 + 1];
-                    const bool take1 = rule1[i] >= 0 && c1 < c0;
+                    const T *lb2 = h_lo2 + (size_t)br[i] * KD, *hb2 = h_hi2 + (size_t)br[i] * KD;
+                    const bool wide = rule1[i] >= 0 &&
+                                      16.0 * ((double)hb2[rule1[i]] - (double)lb2[rule1[i]]) >=
+                                          (double)hb2[rule0[i]] - (double)lb2[rule0[i]];
+                    const bool take1 = wide && c1 < c0;
                     if (take1) choice[i] = rule1[i];
                     prio[i] = take1 ? c1 : c0;
                 }

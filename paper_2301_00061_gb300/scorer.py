@@ -179,7 +179,7 @@ def main(argv=None):
     save(p, a.out, {"samples": int(len(X)), "instances": a.instances, "outlier_instances": a.outlier_instances,
                     "epochs": a.epochs, "loss": loss, "node_limit": a.node_limit, "rounds": a.rounds,
                     "explore": a.explore,
-                    "command": "python -m paper_2301_00061_gb300.scorer train " + " ".join(argv or sys.argv[1:])})
+                    "command": "python -m paper_2301_00061_gb300.scorer " + " ".join(argv or sys.argv[1:])})
     print(json.dumps({"samples": int(len(X)), "loss": loss, "out": a.out}))
 
 
