@@ -867,9 +867,9 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             const T *lo = h_lo2 + (size_t)b * KD, *hi = h_hi2 + (size_t)b * KD;
             if (log) {
                 fprintf(log, "{\"id\":%lld,\"parent\":%lld,\"depth\":%d,\"lb\":%.17g,\"alpha\":%.17g,\"rule\":%d,"
-                             "\"rule0\":%d,\"rule1\":%d,\"feat\":[",
+                             "\"rule0\":%d,\"rule1\":%d,\"n\":%lld,\"feat\":[",
                         (long long)nd.id, (long long)nd.parent, nd.depth, nd.key, alpha, choice[i] == rule0[i] ? 0 : 1,
-                        rule0[i], rule1[i]);
+                        rule0[i], rule1[i], (long long)(lists ? list_n(nd.list) : cur.n));
                 for (int q = 0; q < 12; ++q) fprintf(log, q ? ",%.8g" : "%.8g", (double)h_feat[(size_t)i * 12 + q]);
                 fprintf(log, "]}\n");
             }
