@@ -231,12 +231,13 @@ kc_status kc_sample_reduction(kc_ctx *ctx, const void *lo, const void *hi, int32
 /*
  * The learned node scorer: a 12 -> 64 -> 64 -> 2 perceptron with ReLU
  * activations, bfloat16 weight matrices and float32 biases, activations and
- * accumulation.  Output r predicts the cost (log2 of the number of branched
- * nodes in the subtree, / 10) of branching a node with rule r: rule 0 is the
- * max-range rule of Section 3.3, rule 1 splits the box nearest to the sample
- * attaining the node's lower bound, on the attribute where that sample lies
- * farthest outside it.  The solver takes the cheaper rule and orders equal
- * lower bounds by the smaller predicted cost.  The paper has no
+ * accumulation.  Output r predicts the cost (log2 of the list entries scanned
+ * by the branched nodes of the subtree, / 40) of branching a node with rule r:
+ * rule 0 is the max-range rule of Section 3.3, rule 1 splits the box nearest to
+ * the sample attaining the node's lower bound, on the attribute where that
+ * sample lies farthest outside it (taken only where that attribute's range is
+ * at least 1/16 of the largest).  The solver takes the cheaper rule and orders
+ * equal lower bounds by the smaller predicted cost.  The paper has no
  * learned component: the exact lower bound still decides every prune, so the
  * certified optimum cannot change.  Parameters are one float vector of 5122
  * values [W1 64x12, b1 64, W2 64x64, b2 64, W3 2x64, b3 2] (row major);

@@ -1,7 +1,7 @@
 // kc_mlp.cu -- the learned node scorer: a 12 -> 64 -> 64 -> 2 ReLU perceptron
 // with bfloat16 weight matrices and float32 biases, activations and
-// accumulation.  Output r is the predicted cost (log2 of the subtree size / 10)
-// of branching a node with rule r.  Inference (one warp per node), training (a fused forward +
+// accumulation.  Output r is the predicted cost (log2 of the work in the
+// subtree / 40) of branching a node with rule r.  Inference (one warp per node), training (a fused forward +
 // backward kernel over chunks of 32 samples staged in shared memory, gradient
 // sums merged with atomics, then Adam) -- all hand-written.
 //

@@ -1,16 +1,17 @@
 """Training data and training for the learned node scorer.
 
 The scorer predicts, for a node about to be branched, the cost of branching it
-with each rule: output r = log2(1 + number of branched nodes in the subtree) / 10
-when rule r is applied (rule 0: max-range; rule 1: split the box nearest to the
+with each rule: output r = log2(1 + the solver's work in the subtree) / 40 when
+rule r is applied, the work being the number of list entries the branched nodes
+of the subtree scan (the sample count of each node's list, summed) (rule 0: max-range; rule 1: split the box nearest to the
 sample attaining the node's bound, on the attribute where that sample lies
 farthest outside).  The solver takes the cheaper rule.
 
 Training data come from the solver itself: with ``explore`` set it branches
 that percentage of the nodes with a random one of the two rules (where they
 differ) and, given a ``log_path``, writes one JSON line per branched node
-(features, parent, the rule taken).  A node's subtree size is counted from the
-log and becomes the target of the output of the rule that was taken; where the
+(features, parent, the rule taken, its list size).  A node's subtree work is
+summed from the log and becomes the target of the output of the rule that was taken; where the
 two rules coincide it is the target of both.  Round 1 explores every node under
 max-range; round 2 explores 30 % of the nodes under the round-1 model, and the
 model is retrained on both rounds' data.  Training runs on the GPU with the
@@ -42,14 +43,14 @@ def dataset_from_log(records):
     if not records:
         return (np.zeros((0, 12), np.float32), np.zeros((0, 2), np.float32), np.zeros((0, 2), np.float32))
     idx = {r["id"]: i for i, r in enumerate(records)}
-    size = np.ones(len(records))
-    # children are logged after their parents: accumulate subtree sizes backwards
+    work = np.array([float(r.get("n", 1)) for r in records])
+    # children are logged after their parents: accumulate subtree work backwards
     for i in range(len(records) - 1, -1, -1):
         p = records[i]["parent"]
         if p in idx:
-            size[idx[p]] += size[i]
+            work[idx[p]] += work[i]
     X = np.array([r["feat"] for r in records], np.float32)
-    cost = np.log2(1.0 + size) / 10.0
+    cost = np.log2(1.0 + work) / 40.0
     T = np.stack([cost, cost], 1)
     M = np.zeros((len(records), 2))
     for i, r in enumerate(records):
