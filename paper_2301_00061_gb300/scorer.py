@@ -168,9 +168,12 @@ def main(argv=None):
     ap.add_argument("--rounds", type=int, default=2,
                     help="1: random-rule data only; 2: then on-policy data from the first model, retrain on both")
     ap.add_argument("--explore", type=int, default=30, help="percent of random rules in on-policy rounds")
+    ap.add_argument("--n-lo", type=int, default=10_000, help="smallest training instance")
+    ap.add_argument("--n-hi", type=int, default=200_000, help="largest training instance")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(HERE))
-    inst = family_instances(a.instances) + outlier_instances(a.outlier_instances)
+    inst = (family_instances(a.instances, n_lo=a.n_lo, n_hi=a.n_hi) +
+            outlier_instances(a.outlier_instances, n_lo=a.n_lo, n_hi=a.n_hi))
     X, T, M = generate(inst, node_limit=a.node_limit)
     p, loss = train_scorer(X, T, M, epochs=a.epochs)
     for r in range(1, a.rounds):
@@ -179,7 +182,7 @@ def main(argv=None):
         p, loss = train_scorer(X, T, M, epochs=a.epochs)
     save(p, a.out, {"samples": int(len(X)), "instances": a.instances, "outlier_instances": a.outlier_instances,
                     "epochs": a.epochs, "loss": loss, "node_limit": a.node_limit, "rounds": a.rounds,
-                    "explore": a.explore,
+                    "explore": a.explore, "n_lo": a.n_lo, "n_hi": a.n_hi,
                     "command": "python -m paper_2301_00061_gb300.scorer " + " ".join(argv or sys.argv[1:])})
     print(json.dumps({"samples": int(len(X)), "loss": loss, "out": a.out}))
 
