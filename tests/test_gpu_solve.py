@@ -266,3 +266,26 @@ def test_solve_batched_workload_reduced():
     g, r = _solve_both(X, 3)
     assert g["status"] == 0
     assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
+
+
+def test_full_size_solves_properties():
+    """Full-size recipes, where the serial oracle cannot finish a solve: the
+    properties that hold at any size.  The FFT start equals the oracle's FFT;
+    the reported objective is the exact double objective of the returned
+    centers over all N samples (the oracle recomputes it); the certified lower
+    bound never exceeds it; a certified solve meets the 1e-12 stop rule.
+    Learned-order recipe at N=1e7 (certifies in seconds) and the batched-solve
+    recipe at N=1e7 under a 10 s limit."""
+    for name, n, limit in (("learned_order", 10_000_000, 120.0), ("batched_solve", 10_000_000, 10.0)):
+        X, w = synth.make_workload(name, n=n)
+        kc = KCenter(_t(X), w.k)
+        g = kc.solve(tol=1e-12, time_limit_s=limit)
+        kc.close()
+        assert g["status"] in (0, 4), g
+        if name == "learned_order":
+            assert g["status"] == 0
+            assert g["gap"] <= 1e-12 + 4 * 2.0**-53
+        _, fobj = oracle.fft(X, w.k, 0)
+        assert g["fft_objective"] == fobj
+        assert oracle.objective(X, g["centers"])[0] == g["objective"]
+        assert 0.0 <= g["lower_bound"] <= g["objective"] <= g["fft_objective"]
