@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--solve-n", type=int, default=1_000_000,
                    help="N of the batched-solve workload timed to a certified optimum (0: skip)")
     p.add_argument("--solve-time-limit", type=float, default=120.0)
+    p.add_argument("--learned-n", type=int, default=100_000_000,
+                   help="N of the learned-order workload solved with the scorer and with best bound (0: skip)")
     return p.parse_args()
 
 
@@ -296,6 +298,29 @@ def main():
         kc.close()
         del Xsd
 
+    # ---- learned node order against best bound on the learned-order recipe
+    # (4 blobs + 1 % outliers, D = 2, K = 4): both to tol 1e-12, data resident
+    learned = None
+    if args.learned_n > 0:
+        from paper_2301_00061_gb300 import scorer as kc_scorer
+        Xl, wl = synth.make_workload("learned_order", n=args.learned_n, seed=3 + rank)
+        kc = kcm.KCenter(torch.from_numpy(Xl).to(dev), wl.k)
+        del Xl
+        sc = kcm.Scorer(kc_scorer.load())
+        kc.set_scorer(sc)
+        res = {}
+        for order in (1, 0):
+            torch.cuda.synchronize()
+            barrier()
+            r = kc.solve(tol=1e-12, order=order, time_limit_s=args.solve_time_limit)
+            res[order] = {"seconds": max_over_ranks(r["seconds"], ws), "nodes": int(r["nodes"]),
+                          "certified": r["status"] == 0, "objective": r["objective"]}
+        learned = {"workload": f"learned_order: N={args.learned_n:,} D={wl.d} K={wl.k} float32, 4 blobs + 1% outliers",
+                   "metric": "time to certified optimum (tol 1e-12)", "learned": res[1], "best_bound": res[0],
+                   "same_objective": res[1]["objective"] == res[0]["objective"]}
+        kc.close()
+        sc.close()
+
     cfg = config_dict(n, w)
     cfg["autotuned"] = {"samples_per_thread": tuned_st, "nodes_per_launch": tuned_chunk}
     line = {
@@ -306,6 +331,8 @@ def main():
     }
     if solve is not None:
         line["solve"] = solve
+    if learned is not None:
+        line["learned_order"] = learned
     if rank == 0 and not args.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(X, lo, hi, 200_000)
         line["cpu_baseline"] = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
