@@ -277,10 +277,9 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
     // out_pool NULL: count the surviving samples only
     __shared__ uint64_t sbox[kMaxK * DMAX];
     __shared__ float sl[kMaxK * DMAX], sh[kMaxK * DMAX];
-    __shared__ unsigned wsum[8];
-    __shared__ unsigned long long base_s, red[8];
+    __shared__ unsigned long long red[8];
     const int Dp = (D + 1) & ~1;
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
         int b;
         int64_t st;
@@ -288,6 +287,7 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
         const int64_t nb = L.seg_n[b];
         const int tn = (int)((nb - st) < (int64_t)kLT ? (nb - st) : (int64_t)kLT);
         const uint32_t *ids = L.pool + L.seg_off[b] + st;
+        __syncthreads();   // the previous item's readers of the boxes are done
         for (int i = threadIdx.x; i < K * Dp; i += blockDim.x) {
             const int k = i / Dp, a = i % Dp;
             const size_t o = ((size_t)b * K + k) * D + a;
@@ -371,22 +371,16 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
                     best1 = k1 > best1 ? k1 : best1;
                 }
             }
+            // one reservation per warp (no block barrier): lane 0 claims the
+            // warp's surviving entries, the others write behind it in lane order
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0) wsum[wp] = __popc(bal);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                unsigned tot = 0;
-                for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += wsum[q];
-                base_s = tot ? atomicAdd(&out_n[b], (unsigned long long)tot) : 0ull;
+            if (bal) {
+                unsigned long long base = 0ull;
+                if (lane == 0) base = atomicAdd(&out_n[b], (unsigned long long)__popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (keep && out_pool)
+                    out_pool[out_off[b] + (int64_t)(base + __popc(bal & ((1u << lane) - 1u)))] = id;
             }
-            __syncthreads();
-            if (keep && out_pool) {
-                unsigned before = 0;
-                for (int q = 0; q < wp; ++q) before += wsum[q];
-                const unsigned long long p = base_s + before + __popc(bal & ((1u << lane) - 1u));
-                out_pool[out_off[b] + (int64_t)p] = id;
-            }
-            __syncthreads();
         }
         if (ckeys) {
             best0 = block_max_u64(best0, red);
