@@ -281,7 +281,8 @@ typedef struct {
                               data for the scorer, with log_path */
     int32_t arena_mb;      /* 0: automatic; device memory (MiB) that holds the per-node lists */
     uint64_t seed;         /* 0: FFT start = seed mod N */
-    const char *log_path;  /* NULL, or a file receiving one JSON line per branched node (scorer features) */
+    const char *log_path;  /* NULL, or a file receiving one JSON line per branched node (scorer
+                              features) and one per bounded child (boxes, certified bound, pruned) */
 } kc_solve_opts;
 
 typedef struct {

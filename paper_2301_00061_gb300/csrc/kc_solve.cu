@@ -954,6 +954,16 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             for (int q = 0; q < nk; ++q) {
                 Node<T> &ch = kids[k0 + q];
                 ++created;
+                if (log) {
+                    // every bounded child: its boxes and certified bound, for
+                    // checking bounds and prunes against a double evaluation
+                    fprintf(log, "{\"child\":%lld,\"parent\":%lld,\"key\":%.17g,\"pruned\":%d,\"lo\":[",
+                            (long long)ch.id, (long long)ch.parent, ch.key, ch.key >= prune_threshold() ? 1 : 0);
+                    for (int i = 0; i < KD; ++i) fprintf(log, i ? ",%.9g" : "%.9g", (double)ch.lo[i]);
+                    fprintf(log, "],\"hi\":[");
+                    for (int i = 0; i < KD; ++i) fprintf(log, i ? ",%.9g" : "%.9g", (double)ch.hi[i]);
+                    fprintf(log, "]}\n");
+                }
                 if (ch.key >= prune_threshold()) {
                     drop_list(ch);
                     continue;

@@ -34,8 +34,10 @@ DEFAULT_WEIGHTS = os.path.join(HERE, "scorer_weights.json")
 
 
 def read_log(path):
+    """The branched-node records of a solver log (child records are skipped)."""
     with open(path) as f:
-        return [json.loads(line) for line in f if line.strip()]
+        recs = [json.loads(line) for line in f if line.strip()]
+    return [r for r in recs if "feat" in r]
 
 
 def dataset_from_log(records):

@@ -289,3 +289,32 @@ def test_full_size_solves_properties():
         assert g["fft_objective"] == fobj
         assert oracle.objective(X, g["centers"])[0] == g["objective"]
         assert 0.0 <= g["lower_bound"] <= g["objective"] <= g["fft_objective"]
+
+
+def test_full_size_bounds_and_prunes_replayed(tmp_path):
+    """A full-size solve (learned-order recipe, N=1e7) logs every child it
+    bounds; a seeded sample of them is re-bounded by the oracle in double over
+    all N samples.  Each certified bound lies within 1e-6 below the double
+    closed form and never above it, and each pruned child's double bound
+    reaches the final incumbent times (1 - tol), so the prune was sound."""
+    import json
+    X, w = synth.make_workload("learned_order", n=10_000_000)
+    kc = KCenter(_t(X), w.k)
+    log = tmp_path / "tree.jsonl"
+    g = kc.solve(tol=1e-12, log_path=str(log))
+    kc.close()
+    assert g["status"] == 0
+    kids = [r for r in map(json.loads, open(log)) if "child" in r]
+    assert len(kids) > 1000
+    rng = np.random.default_rng(0)
+    pruned = [r for r in kids if r["pruned"]]
+    sample = [kids[i] for i in rng.choice(len(kids), 8, replace=False)]
+    sample += [pruned[i] for i in rng.choice(len(pruned), 8, replace=False)]
+    alpha = g["objective"]
+    for r in sample:
+        lo = np.array(r["lo"], np.float32).reshape(w.k, w.d)
+        hi = np.array(r["hi"], np.float32).reshape(w.k, w.d)
+        beta = oracle.lower_bound(X, lo, hi)[0]
+        assert r["key"] <= beta and r["key"] >= beta * (1 - 1e-6), (r["child"], r["key"], beta)
+        if r["pruned"]:
+            assert beta >= alpha * (1 - 1e-12), (r["child"], beta, alpha)
