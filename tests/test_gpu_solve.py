@@ -292,29 +292,32 @@ def test_full_size_solves_properties():
 
 
 def test_full_size_bounds_and_prunes_replayed(tmp_path):
-    """A full-size solve (learned-order recipe, N=1e7) logs every child it
-    bounds; a seeded sample of them is re-bounded by the oracle in double over
-    all N samples.  Each certified bound lies within 1e-6 below the double
-    closed form and never above it, and each pruned child's double bound
-    reaches the final incumbent times (1 - tol), so the prune was sound."""
+    """Full-size solves log every child they bound; a seeded sample is
+    re-bounded by the oracle in double over all N samples.  Each certified
+    bound lies within 1e-6 below the double closed form and never above it,
+    and each pruned child's double bound reaches the final incumbent times
+    (1 - tol), so the prune was sound.  Learned-order recipe at N=1e7 (solved
+    to the certificate) and batched-solve recipe at N=1e7 (first 100,000
+    nodes)."""
     import json
-    X, w = synth.make_workload("learned_order", n=10_000_000)
-    kc = KCenter(_t(X), w.k)
-    log = tmp_path / "tree.jsonl"
-    g = kc.solve(tol=1e-12, log_path=str(log))
-    kc.close()
-    assert g["status"] == 0
-    kids = [r for r in map(json.loads, open(log)) if "child" in r]
-    assert len(kids) > 1000
-    rng = np.random.default_rng(0)
-    pruned = [r for r in kids if r["pruned"]]
-    sample = [kids[i] for i in rng.choice(len(kids), 8, replace=False)]
-    sample += [pruned[i] for i in rng.choice(len(pruned), 8, replace=False)]
-    alpha = g["objective"]
-    for r in sample:
-        lo = np.array(r["lo"], np.float32).reshape(w.k, w.d)
-        hi = np.array(r["hi"], np.float32).reshape(w.k, w.d)
-        beta = oracle.lower_bound(X, lo, hi)[0]
-        assert r["key"] <= beta and r["key"] >= beta * (1 - 1e-6), (r["child"], r["key"], beta)
-        if r["pruned"]:
-            assert beta >= alpha * (1 - 1e-12), (r["child"], beta, alpha)
+    for name, node_limit in (("learned_order", 0), ("batched_solve", 100_000)):
+        X, w = synth.make_workload(name, n=10_000_000)
+        kc = KCenter(_t(X), w.k)
+        log = tmp_path / f"{name}.jsonl"
+        g = kc.solve(tol=1e-12, log_path=str(log), node_limit=node_limit)
+        kc.close()
+        assert g["status"] == (0 if node_limit == 0 else 5)
+        kids = [r for r in map(json.loads, open(log)) if "child" in r]
+        assert len(kids) > 1000
+        rng = np.random.default_rng(0)
+        pruned = [r for r in kids if r["pruned"]]
+        sample = [kids[i] for i in rng.choice(len(kids), 8, replace=False)]
+        sample += [pruned[i] for i in rng.choice(len(pruned), min(8, len(pruned)), replace=False)]
+        alpha = g["objective"]
+        for r in sample:
+            lo = np.array(r["lo"], np.float32).reshape(w.k, w.d)
+            hi = np.array(r["hi"], np.float32).reshape(w.k, w.d)
+            beta = oracle.lower_bound(X, lo, hi)[0]
+            assert r["key"] <= beta and r["key"] >= beta * (1 - 1e-6), (name, r["child"], r["key"], beta)
+            if r["pruned"]:
+                assert beta >= alpha * (1 - 1e-12), (name, r["child"], beta, alpha)
