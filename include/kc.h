@@ -306,13 +306,19 @@ void kc_solve_defaults(kc_solve_opts *opt);
 
 /*
  * kc_solve -- the branch and bound of Algorithm 1 to a certified optimum:
- * root box, FFT upper bound and seeds, then batches of open nodes are
- * bounded, tightened and branched on the GPU (max-range variable, midpoint
- * value), pruning every node whose certified lower bound reaches the upper
- * bound, with sample reduction between batches.  The returned objective is
+ * root box, FFT upper bound and seeds (Algorithm 2, Section 4.1.1), then
+ * batches of open nodes with the smallest bounds are tightened, given an
+ * upper-bound candidate and branched on the GPU (max-range variable or the
+ * scorer's rule, midpoint value); children are bounded when created and every
+ * node whose certified lower bound reaches UB (1 - tol) is pruned.  Sample
+ * reduction (Section 4.2) runs per node: with opt->lists (float data) each
+ * node's children scan only the samples that survive in it; otherwise one
+ * shared sample set is reduced between batches.  Float bounds that cannot
+ * decide a prune are re-evaluated in double.  The returned objective is
  * recomputed in double over all samples.  opt may be NULL (defaults); tol
  * overrides opt->tol when >= 0.  Returns KC_OK at optimality within tol,
- * KC_ETIMEOUT / KC_ELIMIT (with *out filled) at a limit.
+ * KC_ETIMEOUT / KC_ELIMIT (with *out filled) at a limit, KC_EINVAL for
+ * options out of range, KC_ENOMEM when the list arena or buffers do not fit.
  */
 kc_status kc_solve(kc_ctx *ctx, double tol, const kc_solve_opts *opt, kc_result *out);
 
