@@ -283,6 +283,8 @@ typedef struct {
     uint64_t seed;         /* 0: FFT start = seed mod N */
     const char *log_path;  /* NULL, or a file receiving one JSON line per branched node (scorer
                               features) and one per bounded child (boxes, certified bound, pruned) */
+    double rule_margin;    /* 0: with order = 1, rule 1 is taken only when its predicted cost is
+                              lower than max-range's by more than this (cost units: log2 / 40) */
 } kc_solve_opts;
 
 typedef struct {

@@ -47,6 +47,7 @@ class SolveOpts(C.Structure):
         ("arena_mb", C.c_int32),
         ("seed", C.c_uint64),
         ("log_path", C.c_char_p),
+        ("rule_margin", C.c_double),
     ]
 
 

@@ -765,7 +765,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                     const bool wide = rule1[i] >= 0 &&
                                       16.0 * ((double)hb2[rule1[i]] - (double)lb2[rule1[i]]) >=
                                           (double)hb2[rule0[i]] - (double)lb2[rule0[i]];
-                    const bool take1 = wide && c1 < c0;
+                    const bool take1 = wide && (double)c1 < (double)c0 - o.rule_margin;
                     if (take1) choice[i] = rule1[i];
                     prio[i] = take1 ? c1 : c0;
                 }
@@ -1245,6 +1245,7 @@ kc_status kc_solve(kc_ctx *c, double tol, const kc_solve_opts *opt, kc_result *o
     if (o.lists != 0 && o.lists != 1) return set_err(c, KC_EINVAL, "kc_solve: lists must be 0 or 1");
     if (o.arena_mb < 0) return set_err(c, KC_EINVAL, "kc_solve: arena_mb must be >= 0");
     if (o.explore < 0 || o.explore > 100) return set_err(c, KC_EINVAL, "kc_solve: explore must be in [0, 100]");
+    if (!(o.rule_margin >= 0.0)) return set_err(c, KC_EINVAL, "kc_solve: rule_margin must be >= 0");
     std::memset(out, 0, sizeof(*out));
     if (c->dt == KC_F32) return solve_impl<float>(c, o, out);
     return solve_impl<double>(c, o, out);
