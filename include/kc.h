@@ -285,6 +285,9 @@ typedef struct {
                               features) and one per bounded child (boxes, certified bound, pruned) */
     double rule_margin;    /* 0: with order = 1, rule 1 is taken only when its predicted cost is
                               lower than max-range's by more than this (cost units: log2 / 40) */
+    int32_t fft_starts;    /* 1 (0 = 1): FFT runs from this many start samples (seed mod N, then
+                              steps of 2654435761 mod N); the best is the first incumbent and
+                              kc_result.fft_objective */
 } kc_solve_opts;
 
 typedef struct {

@@ -48,6 +48,7 @@ class SolveOpts(C.Structure):
         ("seed", C.c_uint64),
         ("log_path", C.c_char_p),
         ("rule_margin", C.c_double),
+        ("fft_starts", C.c_int32),
     ]
 
 

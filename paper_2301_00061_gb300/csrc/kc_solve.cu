@@ -281,19 +281,29 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         KC_CUDA(c, cudaMemcpyAsync(root_lo.data(), d, D * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
         KC_CUDA(c, cudaMemcpyAsync(root_hi.data(), d + 1024, D * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
     }
-    const int64_t start = (int64_t)(o.seed % (uint64_t)c->N);
     KC_TRY(ensure(c, sb.sets, 4096));
     int64_t *T_dev = static_cast<int64_t *>(sb.sets.p);
     double *v_dev = reinterpret_cast<double *>(static_cast<char *>(sb.sets.p) + 1024);
-    KC_CUDA(c, cudaMemcpyAsync(T_dev, &start, 8, cudaMemcpyHostToDevice, c->stream));
-    for (int t = 1; t < K; ++t)
-        KC_TRY(launch_objective(c, full_view(c), T_dev, 1, t, __builtin_huge_val(), v_dev, T_dev + t));
-    KC_TRY(launch_objective(c, full_view(c), T_dev, 1, K, __builtin_huge_val(), v_dev, nullptr));
-    std::vector<int64_t> inc(K);
-    double alpha = 0.0;
-    KC_CUDA(c, cudaMemcpyAsync(inc.data(), T_dev, K * 8, cudaMemcpyDeviceToHost, c->stream));
-    KC_CUDA(c, cudaMemcpyAsync(&alpha, v_dev, 8, cudaMemcpyDeviceToHost, c->stream));
-    KC_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<int64_t> inc(K), trial(K);
+    double alpha = __builtin_huge_val();
+    // FFT from fft_starts start samples (seed mod N, then steps of a large odd
+    // multiplier); the best objective is the first incumbent
+    for (int i = 0; i < std::max(1, o.fft_starts); ++i) {
+        const int64_t start = (int64_t)((o.seed + (uint64_t)i * 2654435761ull) % (uint64_t)c->N);
+        KC_CUDA(c, cudaMemcpyAsync(T_dev, &start, 8, cudaMemcpyHostToDevice, c->stream));
+        for (int t = 1; t < K; ++t)
+            KC_TRY(launch_objective(c, full_view(c), T_dev, 1, t, __builtin_huge_val(), v_dev, T_dev + t));
+        KC_TRY(launch_objective(c, full_view(c), T_dev, 1, K, __builtin_huge_val(), v_dev, nullptr));
+        double a = 0.0;
+        KC_CUDA(c, cudaMemcpyAsync(trial.data(), T_dev, K * 8, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaMemcpyAsync(&a, v_dev, 8, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (a < alpha) {
+            alpha = a;
+            inc = trial;
+        }
+    }
+    KC_CUDA(c, cudaMemcpyAsync(T_dev, inc.data(), K * 8, cudaMemcpyHostToDevice, c->stream));
     res->fft_objective = alpha;
 
     bool seeds_found = false;
@@ -1246,6 +1256,7 @@ kc_status kc_solve(kc_ctx *c, double tol, const kc_solve_opts *opt, kc_result *o
     if (o.arena_mb < 0) return set_err(c, KC_EINVAL, "kc_solve: arena_mb must be >= 0");
     if (o.explore < 0 || o.explore > 100) return set_err(c, KC_EINVAL, "kc_solve: explore must be in [0, 100]");
     if (!(o.rule_margin >= 0.0)) return set_err(c, KC_EINVAL, "kc_solve: rule_margin must be >= 0");
+    if (o.fft_starts < 0 || o.fft_starts > 4096) return set_err(c, KC_EINVAL, "kc_solve: fft_starts must be in [0, 4096]");
     std::memset(out, 0, sizeof(*out));
     if (c->dt == KC_F32) return solve_impl<float>(c, o, out);
     return solve_impl<double>(c, o, out);
