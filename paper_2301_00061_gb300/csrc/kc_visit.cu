@@ -581,10 +581,12 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
                 T x[DM];
 #pragma unroll
                 for (int a = 0; a < DM; ++a) x[a] = a < D ? tx[(size_t)a * tile + j] : T(0);
+                // clusters the center-based rule leaves open (only needed when the
+                // sample-based rule can run: every cluster has representatives)
                 int left = 0;
 #pragma unroll
                 for (int k = 0; k < KM; ++k)
-                    if (k < K) {
+                    if (have && k < K) {
                         bool excl;
                         if constexpr (F32) {
                             uint64_t px[DM];
