@@ -163,20 +163,9 @@ struct ListBatch {
     const int64_t *seg_n = nullptr;
     const int64_t *tile_prefix = nullptr;   // [B + 1]
     const int *node_start = nullptr;        // [B + 1] or NULL
-    // per (tile, node) blocks of one bit per entry (grouped batches): group g's
-    // blocks start at bits_prefix[g] = sum over earlier groups of tiles x nodes
-    const int64_t *bits_prefix = nullptr;   // [B + 1] or NULL
-    int64_t bits_blocks = 0;                // bits_prefix[B] (host value)
     int B = 0;                              // groups
     int64_t W = 0;                          // tile_prefix[B]
 };
-
-// The bit block of (work item w = tile t of group g, node nd of the group).
-__host__ __device__ inline int64_t list_bits_block(const ListBatch &L, int g, int64_t t, int nd)
-{
-    const int n0 = L.node_start ? L.node_start[g] : g, n1 = L.node_start ? L.node_start[g + 1] : g + 1;
-    return L.bits_prefix[g] + t * (int64_t)(n1 - n0) + (nd - n0);
-}
 
 // ----------------------------------------------------------- kernel launchers
 // (implemented in the .cu files; all run on c->stream)

@@ -424,7 +424,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     // ---- per-node surviving-sample lists (float data)
     const bool lists = o.lists != 0 && c->dt == KC_F32;
     const int LT = list_tile();
-    const size_t slot_bytes = ((size_t)4 * (Bmax + 1) * 8 + (size_t)(2 * Bmax + 1) * 4 + 255) & ~(size_t)255;
+    const size_t slot_bytes = ((size_t)3 * (Bmax + 1) * 8 + (size_t)(2 * Bmax + 1) * 4 + 255) & ~(size_t)255;
     const int kSlots = 6;   // batch, its refinement, upper bounds, filter, children, their refinement
     const size_t l_keys = (size_t)kSlots * slot_bytes, l_vmax = l_keys + (size_t)Bmax * 8;
     const size_t l_thr = l_vmax + (size_t)Bmax * 8, l_beta = l_thr + (size_t)Bmax * 4;
@@ -480,8 +480,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         char *hp = static_cast<char *>(sb.lpin) + (size_t)slot * slot_bytes;
         char *dp = static_cast<char *>(sb.lists.p) + (size_t)slot * slot_bytes;
         int64_t *so = reinterpret_cast<int64_t *>(hp), *sn = so + (Bmax + 1), *tp = sn + (Bmax + 1);
-        int64_t *bp = tp + (Bmax + 1);
-        int *rm = reinterpret_cast<int *>(bp + (Bmax + 1)), *ns = rm + Bmax;
+        int *rm = reinterpret_cast<int *>(tp + (Bmax + 1)), *ns = rm + Bmax;
         tp[0] = 0;
         int G = 0, prev = -1;
         for (int i = 0; i < n; ++i) {
@@ -497,18 +496,14 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             prev = h;
         }
         ns[G] = n;
-        bp[0] = 0;
-        for (int g = 0; g < G; ++g) bp[g + 1] = bp[g] + (tp[g + 1] - tp[g]) * (int64_t)(ns[g + 1] - ns[g]);
         KC_CUDA(c, cudaMemcpyAsync(dp, hp, slot_bytes, cudaMemcpyHostToDevice, c->stream));
         const int64_t *sod = reinterpret_cast<const int64_t *>(dp);
         L->pool = arena.ids();
         L->seg_off = sod;
         L->seg_n = sod + (Bmax + 1);
         L->tile_prefix = sod + 2 * (Bmax + 1);
-        const int *rmd = reinterpret_cast<const int *>(sod + 4 * (Bmax + 1));
+        const int *rmd = reinterpret_cast<const int *>(sod + 3 * (Bmax + 1));
         L->node_start = group ? rmd + Bmax : nullptr;
-        L->bits_prefix = group ? sod + 3 * (Bmax + 1) : nullptr;
-        L->bits_blocks = group ? bp[G] : 0;
         L->B = G;
         L->W = tp[G];
         if (rows_dev) *rows_dev = rmd;

@@ -201,7 +201,7 @@ __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td
                                             const T *__restrict__ hi, int b, int K, int D, double alpha,
                                             const Margins &mg, typename Key<T>::K *__restrict__ lbkey,
                                             typename Key<T>::K *__restrict__ amax, typename Key<T>::K *__restrict__ amin,
-                                            unsigned *__restrict__ flags, uint32_t *__restrict__ open_bits = nullptr)
+                                            unsigned *__restrict__ flags)
 {
     using KT = Key<T>;
     using KY = typename KT::K;
@@ -230,61 +230,50 @@ __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td
 #pragma unroll
         for (int a = 0; a < DM; ++a) { acc_max[k][a] = KT::none(); acc_min[k][a] = KT::none(); }
     bool infeasible = false;
-    // warp-uniform loop (jw = the warp's first entry) so that the per-entry
-    // "left open" bits can be written with one ballot per 32 entries
-    for (int jw = j0 - lane; jw < tn; jw += step) {
-        const int j = jw + lane;
-        bool open = false;
-        if (j < tn) {
-            const uint32_t pos = tids ? tids[j] : (uint32_t)(base + j);
-            T x[DM];
-            uint64_t px[DM];
+    for (int j = j0; j < tn; j += step) {
+        const uint32_t pos = tids ? tids[j] : (uint32_t)(base + j);
+        T x[DM];
+        uint64_t px[DM];
 #pragma unroll
-            for (int a = 0; a < DM; ++a) {
-                if constexpr (F32) {
-                    px[a] = a < D ? tp[(size_t)a * tile + j] : pk(0.f, -0.f);
-                    x[a] = upk(px[a]).x;
-                } else {
-                    x[a] = a < D ? td[(size_t)a * tile + j] : 0.0;
-                }
+        for (int a = 0; a < DM; ++a) {
+            if constexpr (F32) {
+                px[a] = a < D ? tp[(size_t)a * tile + j] : pk(0.f, -0.f);
+                x[a] = upk(px[a]).x;
+            } else {
+                x[a] = a < D ? td[(size_t)a * tile + j] : 0.0;
             }
-            T bmin = T(0);
-            int left = 0, k1 = -1;
-#pragma unroll
-            for (int k = 0; k < KM; ++k) {
-                if (k < K) {
-                    T v;
-                    bool excl;
-                    if constexpr (F32) {
-                        v = box_dist_pad<DM>(px, bx[k]);
-                        excl = v > mg.t_alpha;
-                    } else {
-                        v = box_dist_f64<DM>(reinterpret_cast<const double *>(x), blo[k], bhi[k], D);
-                        excl = v > alpha;
-                    }
-                    bmin = (k == 0 || v < bmin) ? v : bmin;
-                    if (!excl) { ++left; k1 = k; }
-                }
-            }
-            acc_lb = kmax<T>(acc_lb, KT::max_of(bmin, pos));
-            if (left == 0) infeasible = true;
-            if (left == 1) {
-#pragma unroll
-                for (int k = 0; k < KM; ++k)
-                    if (k == k1) {
-#pragma unroll
-                        for (int a = 0; a < DM; ++a)
-                            if (a < D) {
-                                acc_max[k][a] = kmax<T>(acc_max[k][a], KT::max_of(x[a], pos));
-                                acc_min[k][a] = kmax<T>(acc_min[k][a], KT::min_of(x[a], pos));
-                            }
-                    }
-            }
-            open = left >= 2;
         }
-        if (open_bits) {
-            const unsigned m = __ballot_sync(0xffffffffu, open);
-            if (lane == 0) open_bits[jw >> 5] = m;
+        T bmin = T(0);
+        int left = 0, k1 = -1;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            if (k < K) {
+                T v;
+                bool excl;
+                if constexpr (F32) {
+                    v = box_dist_pad<DM>(px, bx[k]);
+                    excl = v > mg.t_alpha;
+                } else {
+                    v = box_dist_f64<DM>(reinterpret_cast<const double *>(x), blo[k], bhi[k], D);
+                    excl = v > alpha;
+                }
+                bmin = (k == 0 || v < bmin) ? v : bmin;
+                if (!excl) { ++left; k1 = k; }
+            }
+        }
+        acc_lb = kmax<T>(acc_lb, KT::max_of(bmin, pos));
+        if (left == 0) infeasible = true;
+        if (left == 1) {
+#pragma unroll
+            for (int k = 0; k < KM; ++k)
+                if (k == k1) {
+#pragma unroll
+                    for (int a = 0; a < DM; ++a)
+                        if (a < D) {
+                            acc_max[k][a] = kmax<T>(acc_max[k][a], KT::max_of(x[a], pos));
+                            acc_min[k][a] = kmax<T>(acc_min[k][a], KT::min_of(x[a], pos));
+                        }
+                }
         }
     }
     // warp reduction, then one atomic per accumulator and warp
@@ -349,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 visit_a_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile,
                     const T *__restrict__ lo, const T *__restrict__ hi, int K, int D, double alpha, Margins mg,
                     typename Key<T>::K *__restrict__ lbkey, typename Key<T>::K *__restrict__ amax,
-                    typename Key<T>::K *__restrict__ amin, unsigned *__restrict__ flags, uint32_t *__restrict__ open_bits)
+                    typename Key<T>::K *__restrict__ amin, unsigned *__restrict__ flags)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *tp = reinterpret_cast<uint64_t *>(smem);
@@ -374,9 +363,7 @@ visit_a_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile,
         if (team < teams)
             for (int nd = n0 + team; nd < n1; nd += teams)
                 pass_a_node<T, KM, DM>(tp, td, tile, tn, (warp % wpt) * 32 + lane, wpt * 32, tids, 0, lo, hi, nd, K, D,
-                                       alpha, mg, lbkey, amax, amin, flags,
-                                       open_bits ? open_bits + list_bits_block(L, b, st / tile, nd) * (tile / 32)
-                                                 : nullptr);
+                                       alpha, mg, lbkey, amax, amin, flags);
     }
 }
 
@@ -542,8 +529,7 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
                                             const int64_t *seed_id, unsigned long long *__restrict__ cnt,
                                             OrdT<T> *__restrict__ smax, OrdT<T> *__restrict__ smin,
                                             OrdT<T> *__restrict__ jmax, OrdT<T> *__restrict__ jmin,
-                                            typename Key<T>::K *__restrict__ cand, unsigned *__restrict__ flags,
-                                            const uint32_t *__restrict__ open_bits = nullptr)
+                                            typename Key<T>::K *__restrict__ cand, unsigned *__restrict__ flags)
 {
     using KT = Key<T>;
     using KY = typename KT::K;
@@ -596,13 +582,11 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
 #pragma unroll
                 for (int a = 0; a < DM; ++a) x[a] = a < D ? tx[(size_t)a * tile + j] : T(0);
                 // clusters the center-based rule leaves open (only needed when the
-                // sample-based rule can run: every cluster has representatives);
-                // pass A's bit when it left one, else counted here
+                // sample-based rule can run: every cluster has representatives)
                 int left = 0;
-                if (open_bits) left = ((open_bits[jb >> 5] >> lane) & 1u) ? 2 : 0;
 #pragma unroll
                 for (int k = 0; k < KM; ++k)
-                    if (have && !open_bits && k < K) {
+                    if (have && k < K) {
                         bool excl;
                         if constexpr (F32) {
                             uint64_t px[DM];
@@ -795,7 +779,7 @@ visit_b_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile, 
                     const int *__restrict__ allhave, double alpha, Margins mg, const int64_t *__restrict__ seeds,
                     unsigned long long *__restrict__ cnt, OrdT<T> *__restrict__ smax, OrdT<T> *__restrict__ smin,
                     OrdT<T> *__restrict__ jmax, OrdT<T> *__restrict__ jmin, typename Key<T>::K *__restrict__ cand,
-                    unsigned *__restrict__ flags, const uint32_t *__restrict__ open_bits)
+                    unsigned *__restrict__ flags)
 {
     int64_t seed_id[KM];
 #pragma unroll
@@ -827,9 +811,7 @@ visit_b_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile, 
             for (int nd = n0 + team; nd < n1; nd += teams)
                 pass_b_node<T, KM, DM, RMX>(tx, tile, tn, (warp % wpt) * 32, wpt * 32, tids, nullptr, 0, list,
                                             slots + warp, nd, K, D, RM, lo_in, hi_in, blo, bhi, repx, nreps, allhave,
-                                            alpha, mg, seed_id, cnt, smax, smin, jmax, jmin, cand, flags,
-                                            open_bits ? open_bits + list_bits_block(L, b, st / tile, nd) * (tile / 32)
-                                                      : nullptr);
+                                            alpha, mg, seed_id, cnt, smax, smin, jmax, jmin, cand, flags);
         (void)lane;
     }
 }
@@ -1057,13 +1039,6 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     const size_t o_have = take(B * 4), o_cnt = take(BK * 8), o_smax = take(KD * sizeof(OrdT<T>));
     const size_t o_smin = take(KD * sizeof(OrdT<T>)), o_jmax = take(KD * sizeof(OrdT<T>));
     const size_t o_jmin = take(KD * sizeof(OrdT<T>)), o_cand = take(BK * sizeof(KY));
-    const size_t o_cand_end = off;
-    // list mode: pass A's "left open" bit per (node, list entry), read by pass B
-    // (skipped above 1 GiB, e.g. hundreds of nodes sharing a 1e9-entry list:
-    // pass B then recounts)
-    int64_t bits_words = (L && L->bits_prefix) ? L->bits_blocks * (list_tile() / 32) : 0;
-    if (bits_words * 4 > ((int64_t)1 << 30)) bits_words = 0;
-    const size_t o_bits = take((size_t)bits_words * 4);
     KC_TRY(ensure(c, vs->buf, off));
     char *w = static_cast<char *>(vs->buf.p);
     KY *lbkey = reinterpret_cast<KY *>(w + o_lbkey), *amax = reinterpret_cast<KY *>(w + o_amax);
@@ -1081,8 +1056,7 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     KC_CUDA(c, cudaMemsetAsync(w + o_smin, 0xFF, o_jmax - o_smin, c->stream));
     KC_CUDA(c, cudaMemsetAsync(w + o_jmax, 0, o_jmin - o_jmax, c->stream));
     KC_CUDA(c, cudaMemsetAsync(w + o_jmin, 0xFF, o_cand - o_jmin, c->stream));
-    KC_CUDA(c, cudaMemsetAsync(w + o_cand, 0, o_cand_end - o_cand, c->stream));
-    uint32_t *open_bits = bits_words ? reinterpret_cast<uint32_t *>(w + o_bits) : nullptr;
+    KC_CUDA(c, cudaMemsetAsync(w + o_cand, 0, off - o_cand, c->stream));
 
     const Margins mg = make_margins(c, alpha, 0.0);
     const double r_up = nextafter(std::sqrt(alpha), __builtin_huge_val());
@@ -1101,7 +1075,7 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
         KC_TRY(grid_of(c, kAL, smem, std::max<int64_t>(1, L->W), &g));
         if (L->W > 0) {
             kAL<<<g, kThreads, smem, c->stream>>>(static_cast<const T *>(c->X), c->ldx, *L, lt, lo, hi, K_, D, alpha,
-                                                  mg, lbkey, amax, amin, flags, open_bits);
+                                                  mg, lbkey, amax, amin, flags);
             KC_TRY(after_launch(c, "tighten pass A (lists)"));
         }
     } else {
@@ -1143,7 +1117,7 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
         if (L->W > 0) {
             kBL<<<g, kThreads, smem, c->stream>>>(static_cast<const T *>(c->X), c->ldx, *L, lt, K_, D, RM, lo, hi, blo,
                                                   bhi, repx, nreps, have, alpha, mg, seeds, cnt, smax, smin, jmax, jmin,
-                                                  cand, flags, open_bits);
+                                                  cand, flags);
             KC_TRY(after_launch(c, "tighten pass B (lists)"));
         }
     } else {
