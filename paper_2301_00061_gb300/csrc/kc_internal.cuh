@@ -289,7 +289,6 @@ kc_status mlp_forward_device(kc_mlp *m, const float *feats, int B, float *out, c
 // ---- per-node sample lists (kc_lists.cu)
 int list_tile();
 kc_status launch_iota(kc_ctx *c, uint32_t *p, int64_t n);
-kc_status launch_copy_segments(kc_ctx *c, const ListBatch &L, uint32_t *dst, const int64_t *dn);
 kc_status launch_seg_lb(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, unsigned long long *keys,
                         double *lb, double *raw, int64_t *arg);
 kc_status launch_seg_refine(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, const double *raw_host,

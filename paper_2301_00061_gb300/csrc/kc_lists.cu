@@ -399,18 +399,6 @@ __global__ void iota_kernel(uint32_t *p, int64_t n)
         p[i] = (uint32_t)i;
 }
 
-// Copies the lists of a batch to dst at offsets dn[b] (arena compaction).
-__global__ void copy_segments_kernel(ListBatch L, uint32_t *__restrict__ dst, const int64_t *__restrict__ dn)
-{
-    for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
-        int b;
-        int64_t st;
-        list_item(L.tile_prefix, L.B, w, kLT, &b, &st);
-        const int64_t n = L.seg_n[b] - st < kLT ? L.seg_n[b] - st : kLT;
-        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) dst[dn[b] + st + j] = L.pool[L.seg_off[b] + st + j];
-    }
-}
-
 __global__ void keys_finalize(const unsigned long long *__restrict__ keys, int B, double defl, double slack,
                               double *__restrict__ lb, double *__restrict__ raw, int64_t *__restrict__ arg)
 {
@@ -455,13 +443,6 @@ kc_status launch_iota(kc_ctx *c, uint32_t *p, int64_t n)
 {
     iota_kernel<<<c->num_sms * 8, 256, 0, c->stream>>>(p, n);
     return after_launch(c, "list iota");
-}
-
-kc_status launch_copy_segments(kc_ctx *c, const ListBatch &L, uint32_t *dst, const int64_t *dn)
-{
-    if (L.W <= 0) return KC_OK;
-    copy_segments_kernel<<<grid_items(c, L.W), 256, 0, c->stream>>>(L, dst, dn);
-    return after_launch(c, "list copy");
 }
 
 // keys [B] (device scratch, zeroed here) -> lb, raw, arg (device).
