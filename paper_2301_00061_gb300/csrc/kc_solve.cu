@@ -24,6 +24,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <memory>
 #include <set>
 #include <vector>
 
@@ -541,7 +542,10 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     kc_status status = KC_OK;
     std::vector<Node<T>> batch;
     std::vector<int> live;
-    FILE *log = o.log_path ? fopen(o.log_path, "w") : nullptr;
+    // node log: closed on every return path
+    std::unique_ptr<FILE, int (*)(FILE *)> log_file(o.log_path ? fopen(o.log_path, "w") : nullptr, &fclose);
+    if (o.log_path && !log_file) return set_err(c, KC_EINVAL, "kc_solve: cannot open log_path '%s'", o.log_path);
+    FILE *log = log_file.get();
     double prof[5] = {0, 0, 0, 0, 0};
     double tA = 0;
 
@@ -1087,7 +1091,8 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                         heap.empty() ? alpha : heap.front().key, (long long)(lists ? arena.used : cur.n));
         }
     }
-    if (log) fclose(log);
+    log_file.reset();
+    log = nullptr;
     if (o.verbose)
         fprintf(stderr, "[kc_solve] seconds: tighten %.3f, upper bounds %.3f, branch+child bounds %.3f, "
                         "sample reduction %.3f; batches %lld, visits %lld, created %lld, refined %lld\n",
