@@ -12,9 +12,9 @@ that percentage of the nodes with a random one of the two rules (where they
 differ) and, given a ``log_path``, writes one JSON line per branched node
 (features, parent, the rule taken, its list size).  A node's subtree work is
 summed from the log and becomes the target of the output of the rule that was taken; where the
-two rules coincide it is the target of both.  Round 1 explores every node under
-max-range; round 2 explores 30 % of the nodes under the round-1 model, and the
-model is retrained on both rounds' data.  Training runs on the GPU with the
+two rules coincide it is the target of both.  Stage 1 explores every node under
+max-range; stage 2 explores 30 % of the nodes under the stage-1 model, and the
+model is retrained on both stages' data.  Training runs on the GPU with the
 library's kernels.
 
     python -m paper_2301_00061_gb300.scorer train --out weights.json
@@ -167,9 +167,9 @@ def main(argv=None):
     ap.add_argument("--outlier-instances", type=int, default=6, help="outlier family instances")
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--node-limit", type=int, default=8_000)
-    ap.add_argument("--rounds", type=int, default=2,
+    ap.add_argument("--stages", type=int, default=2,
                     help="1: random-rule data only; 2: then on-policy data from the first model, retrain on both")
-    ap.add_argument("--explore", type=int, default=30, help="percent of random rules in on-policy rounds")
+    ap.add_argument("--explore", type=int, default=30, help="percent of random rules in on-policy stages")
     ap.add_argument("--n-lo", type=int, default=10_000, help="smallest training instance")
     ap.add_argument("--n-hi", type=int, default=200_000, help="largest training instance")
     a = ap.parse_args(argv)
@@ -178,12 +178,12 @@ def main(argv=None):
             outlier_instances(a.outlier_instances, n_lo=a.n_lo, n_hi=a.n_hi))
     X, T, M = generate(inst, node_limit=a.node_limit)
     p, loss = train_scorer(X, T, M, epochs=a.epochs)
-    for r in range(1, a.rounds):
+    for r in range(1, a.stages):
         X2, T2, M2 = generate(inst, node_limit=a.node_limit, seed=1000 * r + 1, params=p, explore=a.explore)
         X, T, M = np.concatenate([X, X2]), np.concatenate([T, T2]), np.concatenate([M, M2])
         p, loss = train_scorer(X, T, M, epochs=a.epochs)
     save(p, a.out, {"samples": int(len(X)), "instances": a.instances, "outlier_instances": a.outlier_instances,
-                    "epochs": a.epochs, "loss": loss, "node_limit": a.node_limit, "rounds": a.rounds,
+                    "epochs": a.epochs, "loss": loss, "node_limit": a.node_limit, "stages": a.stages,
                     "explore": a.explore, "n_lo": a.n_lo, "n_hi": a.n_hi,
                     "command": "python -m paper_2301_00061_gb300.scorer " + " ".join(argv or sys.argv[1:])})
     print(json.dumps({"samples": int(len(X)), "loss": loss, "out": a.out}))
