@@ -321,3 +321,33 @@ def test_full_size_bounds_and_prunes_replayed(tmp_path):
             assert r["key"] <= beta and r["key"] >= beta * (1 - 1e-6), (name, r["child"], r["key"], beta)
             if r["pruned"]:
                 assert beta >= alpha * (1 - 1e-12), (name, r["child"], beta, alpha)
+
+
+def test_solve_degenerate_and_edge_inputs():
+    """Edge cases of the method: N = K (every sample its own center, optimum
+    0); all samples identical (zero-range root box, optimum 0); one attribute;
+    float data smaller than one list tile (per-node lists never filtered);
+    options out of range are rejected with a message."""
+    from paper_2301_00061_gb300 import KCError
+    X = np.array([[0.0, 0.0], [3.0, 1.0], [-2.0, 5.0]], np.float32)
+    g = KCenter(_t(X), 3).solve(tol=1e-12)
+    assert g["status"] == 0 and g["objective"] == 0.0 and sorted(g["centers"].tolist()) == [0, 1, 2]
+    X = np.full((50, 3), 1.25, np.float32)
+    g = KCenter(_t(X), 2).solve(tol=1e-12)
+    assert g["status"] == 0 and g["objective"] == 0.0
+    X = _blobs(500, 1, 3, seed=9, dtype=np.float32)
+    g, r = _solve_both(X, 3)
+    assert g["status"] == 0 and abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"]
+    for seed in range(3):
+        X = _blobs(int(np.random.default_rng(seed).integers(20, 60)), 2, 3, seed=seed, dtype=np.float32)
+        g = KCenter(_t(X), 3).solve(tol=0.0, lists=1)
+        z, _ = oracle.bruteforce(X, 3)
+        assert abs(g["objective"] - z) <= 1e-12 * z, (seed, g, z)
+    kc = KCenter(_t(_blobs(200, 2, 3, seed=1, dtype=np.float32)), 3)
+    for bad in (dict(explore=101), dict(batch=5000), dict(rule_margin=-1.0), dict(fft_starts=-1), dict(lists=2),
+                dict(order=1)):
+        with pytest.raises(KCError) as e:
+            kc.solve(tol=1e-12, **bad)
+        assert "kc_solve" in str(e.value), (bad, str(e.value))
+    with pytest.raises(KCError):
+        kc.solve(tol=1.5)
