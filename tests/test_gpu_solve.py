@@ -351,3 +351,15 @@ def test_solve_degenerate_and_edge_inputs():
         assert "kc_solve" in str(e.value), (bad, str(e.value))
     with pytest.raises(KCError):
         kc.solve(tol=1.5)
+
+
+@pytest.mark.parametrize("d,k", [(3, 3), (3, 4), (6, 2), (8, 2), (4, 4)])
+def test_solve_f32_lists_other_shapes(d, k):
+    """Per-node lists with the remaining compiled tightening shapes (K=3 D=3,
+    K<=4 D<=4, K<=2 D<=8): the certified optimum equals the oracle's.  Seed 1
+    of each shape gives a tree of 15-1,600 oracle nodes."""
+    X = _blobs(2_500, d, k, seed=1, dtype=np.float32)
+    g, r = _solve_both(X, k, lists=1)
+    assert g["status"] == 0
+    assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
+    assert oracle.objective(X, g["centers"])[0] == g["objective"]
