@@ -49,6 +49,7 @@ class SolveOpts(C.Structure):
         ("log_path", C.c_char_p),
         ("rule_margin", C.c_double),
         ("fft_starts", C.c_int32),
+        ("rule_width", C.c_int32),
     ]
 
 

@@ -352,6 +352,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     std::vector<double> range0(D);
     for (int a = 0; a < D; ++a) range0[a] = std::max((double)root_hi[a] - (double)root_lo[a], 1e-300);
     kc_mlp *scorer = (o.order == 1) ? c->scorer : nullptr;
+    const double rule_width = o.rule_width > 0 ? (double)o.rule_width : 16.0;
 
     const int Bmax = o.batch > 0 ? o.batch : 256;
     // device batch buffers
@@ -770,14 +771,15 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 KC_CUDA(c, cudaMemcpyAsync(h_out.data(), d_out, (size_t)NB * 2 * 4, cudaMemcpyDeviceToHost, c->stream));
                 KC_CUDA(c, cudaStreamSynchronize(c->stream));
                 // output r: predicted cost of branching with rule r; take the cheaper,
-                // but rule 1 only on a variable whose range is at least 1/16 of the
-                // largest: splitting one short side over and over leaves the other
-                // boxes large, and tightening and list filtering then stall
+                // but rule 1 only on a variable whose range is at least 1/rule_width
+                // (default 1/16) of the largest: splitting one short side over and
+                // over leaves the other boxes large, and tightening and list
+                // filtering then stall
                 for (int i = 0; i < NB; ++i) {
                     const float c0 = h_out[(size_t)i * 2], c1 = h_out[(size_t)i * 2 + 1];
                     const T *lb2 = h_lo2 + (size_t)br[i] * KD, *hb2 = h_hi2 + (size_t)br[i] * KD;
                     const bool wide = rule1[i] >= 0 &&
-                                      16.0 * ((double)hb2[rule1[i]] - (double)lb2[rule1[i]]) >=
+                                      rule_width * ((double)hb2[rule1[i]] - (double)lb2[rule1[i]]) >=
                                           (double)hb2[rule0[i]] - (double)lb2[rule0[i]];
                     const bool take1 = wide && (double)c1 < (double)c0 - o.rule_margin;
                     if (take1) choice[i] = rule1[i];
@@ -1262,6 +1264,7 @@ kc_status kc_solve(kc_ctx *c, double tol, const kc_solve_opts *opt, kc_result *o
     if (o.explore < 0 || o.explore > 100) return set_err(c, KC_EINVAL, "kc_solve: explore must be in [0, 100]");
     if (!(o.rule_margin >= 0.0)) return set_err(c, KC_EINVAL, "kc_solve: rule_margin must be >= 0");
     if (o.fft_starts < 0 || o.fft_starts > 4096) return set_err(c, KC_EINVAL, "kc_solve: fft_starts must be in [0, 4096]");
+    if (o.rule_width < 0) return set_err(c, KC_EINVAL, "kc_solve: rule_width must be >= 0");
     std::memset(out, 0, sizeof(*out));
     if (c->dt == KC_F32) return solve_impl<float>(c, o, out);
     return solve_impl<double>(c, o, out);
