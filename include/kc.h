@@ -236,7 +236,7 @@ kc_status kc_sample_reduction(kc_ctx *ctx, const void *lo, const void *hi, int32
  * rule 0 is the max-range rule of Section 3.3, rule 1 splits the box nearest to
  * the sample attaining the node's lower bound, on the attribute where that
  * sample lies farthest outside it (taken only where that attribute's range is
- * at least 1/16 of the largest, kc_solve_opts.rule_width).  The solver takes the cheaper rule and orders
+ * at least 1/4 of the largest, kc_solve_opts.rule_width).  The solver takes the cheaper rule and orders
  * equal lower bounds by the smaller predicted cost.  The paper has no
  * learned component: the exact lower bound still decides every prune, so the
  * certified optimum cannot change.  Parameters are one float vector of 5122
@@ -288,7 +288,7 @@ typedef struct {
     int32_t fft_starts;    /* 1 (0 = 1): FFT runs from this many start samples (seed mod N, then
                               steps of 2654435761 mod N); the best is the first incumbent and
                               kc_result.fft_objective */
-    int32_t rule_width;    /* 16 (0 = 16): with order = 1, rule 1 only on a variable whose range is
+    int32_t rule_width;    /* 4 (0 = 4): with order = 1, rule 1 only on a variable whose range is
                               at least 1/rule_width of the largest range */
 } kc_solve_opts;
 

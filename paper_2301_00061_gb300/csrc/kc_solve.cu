@@ -352,7 +352,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     std::vector<double> range0(D);
     for (int a = 0; a < D; ++a) range0[a] = std::max((double)root_hi[a] - (double)root_lo[a], 1e-300);
     kc_mlp *scorer = (o.order == 1) ? c->scorer : nullptr;
-    const double rule_width = o.rule_width > 0 ? (double)o.rule_width : 16.0;
+    const double rule_width = o.rule_width > 0 ? (double)o.rule_width : 4.0;
 
     const int Bmax = o.batch > 0 ? o.batch : 256;
     // device batch buffers
@@ -772,7 +772,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 KC_CUDA(c, cudaStreamSynchronize(c->stream));
                 // output r: predicted cost of branching with rule r; take the cheaper,
                 // but rule 1 only on a variable whose range is at least 1/rule_width
-                // (default 1/16) of the largest: splitting one short side over and
+                // (default 1/4) of the largest: splitting one short side over and
                 // over leaves the other boxes large, and tightening and list
                 // filtering then stall
                 for (int i = 0; i < NB; ++i) {
@@ -1245,6 +1245,7 @@ void kc_solve_defaults(kc_solve_opts *o)
     o->i_sr = 1;
     o->use_bt = 1;
     o->lists = 1;
+    o->rule_width = 4;
 }
 
 kc_status kc_solve(kc_ctx *c, double tol, const kc_solve_opts *opt, kc_result *out)
