@@ -341,3 +341,18 @@ def test_sample_reduction_keeps_bound_samples():
     # the root node keeps everything: alpha_s(M0) is large
     act0 = oracle.sample_reduction(X, L, H, 0.0, alpha, np.ones(300, bool))
     assert act0.all()
+
+
+def test_tighten_hand_examples():
+    """Tightening (Algorithms 3-4) on hand-derived 1-D instances: assignment,
+    box-based tightening with the sqrt(alpha) radius, centers on samples,
+    candidates, infeasibility and the leaf status."""
+    for ex in GOLD["tighten"]:
+        X = np.array(ex["X"])
+        r = oracle.tighten(X, np.array(ex["lo"]), np.array(ex["hi"]), ex["alpha"])
+        assert r["status"] == ex["status"], ex["derivation"]
+        assert r["beta"] == ex["beta"]
+        if ex["status"] == 0:
+            assert r["box_bt_lo"].tolist() == ex["box_bt_lo"] and r["box_bt_hi"].tolist() == ex["box_bt_hi"]
+            assert r["lo"].tolist() == ex["lo_out"] and r["hi"].tolist() == ex["hi_out"]
+            assert list(r["count"]) == ex["count"] and list(r["cand"]) == ex["cand"]
