@@ -9,13 +9,18 @@
 //      samples" boxes, counts and an upper-bound candidate per cluster;
 //   3. evaluate the candidates' objective (float screen, exact double value);
 //   4. prune (bound >= incumbent), drop infeasible nodes, close leaves, and
-//      branch the rest on the max-range variable at its midpoint; children
-//      inherit the parent's certified bound as their key;
-//   5. every i_sr batches, sample reduction against the hull of the open
-//      nodes, then compaction of the surviving samples.
-// Bounds are computed when a node is visited rather than when it is created
-// (the children of one batch are bounded in the next), so one pass per node
-// evaluates its bound, tightens it and yields its candidate.
+//      branch the rest at the midpoint of the chosen variable (max range, or
+//      the learned scorer's pick between two rules);
+//   5. sample reduction (Section 4.2): with per-node lists (float data), the
+//      branched node's list is filtered to the samples that are not
+//      redundant for both bounds, and the same pass bounds both children over
+//      it; with one shared sample set, every i_sr batches the set is reduced
+//      against the hulls of the open nodes and compacted;
+//   6. bound the children as they are created (those not bounded by the
+//      filter get a bound launch over their list); only children below the
+//      incumbent enter the open set, keyed by max(parent bound, own bound).
+// A visited node's bound is evaluated again by the tightening pass, over the
+// samples it holds then, and its key is the larger of the two.
 #include <cuda_runtime.h>
 
 #include <algorithm>
