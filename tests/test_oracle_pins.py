@@ -356,3 +356,16 @@ def test_tighten_hand_examples():
             assert r["box_bt_lo"].tolist() == ex["box_bt_lo"] and r["box_bt_hi"].tolist() == ex["box_bt_hi"]
             assert r["lo"].tolist() == ex["lo_out"] and r["hi"].tolist() == ex["hi_out"]
             assert list(r["count"]) == ex["count"] and list(r["cand"]) == ex["cand"]
+
+
+def test_sample_reduction_hand_examples():
+    """Algorithm 5 on hand-derived 1-D instances: both redundancy tests, the
+    strict LB-redundancy inequality, deletion only when redundant in every
+    node, and the no-representative case."""
+    for ex in GOLD["sample_reduction"]:
+        lo = np.array([nd["lo"] for nd in ex["nodes"]])
+        hi = np.array([nd["hi"] for nd in ex["nodes"]])
+        X = np.array(ex["X"])
+        act = oracle.sample_reduction(X, lo, hi, ex["beta_glob"], ex["alpha"], np.ones(len(X), bool),
+                                      reps=ex["reps"])
+        assert act.astype(int).tolist() == ex["active_out"], ex["derivation"]
