@@ -27,14 +27,15 @@ _lib = None
 MAXK, MAXD, MAXREPS = 16, 64, 50
 
 
+GCC_FLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+
+
 def build(force=False):
     """Compile kc_oracle.c into liboracle.so next to it (gcc, no FP contraction)."""
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    subprocess.run(["gcc", *GCC_FLAGS, "-o", tmp, _SRC, "-lm"], check=True)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -94,8 +95,13 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_LIB)
+            # KCO_ORACLE_LIB names a prebuilt variant of this file's library
+            # (the mutation tests plant a mistake in a copy of kc_oracle.c and
+            # check that the pins catch it); otherwise build next to the source
+            path = os.environ.get("KCO_ORACLE_LIB")
+            if not path:
+                path = build()
+            L = C.CDLL(path)
             sig = {
                 "kco_beta_sk": (_D, [_P, _P, _P, _I32]),
                 "kco_root_box": (_I32, [_P, _I64, _I32, _P, _P]),
@@ -110,6 +116,7 @@ def lib():
                 "kco_tighten": (_I32, [_P, _I64, _I32, _I32, _P, _P, _D, _P, _P, _I32, _I32, _P]),
                 "kco_sample_reduction": (_I64, [_P, _I64, _I32, _I32, _I32, _P, _P, _P, _P, _D, _D, _P]),
                 "kco_solve": (_I32, [_P, _I64, _I32, _I32, _P, _P]),
+                "kco_split_point": (None, [_D, _D, _I32, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -202,6 +209,14 @@ def mid_candidate(X, lo, hi, active=None):
     m = _mask(active)
     idx = lib().kco_mid_candidate(_ptr(X), n, d, _ptr(lo), _ptr(hi), _ptr(m), C.addressof(dist))
     return idx, dist.value
+
+
+def split_point(lo, hi, is_f32=False):
+    """Branching value m of [lo, hi] (lo < hi) and the lower end succ(m) of the
+    upper child: children [lo, m] and [succ(m), hi]."""
+    m, succ = C.c_double(), C.c_double()
+    lib().kco_split_point(float(lo), float(hi), int(bool(is_f32)), C.addressof(m), C.addressof(succ))
+    return m.value, succ.value
 
 
 def fft(X, k, start):

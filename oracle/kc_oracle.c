@@ -314,6 +314,12 @@ static void split_point(double lo, double hi, int is_f32, double *m_out, double 
     }
 }
 
+/* The branching value of [lo, hi] and its successor, for the tests. */
+void kco_split_point(double lo, double hi, int is_f32, double *m_out, double *succ_out)
+{
+    split_point(lo, hi, is_f32, m_out, succ_out);
+}
+
 /* ---------------------------------------------------------------------- */
 /* Cluster assignment and bounds tightening (Section 4.1, Algorithms 3, 4) */
 /* ---------------------------------------------------------------------- */

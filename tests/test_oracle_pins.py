@@ -353,9 +353,17 @@ def test_tighten_hand_examples():
         assert r["status"] == ex["status"], ex["derivation"]
         assert r["beta"] == ex["beta"]
         if ex["status"] == 0:
-            assert r["box_bt_lo"].tolist() == ex["box_bt_lo"] and r["box_bt_hi"].tolist() == ex["box_bt_hi"]
+            blo, bhi = np.array(ex["box_bt_lo"]), np.array(ex["box_bt_hi"])
+            if ex.get("outward"):
+                # radius rounded up, bounds rounded outward: at most a few ulps wider
+                assert np.all(r["box_bt_lo"] <= blo) and np.all(r["box_bt_lo"] >= blo - 1e-14)
+                assert np.all(r["box_bt_hi"] >= bhi) and np.all(r["box_bt_hi"] <= bhi + 1e-14)
+            else:
+                assert r["box_bt_lo"].tolist() == ex["box_bt_lo"] and r["box_bt_hi"].tolist() == ex["box_bt_hi"]
             assert r["lo"].tolist() == ex["lo_out"] and r["hi"].tolist() == ex["hi_out"]
             assert list(r["count"]) == ex["count"] and list(r["cand"]) == ex["cand"]
+            if "n_assigned" in ex:
+                assert list(r["n_assigned"]) == ex["n_assigned"]
 
 
 def test_sample_reduction_hand_examples():
@@ -369,3 +377,36 @@ def test_sample_reduction_hand_examples():
         act = oracle.sample_reduction(X, lo, hi, ex["beta_glob"], ex["alpha"], np.ones(len(X), bool),
                                       reps=ex["reps"])
         assert act.astype(int).tolist() == ex["active_out"], ex["derivation"]
+
+
+@pytest.mark.parametrize("ex", GOLD["mid_candidate"], ids=lambda e: e["cite"][:24])
+def test_golden_mid_candidate(ex):
+    """UB candidate of one box (Section 3.2): the sample inside the box nearest
+    to its middle point, smallest index on ties, -1 for an empty box."""
+    idx, dist = oracle.mid_candidate(np.array(ex["X"]), np.array(ex["lo"]), np.array(ex["hi"]))
+    assert idx == ex["index"], ex["derivation"]
+    if idx >= 0:
+        assert dist == ex["dist"]
+
+
+def test_root_box_every_row_position():
+    """M0 (Section 2.1) under every order of the rows: each extreme is taken
+    whichever position holds it."""
+    X = np.array([[0.0, 5.0], [3.0, -1.0], [-2.0, 2.0], [1.0, 7.0]])
+    for perm in itertools.permutations(range(4)):
+        lo, hi = oracle.root_box(X[list(perm)])
+        assert lo.tolist() == [-2.0, -1.0] and hi.tolist() == [3.0, 7.0]
+
+
+@pytest.mark.parametrize("ex", GOLD["objective_argmax"], ids=lambda e: e["derivation"][:16])
+def test_golden_objective_argmax(ex):
+    """Objective of a center set and the sample attaining it (Eq. 1)."""
+    v, arg = oracle.objective(np.array(ex["X"]), np.array(ex["centers"]))
+    assert v == ex["value"] and arg == ex["argmax"], ex["derivation"]
+
+
+@pytest.mark.parametrize("ex", GOLD["split_point"], ids=lambda e: f'{e["lo"]}-{e["hi"]}')
+def test_golden_split_point(ex):
+    """Branching value (Section 3.3) and the upper child's lower end."""
+    m, succ = oracle.split_point(ex["lo"], ex["hi"], ex["is_f32"])
+    assert (m, succ) == (ex["m"], ex["succ"]), ex["derivation"]
