@@ -68,3 +68,28 @@ def test_init_is_seeded_and_he_scaled():
     assert np.array_equal(a, b) and a.dtype == np.float32 and a.size == mlp.NPARAM == 5122
     W1 = mlp.unpack(a)["W1"]
     assert np.abs(W1).max() <= np.sqrt(6.0 / 12) + 1e-6
+
+
+def test_forward_one_path_closed_form():
+    """A single active path through the network (bf16-exact weights): input
+    e_0 -> hidden unit 5 of layer 1 (weight 1) -> unit 7 of layer 2 (weight
+    2) -> output 1 (weight 3) gives y = (0, 6); the weight W[i, j] maps unit j
+    of the layer below to unit i (z = W h + b)."""
+    p = mlp.unpack(np.zeros(mlp.NPARAM, np.float32).copy())
+    p["W1"][5, 0] = 1.0
+    p["W2"][7, 5] = 2.0
+    p["W3"][1, 7] = 3.0
+    theta = mlp.pack(p).astype(np.float32)
+    x = np.zeros((2, mlp.NIN)); x[0, 0] = 1.0; x[1, 0] = -1.0
+    y, _ = mlp.forward(theta, x)
+    assert y.tolist() == [[0.0, 6.0], [0.0, 0.0]]   # the negative input is cut by the first ReLU
+
+
+def test_adam_bias_correction_over_steps():
+    """Adam with a constant gradient g: the bias-corrected moments are exactly
+    g and g^2 at every step, so each step moves lr * g / (|g| + eps)."""
+    g = np.array([2.0, -0.25])
+    th, m, v = np.zeros(2), np.zeros(2), np.zeros(2)
+    for t in range(1, 4):
+        th, m, v = mlp.adam_step(th, m, v, g, t, lr=0.01)
+    assert th == pytest.approx(-3 * 0.01 * g / (np.abs(g) + 1e-8), rel=1e-12)
