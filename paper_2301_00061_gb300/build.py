@@ -1,8 +1,8 @@
 """Builds libkc.so (the CUDA library behind include/kc.h) for sm_103a.
 
 Each .cu file is compiled on its own thread, then linked into a shared
-library next to this file.  Used by ``__graft_entry__.build()`` and by the
-package import when the library is missing or older than its sources.
+library next to this file.  Used by ``__graft_entry__.build()``; the package
+import never builds, and refuses to load when the library is missing.
 """
 from __future__ import annotations
 

@@ -58,3 +58,20 @@ def test_null_context_is_rejected(kcpkg):
     assert lib.kc_root_box(None, None, None) == 1
     lib.kc_last_error.restype = C.c_char_p
     assert lib.kc_last_error(None) == b"null context"
+
+
+def test_import_fails_loudly_without_the_library(tmp_path):
+    """A copy of the package without libkc.so refuses to import: no CPU
+    fallback exists."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = os.path.join(ROOT, "paper_2301_00061_gb300")
+    dst = tmp_path / "paper_2301_00061_gb300"
+    dst.mkdir()
+    for f in os.listdir(pkg):
+        if f.endswith(".py") or f.endswith(".json"):
+            shutil.copy(os.path.join(pkg, f), dst / f)
+    r = subprocess.run([sys.executable, "-c", "import paper_2301_00061_gb300"], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0 and "ImportError" in r.stderr and "not built" in r.stderr, r.stderr[-2000:]
