@@ -204,6 +204,10 @@ kc_status kc_fft(kc_ctx *ctx, int64_t start, int64_t *centers_out, double *obj_o
  *   status          [B] int8: 0 feasible, 1 proved to hold no solution of
  *                   value <= alpha, 2 leaf (every tightened box is a point).
  * ball_cap <= 0 selects the default of 50.
+ * Shapes: float data K <= 4 with D <= 4, or K <= 2 with D <= 8; double data
+ * K <= 4 with D <= 4 (the kernels keep a node's boxes in registers and
+ * per-warp shared memory sized at compile time).  Other shapes return
+ * KC_EINVAL.
  */
 kc_status kc_tighten(kc_ctx *ctx, const void *lo, const void *hi, int32_t B, double alpha,
                      const int64_t *seeds, int32_t ball_cap, void *lo_out, void *hi_out,
@@ -223,6 +227,7 @@ kc_status kc_tighten(kc_ctx *ctx, const void *lo, const void *hi, int32_t B, dou
  *                 the sample is deleted.  Float data delete only where the
  *                 float evaluation proves redundancy.
  *   n_active_out  remaining samples, or NULL.
+ * Shapes: D <= 8 (KC_EINVAL otherwise).
  */
 kc_status kc_sample_reduction(kc_ctx *ctx, const void *lo, const void *hi, int32_t M,
                               const int64_t *reps, int32_t R, double beta_glob, double alpha,
@@ -326,6 +331,8 @@ void kc_solve_defaults(kc_solve_opts *opt);
  * overrides opt->tol when >= 0.  Returns KC_OK at optimality within tol,
  * KC_ETIMEOUT / KC_ELIMIT (with *out filled) at a limit, KC_EINVAL for
  * options out of range, KC_ENOMEM when the list arena or buffers do not fit.
+ * Shapes: those of kc_tighten (float K <= 4 with D <= 4, or K <= 2 with
+ * D <= 8; double K <= 4 with D <= 4); other shapes return KC_EINVAL.
  */
 kc_status kc_solve(kc_ctx *ctx, double tol, const kc_solve_opts *opt, kc_result *out);
 
