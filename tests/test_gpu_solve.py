@@ -314,6 +314,26 @@ def test_full_size_bounds_and_prunes_replayed(tmp_path):
         sample = [kids[i] for i in rng.choice(len(kids), 8, replace=False)]
         sample += [pruned[i] for i in rng.choice(len(pruned), min(8, len(pruned)), replace=False)]
         alpha = g["objective"]
+        # the two children of every branched node partition its boxes: equal
+        # except at one coordinate, split into [lo, m] and [succ(m), hi] with
+        # succ the next float; each child's key is at least its parent's bound
+        nodes = {r["id"]: r for r in map(json.loads, open(log)) if "id" in r}
+        by_parent = {}
+        for r in kids:
+            by_parent.setdefault(r["parent"], []).append(r)
+        assert all(len(v) == 2 for v in by_parent.values())
+        for pid, (c0, c1) in by_parent.items():
+            lo0, hi0 = np.array(c0["lo"], np.float32), np.array(c0["hi"], np.float32)
+            lo1, hi1 = np.array(c1["lo"], np.float32), np.array(c1["hi"], np.float32)
+            if c0["child"] > c1["child"]:
+                lo0, hi0, lo1, hi1 = lo1, hi1, lo0, hi0
+            split = np.flatnonzero((lo0 != lo1) | (hi0 != hi1))
+            assert len(split) == 1, (name, pid)
+            i = split[0]
+            assert lo0[i] <= hi0[i] < lo1[i] <= hi1[i] and lo1[i] == np.nextafter(hi0[i], np.float32(np.inf))
+            assert np.array_equal(np.delete(lo0, i), np.delete(lo1, i)) and np.array_equal(np.delete(hi0, i), np.delete(hi1, i))
+            if pid in nodes:
+                assert min(c0["key"], c1["key"]) >= nodes[pid]["lb"], (name, pid)
         for r in sample:
             lo = np.array(r["lo"], np.float32).reshape(w.k, w.d)
             hi = np.array(r["hi"], np.float32).reshape(w.k, w.d)
@@ -351,6 +371,12 @@ def test_solve_degenerate_and_edge_inputs():
         assert "kc_solve" in str(e.value), (bad, str(e.value))
     with pytest.raises(KCError):
         kc.solve(tol=1.5)
+    # shapes without a tightening instantiation are refused, not run
+    kc5 = KCenter(_t(_blobs(200, 2, 5, seed=1, dtype=np.float32)), 5)
+    with pytest.raises(KCError) as e:
+        kc5.solve(tol=1e-12)
+    assert e.value.status == 1 and "kc_tighten" in str(e.value)
+    kc5.close()
 
 
 @pytest.mark.parametrize("d,k", [(3, 3), (3, 4), (6, 2), (8, 2), (4, 4)])
