@@ -61,7 +61,7 @@ struct kc_ctx {
     size_t pinned_bytes = 0;
     int64_t launches = 0;
     std::string err;
-    // autotuned launch shapes, keyed by kernel family (see kc_tune.cu)
+    // launch shape of the float lower-bound kernel, set by kc_autotune (kc_lb.cu)
     int lb_st = 0;               // samples per thread of the float lower-bound kernel
     int lb_chunk = 0;            // node chunk of the float lower-bound kernel (0: largest that fits)
 };
