@@ -389,3 +389,31 @@ def test_solve_f32_lists_other_shapes(d, k):
     assert g["status"] == 0
     assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
     assert oracle.objective(X, g["centers"])[0] == g["objective"]
+
+
+def test_solve_limits_and_repeatability():
+    """Stopping rules and determinism.  A time limit or a node limit returns
+    KC_ETIMEOUT (4) or KC_ELIMIT (5) with a valid incumbent (its double
+    objective over all samples), a certified bound no higher than it and the
+    gap between them.  The same solve repeated gives the same optimum,
+    centers, bound and node count, and the same bound batch repeated gives
+    bitwise-equal outputs: the packed-key reductions do not depend on the
+    order in which threads finish."""
+    X = _blobs(200_000, 4, 3, seed=3, dtype=np.float32)
+    kc = KCenter(_t(X), 3)
+    for kw, st in ((dict(time_limit_s=1e-6), 4), (dict(node_limit=1), 5)):
+        g = kc.solve(tol=1e-12, **kw)
+        assert g["status"] == st, (kw, g)
+        assert g["objective"] == oracle.objective(X, g["centers"])[0]
+        assert 0.0 <= g["lower_bound"] <= g["objective"]
+        assert g["gap"] == pytest.approx((g["objective"] - g["lower_bound"]) / g["objective"], rel=1e-12)
+    runs = [kc.solve(tol=1e-12, node_limit=3000) for _ in range(2)]
+    for key in ("status", "objective", "lower_bound", "nodes", "batches", "lists_filtered", "samples_dropped"):
+        assert runs[0][key] == runs[1][key], (key, runs)
+    assert np.array_equal(runs[0]["centers"], runs[1]["centers"])
+    lo, hi = _nodes_around(X, runs[0]["centers"], 64, seed=4)
+    outs = [[t.cpu().numpy() for t in kc.lower_bounds(_t(lo), _t(hi))] for _ in range(3)]
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+    kc.close()
