@@ -242,13 +242,18 @@ def main():
     lbh = torch.empty(B_NODES, dtype=torch.float64).pin_memory()
     argh = torch.empty(B_NODES, dtype=torch.int64).pin_memory()
     e2e_steps = max(1, args.e2e_steps)
+
+    def e2e_step():
+        h2 = kcm.kc_create(Xp, w.k, stream=stream.cuda_stream)
+        kcm.kc_lower_bounds(h2, lop, hip, lbh, None, argh)
+        kcm.kc_destroy(h2)
+
+    e2e_step()   # untimed warm-up (first-touch of the pinned buffers)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        h2 = kcm.kc_create(Xp, w.k, stream=stream.cuda_stream)
-        kcm.kc_lower_bounds(h2, lop, hip, lbh, None, argh)
-        kcm.kc_destroy(h2)
+        e2e_step()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = max_over_ranks(e2e_s, ws)

@@ -3,6 +3,7 @@
 // single kernel family (root box, lower bounds, upper bounds, FFT).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
@@ -153,14 +154,16 @@ kc_status kc_create(const void *X, int64_t N, int32_t D, int32_t K, kc_dtype dt,
         set_err(c, KC_ECUDA, "kc_create: no CUDA device");
         return fail(KC_ECUDA);
     }
-    cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, c->dev) != cudaSuccess) {
-        set_err(c, KC_ECUDA, "kc_create: cudaGetDeviceProperties failed");
+    int sms = 0, smem_optin = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, KC_ECUDA, "kc_create: cannot query the device");
         return fail(KC_ECUDA);
     }
-    c->num_sms = prop.multiProcessorCount;
+    c->num_sms = sms;
     if (const char *e = getenv("KC_LB_ST")) c->lb_st = atoi(e);
-    c->smem_optin = prop.sharedMemPerBlockOptin;
+    c->smem_optin = (size_t)smem_optin;
     const size_t xbytes = (size_t)D * c->ldx * c->esize;
     if (cudaMalloc(&c->X, xbytes) != cudaSuccess) {
         cudaGetLastError();
@@ -180,12 +183,24 @@ kc_status kc_create(const void *X, int64_t N, int32_t D, int32_t K, kc_dtype dt,
                                   (c->ldx - N) * c->esize, D, c->stream);
         if (e != cudaSuccess) st = set_err(c, KC_ECUDA, "kc_create: upload failed: %s", cudaGetErrorString(e));
     } else {
-        st = ensure(c, c->work, src_bytes);
-        if (st == KC_OK) {
-            cudaError_t e = cudaMemcpyAsync(c->work.p, X, src_bytes, cudaMemcpyHostToDevice, c->stream);
+        // host rows: upload in chunks of at most 32 MiB through one staging
+        // buffer, each transposed into place (stream order keeps the next
+        // upload behind the previous transpose)
+        const int64_t row_bytes = (int64_t)D * c->esize;
+        const int64_t rows = std::min<int64_t>(N, std::max<int64_t>(1, ((int64_t)32 << 20) / row_bytes));
+        st = ensure(c, c->work, (size_t)(rows * row_bytes));
+        for (int64_t s0 = 0; st == KC_OK && s0 < N; s0 += rows) {
+            const int64_t n = std::min(rows, N - s0);
+            cudaError_t e = cudaMemcpyAsync(c->work.p, static_cast<const char *>(X) + s0 * row_bytes,
+                                            (size_t)(n * row_bytes), cudaMemcpyHostToDevice, c->stream);
             if (e != cudaSuccess) st = set_err(c, KC_ECUDA, "kc_create: upload failed: %s", cudaGetErrorString(e));
+            else st = launch_ingest_rows(c, c->work.p, s0, n);
         }
-        if (st == KC_OK) st = launch_ingest(c, c->work.p, layout, N, D);
+        if (st == KC_OK && c->ldx > N) {
+            cudaError_t e = cudaMemset2DAsync(static_cast<char *>(c->X) + N * c->esize, c->ldx * c->esize, 0,
+                                              (c->ldx - N) * c->esize, D, c->stream);
+            if (e != cudaSuccess) st = set_err(c, KC_ECUDA, "kc_create: padding failed: %s", cudaGetErrorString(e));
+        }
     }
     if (st != KC_OK) return fail(st);
     // non-finite scan (with the root box, which is cheap)
@@ -205,7 +220,7 @@ kc_status kc_create(const void *X, int64_t N, int32_t D, int32_t K, kc_dtype dt,
         set_err(c, KC_EINVAL, "kc_create: the data contain NaN or infinite values");
         return fail(KC_EINVAL);
     }
-    if (src_bytes > ((size_t)64 << 20) && c->work.p) {   // do not keep a dataset-sized scratch around
+    if (src_bytes > ((size_t)64 << 20) && c->work.p) {   // release the upload staging buffer of large datasets
         cudaFree(c->work.p);
         c->work.p = nullptr;
         c->work.bytes = 0;

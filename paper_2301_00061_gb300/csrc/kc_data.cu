@@ -3,6 +3,8 @@
 // stream compaction of the surviving samples after sample reduction.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kc_device.cuh"
 #include "kc_internal.cuh"
 
@@ -20,6 +22,21 @@ __global__ void transpose_in(const T *__restrict__ src, int64_t N, int D, int64_
         const int a = (int)(i / ld);
         const int64_t s = i - (int64_t)a * ld;
         dst[i] = s < N ? src[s * D + a] : T(0);
+    }
+}
+
+// Rows s0 .. s0 + n of a row-major dataset, staged at src as [n][D] ->
+// attribute-major dst[a * ld + s0 + i] (one chunk of a host upload).
+template <typename T>
+__global__ void transpose_rows(const T *__restrict__ src, int64_t s0, int64_t n, int D, int64_t ld,
+                               T *__restrict__ dst)
+{
+    const int64_t total = (int64_t)D * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(i / n);
+        const int64_t s = i - (int64_t)a * n;
+        dst[(size_t)a * ld + s0 + s] = src[s * D + a];
     }
 }
 
@@ -111,6 +128,19 @@ kc_status launch_ingest(kc_ctx *c, const void *src_dev, kc_layout layout, int64_
         transpose_in<double><<<grid, 256, 0, c->stream>>>(static_cast<const double *>(src_dev), N, D, c->ldx,
                                                           static_cast<double *>(c->X));
     return after_launch(c, "ingest transpose");
+}
+
+kc_status launch_ingest_rows(kc_ctx *c, const void *chunk_dev, int64_t s0, int64_t n)
+{
+    if (n <= 0) return KC_OK;
+    const int grid = (int)std::min<int64_t>((int64_t)c->num_sms * 8, ((int64_t)c->D * n + 255) / 256);
+    if (c->dt == KC_F32)
+        transpose_rows<float><<<grid, 256, 0, c->stream>>>(static_cast<const float *>(chunk_dev), s0, n, c->D, c->ldx,
+                                                           static_cast<float *>(c->X));
+    else
+        transpose_rows<double><<<grid, 256, 0, c->stream>>>(static_cast<const double *>(chunk_dev), s0, n, c->D,
+                                                            c->ldx, static_cast<double *>(c->X));
+    return after_launch(c, "ingest transpose (chunk)");
 }
 
 kc_status launch_root_box(kc_ctx *c, void *lo, void *hi, int *nonfinite_dev)

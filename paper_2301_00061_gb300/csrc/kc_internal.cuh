@@ -194,6 +194,9 @@ kc_status launch_root_box(kc_ctx *c, void *lo, void *hi, int *nonfinite_dev);
 
 // Attribute-major padded copy from the user's layout.
 kc_status launch_ingest(kc_ctx *c, const void *src, kc_layout layout, int64_t N, int D);
+// Rows s0 .. s0 + n of a row-major dataset staged on the device as [n][D]
+// into the context's attribute-major copy (padding not touched).
+kc_status launch_ingest_rows(kc_ctx *c, const void *chunk_dev, int64_t s0, int64_t n);
 
 // Cluster assignment + bounds tightening of B nodes over a sample view (see kc.h).
 kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int B, double alpha,

@@ -106,6 +106,30 @@ def test_lower_bound_host_pointers_and_edge_cases():
     assert lb3[0] == 0.0 and raw3[0] == 0.0 and arg3[0] == 0
 
 
+@pytest.mark.parametrize("dtype,n,d", [(np.float32, 4_194_305, 4), (np.float64, 1_398_103, 3)])
+def test_host_row_major_upload_in_chunks(dtype, n, d):
+    """Host row-major data reach the device in 32 MiB chunks, each transposed
+    into the attribute-major copy: with 3 (float, D=4) and 2 (double, D=3)
+    chunks, the last one ragged, the context holds the same data as one made
+    from a device tensor -- same root box, bitwise the same bounds and
+    objective."""
+    X = _mix(n, d, 3, seed=11, dtype=dtype)
+    kh, kd = KCenter(X, 3), KCenter(_t(X), 3)
+    rlo, rhi = kh.root_box()
+    assert np.array_equal(rlo, X.min(0)) and np.array_equal(rhi, X.max(0))
+    lo, hi = synth.random_boxes(X, 3, 16, seed=3)
+    a = kh.lower_bounds(lo, hi)
+    b = [t.cpu().numpy() for t in kd.lower_bounds(_t(lo), _t(hi))]
+    for u, v in zip(a, b):
+        assert np.array_equal(u.view(np.uint8), v.view(np.uint8))
+    c = np.array([[0, n // 2, n - 1]], np.int64)
+    ub_h, w_h = kh.upper_bound(c)
+    ub_d, w_d = kd.upper_bound(_t(c))
+    assert ub_h[0] == float(ub_d[0]) and w_h[0] == int(w_d[0]) and ub_h[0] == oracle.objective(X, c[0])[0]
+    kh.close()
+    kd.close()
+
+
 def test_lower_bounds_ties_and_duplicates():
     base = np.array([[0.0, 0.0], [4.0, 0.0], [0.0, 4.0]], np.float32)
     X = np.concatenate([base, base, base[:1]])      # duplicates: ties at equal distance
