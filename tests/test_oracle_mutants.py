@@ -7,9 +7,14 @@ suites (``test_oracle_pins.py``, ``test_oracle_mlp_pins.py``) are run against
 each mutant in a child process and must report a failed assertion.  Mutants
 are written to a temporary directory; the committed oracle is never touched.
 
-A mutant of the symmetry-breaking step that swaps the assignment direction is
-left out: the serial branch and bound then stops shrinking boxes and does not
-end, which is no assertion.
+Left out: a mutant of the symmetry-breaking step that swaps the assignment
+direction (the serial branch and bound then stops shrinking boxes and does not
+end, which is no assertion), and three that change no result: testing seed k
+against box k at 4 alpha instead of alpha (a box farther than alpha from its
+seed also fails the ball test, which the seed passes as a representative),
+selecting the open node with the largest bound instead of the smallest (the
+same optimum by another tree), and giving the open nodes of sample reduction
+no representatives (fewer deletions, the same optimum).
 """
 import concurrent.futures as cf
 import os
@@ -68,6 +73,10 @@ C_MUTANTS = {
                                           "if (sqdist(x, X + rp[q] * D, D) > 4.0 * alpha) excl = 1;")]),
     "sr_first_node_only": ("Alg. 5", [("for (int m = 0; m < n_nodes && redundant; ++m)",
                                        "for (int m = 0; m < 1 && redundant; ++m)")]),
+    "seed_in_wrong_cluster": ("Sec. 4.1.1", [("asg[seeds[k]] = (int8_t)k;",
+                                              "asg[seeds[k]] = (int8_t)((k + 1) % K);")]),
+    "seeds_at_alpha_not_4alpha": ("Sec. 4.1.1", [("> 4.0 * alpha)) { seeds_found = 0; break; }",
+                                                  "> alpha)) { seeds_found = 0; break; }")]),
 }
 
 # name -> (what, [(original, planted), ...]) in mlp.py
