@@ -75,3 +75,28 @@ def test_import_fails_loudly_without_the_library(tmp_path):
     r = subprocess.run([sys.executable, "-c", "import paper_2301_00061_gb300"], cwd=tmp_path,
                        capture_output=True, text=True, timeout=300)
     assert r.returncode != 0 and "ImportError" in r.stderr and "not built" in r.stderr, r.stderr[-2000:]
+
+
+def test_noalloc_rejects_bad_sizes_before_touching_cuda(kcpkg):
+    """kc_lower_bounds_noalloc validates sizes before any CUDA call: more nodes
+    than its fixed scratch holds, bad K / D / N / ld and NULL arrays return
+    KC_EINVAL (1), an empty batch returns KC_OK, all without a GPU.  (The
+    pointers are host buffers that the rejected calls never read.)"""
+    import numpy as np
+    lib = C.CDLL(kcpkg.library_path())
+    f = lib.kc_lower_bounds_noalloc
+    P, I64, I32 = C.c_void_p, C.c_int64, C.c_int32
+    f.restype = C.c_int
+    f.argtypes = [P, I64, I64, I32, I32, P, P, I32, P, P, P, P]
+    buf = np.zeros(64, np.float64)
+    p = buf.ctypes.data
+    ok = dict(X=p, N=10, ld=16, D=2, K=3, lo=p, hi=p, B=1, lb=p)
+
+    def call(**kw):
+        a = {**ok, **kw}
+        return f(a["X"], a["N"], a["ld"], a["D"], a["K"], a["lo"], a["hi"], a["B"], a["lb"], None, None, None)
+
+    for bad in (dict(B=4097), dict(B=-1), dict(K=0), dict(K=17), dict(D=0), dict(D=65), dict(N=-1),
+                dict(ld=9), dict(N=2 ** 32, ld=2 ** 32), dict(X=None), dict(lo=None), dict(hi=None), dict(lb=None)):
+        assert call(**bad) == 1, bad
+    assert call(B=0) == 0
