@@ -97,8 +97,10 @@ kc_status kc_root_box(kc_ctx *ctx, void *lo, void *hi);
  *   lo, hi     [B][K][D] of the data type, lo <= hi.
  *   lb_out     [B] double: a certified bound, never above the exact real value
  *              of beta(M); for float data it is the float evaluation deflated
- *              by its proved rounding-error bound (relative gap below 1e-6 for
- *              D <= 16), for double data the double evaluation deflated by a
+ *              by its proved rounding-error bound (relative gap at most
+ *              2 gamma_n, n = ceil(D/2) + 3, gamma_n = n u / (1 - n u),
+ *              u = 2^-24: below 1e-6 for D <= 10, 1.3e-6 at D = 16; in
+ *              practice far smaller), for double data the double evaluation deflated by a
  *              few units in the last place.
  *   lb_raw_out [B] double or NULL: the value as evaluated (float data: the
  *              float result; double data: bit-identical to a serial
