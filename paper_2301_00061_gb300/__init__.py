@@ -382,6 +382,8 @@ class KCenter:
         return lo, hi
 
     def lower_bounds(self, lo, hi):
+        """Certified lower bounds of B nodes (Section 3.1): boxes lo, hi of
+        shape (B, K, D) in the data type -> (lb, raw, argmax), each (B,)."""
         B = lo.shape[0]
         lb = self._alloc(lo, (B,), "f64")
         raw = self._alloc(lo, (B,), "f64")
@@ -390,6 +392,8 @@ class KCenter:
         return lb, raw, arg
 
     def upper_bound(self, centers):
+        """Objective (Eq. 1) of S center sets, centers (S, K) int64 sample
+        indices -> (value in double, the sample attaining it), each (S,)."""
         S = centers.shape[0]
         ub = self._alloc(centers, (S,), "f64")
         worst = self._alloc(centers, (S,), "i64")
@@ -397,12 +401,18 @@ class KCenter:
         return ub, worst
 
     def fft(self, start, like=None):
+        """Farthest first traversal (Algorithm 2) from sample `start` ->
+        (K center indices, their objective)."""
         c = self._alloc(like, (self.K,), "i64")
         obj = self._alloc(like, (1,), "f64")
         kc_fft(self.h, start, c, obj)
         return c, obj
 
     def tighten(self, lo, hi, alpha, seeds=None, ball_cap=0):
+        """Cluster assignment and bounds tightening of B nodes given the upper
+        bound alpha (Algorithms 3-4): tightened boxes, |S_+^k| counts,
+        candidates, the input boxes' certified bound and a status per node
+        (0 feasible, 1 infeasible, 2 leaf)."""
         B = lo.shape[0]
         lo_o = self._alloc(lo, tuple(lo.shape), "data")
         hi_o = self._alloc(lo, tuple(lo.shape), "data")
@@ -414,6 +424,8 @@ class KCenter:
         return {"lo": lo_o, "hi": hi_o, "count": counts, "cand": cand, "lb": lb, "status": status}
 
     def sample_reduction(self, lo, hi, beta_glob, alpha, active, reps=None):
+        """Algorithm 5 against M nodes: clears active[s] (uint8, updated in
+        place) for samples redundant in every node; returns (active, count)."""
         n_act = self._alloc(lo, (1,), "i64")
         kc_sample_reduction(self.h, lo, hi, beta_glob, alpha, active, reps, n_act)
         return active, int(n_act[0])
@@ -423,6 +435,13 @@ class KCenter:
         self._scorer = scorer
 
     def solve(self, tol=1e-12, **kw):
+        """Branch and bound to a certified optimum within relative gap `tol`
+        (Algorithm 1).  Keyword options are the fields of kc_solve_opts
+        (time_limit_s, node_limit, batch, ball_cap, i_sr, use_bt, order,
+        lists, verbose, explore, arena_mb, seed, log_path, rule_margin,
+        fft_starts, rule_width).  Returns the objective (double, over all
+        samples), certified lower bound, gap, centers, counters and the
+        status (0 optimal, 4 time limit, 5 node limit)."""
         o = kc_solve_defaults()
         o.tol = tol
         log = kw.pop("log_path", None)
