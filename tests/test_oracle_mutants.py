@@ -77,6 +77,14 @@ C_MUTANTS = {
                                               "asg[seeds[k]] = (int8_t)((k + 1) % K);")]),
     "seeds_at_alpha_not_4alpha": ("Sec. 4.1.1", [("> 4.0 * alpha)) { seeds_found = 0; break; }",
                                                   "> alpha)) { seeds_found = 0; break; }")]),
+    "float_lower_end_rounded_to_nearest": ("Sec. 4.1.2 under rounding",
+                                           [("if ((double)f > v) f = nextafterf(f, -INFINITY);", "")]),
+    "float_upper_end_rounded_to_nearest": ("Sec. 4.1.2 under rounding",
+                                           [("if ((double)f < v) f = nextafterf(f, INFINITY);", "")]),
+    "radius_rounded_to_nearest": ("Sec. 4.1.2 under rounding",
+                                  [("double r = nextafter(sqrt(alpha), INFINITY);", "double r = sqrt(alpha);")]),
+    "float_split_may_equal_upper_end": ("Sec. 3.3", [("if ((double)m >= hi) m = (float)lo;",
+                                                      "if ((double)m > hi) m = (float)lo;")]),
 }
 
 # name -> (what, [(original, planted), ...]) in mlp.py

@@ -410,3 +410,58 @@ def test_golden_split_point(ex):
     """Branching value (Section 3.3) and the upper child's lower end."""
     m, succ = oracle.split_point(ex["lo"], ex["hi"], ex["is_f32"])
     assert (m, succ) == (ex["m"], ex["succ"]), ex["derivation"]
+
+
+def _float32_neighbours(v):
+    f = np.float32(v)
+    return float(np.nextafter(f, np.float32(-np.inf))), float(np.nextafter(f, np.float32(np.inf)))
+
+
+def test_box_bt_float_bounds_round_outward():
+    """Box-based tightening with float data (Section 4.1.2 under rounding):
+    each bound of [max_j x_j - sqrt(alpha), min_j x_j + sqrt(alpha)] is the
+    float nearest to the real value on the outside.  Samples 0 and 10, boxes
+    [-5, 5] and [8, 12], alpha = 2: the real bounds -sqrt2, sqrt2, 10 - sqrt2,
+    10 + sqrt2 are irrational and far (in double terms) from every float, so
+    the oracle's bounds must be the largest float below, or the smallest
+    float above, the real value -- checked in exact arithmetic."""
+    from fractions import Fraction
+    X = np.array([[0.0], [10.0]])
+    r = oracle.tighten(X, np.array([[-5.0], [8.0]]), np.array([[5.0], [12.0]]), 2.0, is_f32=True)
+    for k, c in ((0, 0), (1, 10)):
+        lo_v, hi_v = r["box_bt_lo"][k][0], r["box_bt_hi"][k][0]
+        assert float(np.float32(lo_v)) == lo_v and float(np.float32(hi_v)) == hi_v
+        # lo_v <= c - sqrt2 < next float above lo_v
+        t = Fraction(c) - Fraction(lo_v)
+        assert t > 0 and t * t >= 2
+        t_next = Fraction(c) - Fraction(_float32_neighbours(lo_v)[1])
+        assert t_next < 0 or t_next * t_next < 2
+        # previous float below hi_v < c + sqrt2 <= hi_v
+        u = Fraction(hi_v) - Fraction(c)
+        assert u > 0 and u * u >= 2
+        u_prev = Fraction(_float32_neighbours(hi_v)[0]) - Fraction(c)
+        assert u_prev < 0 or u_prev * u_prev < 2
+
+
+def test_box_bt_bounds_contain_the_real_interval():
+    """Box-based tightening in double never cuts inside the real interval
+    [max_j x_j - sqrt(alpha), min_j x_j + sqrt(alpha)] (Section 4.1.2), for
+    random radii and sample values, checked in exact arithmetic; and it stays
+    within a few units in the last place of it."""
+    from fractions import Fraction
+    rng = np.random.default_rng(21)
+    for _ in range(400):
+        alpha = float(rng.uniform(0.01, 100.0))
+        xs = np.sort(rng.uniform(-3.0, 3.0, size=2))
+        X = np.array([[xs[0]], [xs[1]], [1e6]])
+        lo = np.array([[-1e3], [1e5]]); hi = np.array([[1e3], [1e7]])
+        r = oracle.tighten(X, lo, hi, alpha)
+        assert list(r["n_assigned"]) == [2, 1]
+        lv, hv = Fraction(r["box_bt_lo"][0][0]), Fraction(r["box_bt_hi"][0][0])
+        M, m = Fraction(float(xs[1])), Fraction(float(xs[0]))
+        a = Fraction(alpha)
+        assert M - lv > 0 and (M - lv) ** 2 >= a          # lo' <= max x - sqrt(alpha)
+        assert hv - m > 0 and (hv - m) ** 2 >= a          # hi' >= min x + sqrt(alpha)
+        rt = float(np.sqrt(alpha))
+        assert float(M - lv) - rt <= 8 * np.spacing(rt) + 4 * np.spacing(abs(float(M)) + 1.0)
+        assert float(hv - m) - rt <= 8 * np.spacing(rt) + 4 * np.spacing(abs(float(m)) + 1.0)
