@@ -85,6 +85,14 @@ C_MUTANTS = {
                                   [("double r = nextafter(sqrt(alpha), INFINITY);", "double r = sqrt(alpha);")]),
     "float_split_may_equal_upper_end": ("Sec. 3.3", [("if ((double)m >= hi) m = (float)lo;",
                                                       "if ((double)m > hi) m = (float)lo;")]),
+    "step_b_tightening_wrong_extreme": ("Alg. 4", [
+        ("double l2 = round_down_dt(nextafter(bmax2[i] - r, -INFINITY), is_f32);",
+         "double l2 = round_down_dt(nextafter(bmin2[i] - r, -INFINITY), is_f32);")]),
+    "step_b_tightening_skipped": ("Alg. 4", [("if (nb[k] > 0) {", "if (0) {")]),
+    "representatives_without_minima": ("Sec. 4.1.2", [("KCO_ADD_REP(amin_idx[a]);", "")]),
+    "candidate_tie_to_largest_index": ("Sec. 3.2", [
+        ("if (dm < cdist[k]) { cdist[k] = dm; out->cand[k] = s; }",
+         "if (dm <= cdist[k]) { cdist[k] = dm; out->cand[k] = s; }")]),
 }
 
 # name -> (what, [(original, planted), ...]) in mlp.py
