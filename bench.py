@@ -265,8 +265,9 @@ def main():
     # ---- roofline of the dominant kernel (the float lower-bound kernel)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     f_mhz = ck.get("sm_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
-    # FP32-pipe work per node x sample (see the design notes): per cluster and
-    # attribute two signed differences and one fused multiply-add
+    # FP32-pipe work per node x sample: per cluster and attribute one packed
+    # subtraction (two lanes: lo - x and x - hi) and half a packed fused
+    # multiply-add, 3 lane operations; peak = SMs x 128 FP32 lanes x SM clock
     ops_per_eval = 3 * w.k * w.d
     achieved = ops_per_eval * evals_per_step / (ms * 1e-3) / 1e12
     peak = sms * 128 * f_mhz * 1e6 / 1e12

@@ -18,8 +18,8 @@
  *   - `active` (nullable) is the sample-reduction mask: only samples with
  *     active[s] != 0 take part (Algorithm 5 deletes the others).
  *
- * Readings of the paper where it is silent or garbled are listed in the
- * design notes; each one used here is named in the comment where it applies.
+ * Where the paper is silent or garbled, the reading taken here is stated in
+ * the comment of the function that applies it.
  */
 #include <math.h>
 #include <stdint.h>

@@ -43,8 +43,10 @@ class Workload:
     outlier_frac: float = 0.0
 
 
-# The five workloads.  Items the paper leaves unstated (equal weights, sigma 1,
-# mean range, seeds for some) follow the recipe stated in the design notes.
+# The five workloads, shaped like the paper's (Gaussian clusters; N from 1e3
+# to 1e9).  What the paper leaves unstated is chosen here: equal weights
+# unless given, sigma 1 unless given, means uniform on [0, mean_hi]^D, and
+# a fixed seed per workload.
 WORKLOADS = {
     "small": Workload("small", 1_000, 2, 3, "f64", (1 / 3,) * 3, (1.0,) * 3, (1.0,) * 3, 10.0, 0),
     "lb_microbench": Workload("lb_microbench", 10_000_000, 8, 5, "f32", (0.2,) * 5,
