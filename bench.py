@@ -110,18 +110,19 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for r in self.rows:
-            if len(r) < 9:
-                continue
-            for i, nm in enumerate(names):
-                if r[5 + i].lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return summarize_clocks(self.rows)
+
+
+def summarize_clocks(rows):
+    """Median SM clock, the largest max clock and the throttle reasons seen in
+    nvidia-smi rows of ClockSampler.FIELDS (split on commas, no units)."""
+    full = [r for r in rows if len(r) >= 9]
+    sm = [float(r[1]) for r in full if r[1].replace(".", "", 1).isdigit()]
+    mx = [float(r[2]) for r in full if r[2].replace(".", "", 1).isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = {nm for r in full for i, nm in enumerate(names) if r[5 + i].lower() == "active"}
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def measured_peaks():

@@ -27,3 +27,21 @@ def test_other_ranks_of_the_reference_arm_exit_quietly():
                           "--warmup", "1", "--n", "20000"], capture_output=True, text=True, cwd=ROOT, env=env,
                          timeout=600)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_clock_summary_of_nvidia_smi_rows():
+    """The clocks record of the JSON line: median SM clock under load, the
+    largest max clock, and every throttle reason reported Active."""
+    import bench
+    rows = [
+        ["0", "2070", "2070", "850.1", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["0", "1980", "2070", "1390.5", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+        ["0", "2055", "2070", "1200.0", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["0", "[N/A]", "[N/A]", "[N/A]", "[N/A]", "[N/A]", "[N/A]", "[N/A]", "[N/A]"],
+        ["0", "2070"],                                   # a truncated line is ignored
+    ]
+    c = bench.summarize_clocks(rows)
+    assert c == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = rows[:1] + [["0", "1200", "2070", "1400", "0x40", "Not Active", "Active", "Not Active", "Not Active"]]
+    assert bench.summarize_clocks(hot)["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.summarize_clocks([])["sm_mhz"] is None
