@@ -125,6 +125,30 @@ def summarize_clocks(rows):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def lb_roofline(ms, n, d, k, b, sms, sm_mhz_sampled, sm_mhz_fallback, shape):
+    """Roofline record of the float lower-bound kernel for one launch of b
+    nodes over n samples taking ms milliseconds.
+
+    FP32-pipe work per node x sample: per cluster and attribute one packed
+    subtraction (two lanes: lo - x and x - hi) and half a packed fused
+    multiply-add, 3 lane operations; peak = SMs x 128 FP32 lanes x SM clock
+    (the median sampled during the timed region, else the fallback).  DRAM
+    traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+    an ncu capture of this kernel at N = 5e6, D = 8, K = 5 with 4 samples per
+    thread and 256 nodes per launch: reads scale with N, the per-CTA partials
+    do not; other shapes have no capture (None)."""
+    f_mhz = sm_mhz_sampled or sm_mhz_fallback
+    achieved = 3 * k * d * b * n / (ms * 1e-3) / 1e12
+    peak = sms * 128 * f_mhz * 1e6 / 1e12
+    traffic = None
+    if tuple(shape) == (4, 256) and b == 256 and d == 8 and k == 5:
+        traffic = 160_141_568 * (n / 5e6) + 3_646_720
+    basis = "median SM clock sampled" if sm_mhz_sampled else "no clock sample: fallback clock"
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_basis": f"FP32 pipe: {sms} SMs x 128 lanes x {f_mhz:.0f} MHz ({basis})",
+            "hbm_gbs": n * d * 4 / (ms * 1e-3) / 1e9}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -265,23 +289,8 @@ def main():
 
     # ---- roofline of the dominant kernel (the float lower-bound kernel)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    f_mhz = ck.get("sm_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
-    # FP32-pipe work per node x sample: per cluster and attribute one packed
-    # subtraction (two lanes: lo - x and x - hi) and half a packed fused
-    # multiply-add, 3 lane operations; peak = SMs x 128 FP32 lanes x SM clock
-    ops_per_eval = 3 * w.k * w.d
-    achieved = ops_per_eval * evals_per_step / (ms * 1e-3) / 1e12
-    peak = sms * 128 * f_mhz * 1e6 / 1e12
-    # DRAM traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum)
-    # from an ncu capture of this kernel at N = 5e6 with 4 samples per thread and
-    # 256 nodes per launch: reads scale with N, the per-CTA partials do not.
-    traffic = None
-    if (tuned_st, tuned_chunk) == (4, B_NODES) and w.d == 8 and w.k == 5:
-        traffic = 160_141_568 * (n / 5e6) + 3_646_720
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic,
-                "peak_basis": f"FP32 pipe: {sms} SMs x 128 lanes x {f_mhz:.0f} MHz (median SM clock sampled)",
-                "hbm_gbs": n * w.d * 4 / (ms * 1e-3) / 1e9}
+    roofline = lb_roofline(ms, n, w.d, w.k, B_NODES, sms, ck.get("sm_mhz"),
+                           measured_peaks().get("sm_max_mhz", 2070.0), (tuned_st, tuned_chunk))
 
     # ---- time to a certified optimum (kc_solve, tol 1e-12) on the
     # batched-solve recipe, data resident in HBM; every rank solves its own
