@@ -12,8 +12,8 @@ torchrun) runs one replica per GPU on its own batch with no collective on the
 data path ("scaling": "weak"); only the timing uses a barrier and a max over
 ranks.
 
-``--impl reference`` times the CPU oracle (plain C, FP64, one core) on a
-bounded sample of the same workload per step.
+``--impl reference`` times the CPU oracle (plain C, FP64, its bound loop over
+all host cores) on a bounded sample of the same workload per step.
 """
 from __future__ import annotations
 
@@ -47,8 +47,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--n", type=int, default=None, help="override N (testing only)")
-    p.add_argument("--solve-n", type=int, default=1_000_000,
+    p.add_argument("--solve-n", type=int, default=10_000_000,
                    help="N of the batched-solve workload timed to a certified optimum (0: skip)")
+    p.add_argument("--no-hbm-points", action="store_true")
     p.add_argument("--solve-time-limit", type=float, default=120.0)
     p.add_argument("--learned-n", type=int, default=100_000_000,
                    help="N of the learned-order workload solved with the scorer and with best bound (0: skip)")
@@ -125,28 +126,121 @@ def summarize_clocks(rows):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def lb_roofline(ms, n, d, k, b, sms, sm_mhz_sampled, sm_mhz_fallback, shape):
+def lb_roofline(ms, n, d, k, b, sms, sm_mhz_sampled, sm_mhz_fallback, shape, probe=None):
     """Roofline record of the float lower-bound kernel for one launch of b
     nodes over n samples taking ms milliseconds.
 
-    FP32-pipe work per node x sample: per cluster and attribute one packed
-    subtraction (two lanes: lo - x and x - hi) and half a packed fused
-    multiply-add, 3 lane operations; peak = SMs x 128 FP32 lanes x SM clock
-    (the median sampled during the timed region, else the fallback).  DRAM
-    traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-    an ncu capture of this kernel at N = 5e6, D = 8, K = 5 with 4 samples per
-    thread and 256 nodes per launch: reads scale with N, the per-CTA partials
-    do not; other shapes have no capture (None)."""
+    Work per node x sample, in FP32 lane operations: per cluster and
+    attribute the two differences lo - x and x - hi (one packed f32x2
+    subtraction, 2 lane operations), their maximum with 0 (one 3-input max,
+    1) and the fused multiply-add of the square (half a packed f32x2 FMA, 1);
+    then the K - 1 minima over clusters and the running maximum (K): 4KD + K.
+    peak = SMs x 128 FP32 lanes x SM clock (the median sampled during the
+    timed region, else the fallback): a derived ceiling.  `probe` (optional)
+    holds the measured lane-op rates of kc_fp32_probe; frac_of_probe compares
+    the kernel with the same instruction mix run without memory traffic.
+    DRAM traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from an ncu capture of this kernel at N = 5e6, D = 8, K = 5 with 4 samples
+    per thread and 256 nodes per launch: reads scale with N, the per-CTA
+    partials do not; other shapes have no capture (None)."""
     f_mhz = sm_mhz_sampled or sm_mhz_fallback
-    achieved = 3 * k * d * b * n / (ms * 1e-3) / 1e12
+    ops = 4 * k * d + k
+    evals = b * n / (ms * 1e-3)
+    achieved = ops * evals / 1e12
     peak = sms * 128 * f_mhz * 1e6 / 1e12
     traffic = None
     if tuple(shape) == (4, 256) and b == 256 and d == 8 and k == 5:
         traffic = 160_141_568 * (n / 5e6) + 3_646_720
     basis = "median SM clock sampled" if sm_mhz_sampled else "no clock sample: fallback clock"
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_basis": f"FP32 pipe: {sms} SMs x 128 lanes x {f_mhz:.0f} MHz ({basis})",
-            "hbm_gbs": n * d * 4 / (ms * 1e-3) / 1e9}
+    rec = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": traffic, "ops_per_eval": ops, "ops_count": "FP32 lane operations, 4KD+K per node x sample",
+           "peak_basis": f"derived: FP32 pipe, {sms} SMs x 128 lanes x {f_mhz:.0f} MHz ({basis})",
+           "issue_count": {"instr_per_eval": 2.5 * k * d + k,
+                           "note": "thread instructions: per (k, a) one packed subtraction, one 3-input max and "
+                                   "half a packed FMA; one min per k"},
+           "hbm_gbs": n * d * 4 / (ms * 1e-3) / 1e9}
+    if probe:
+        rec["probe"] = probe
+        mix = probe.get("lb_mix_tops")
+        if mix:
+            rec["frac_of_probe"] = achieved / mix
+    return rec
+
+
+def fp32_probe(kcm, stream):
+    """Measured FP32 lane-op rates (T/s) of the three probe mixes."""
+    out = {}
+    for mode, name in ((0, "fma2_tops"), (1, "max3_tops"), (2, "lb_mix_tops")):
+        r, _ = kcm.kc_fp32_probe(mode, stream)
+        out[name] = r / 1e12
+    return out
+
+
+def time_events(fn, iters, stream, torch):
+    """Average device time (ms) of fn() over iters calls, CUDA events on stream."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(iters):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / iters
+
+
+def hbm_points(kcm, torch, dev, stream, h, lod, hid, n, d, hbm_peak, rank):
+    """Where the HBM ceiling binds: the bound of ONE node (B = 1) over the
+    lower-bound microbenchmark data (4D bytes per sample, 4KD+K lane ops:
+    near the ridge), and the per-node-list gather kernel with one node over
+    the batched-solve recipe (N = 1e7, D = 4): the root list (every sample,
+    ids in order) and a sorted 25 % subset (4 + 4D bytes per entry)."""
+    pts = []
+    lb1 = torch.empty(1, dtype=torch.float64, device=dev)
+    lo1, hi1 = lod[:1].contiguous(), hid[:1].contiguous()
+    for _ in range(5):
+        kcm.kc_lower_bounds(h, lo1, hi1, lb1)
+    ms = time_events(lambda: kcm.kc_lower_bounds(h, lo1, hi1, lb1), 200, stream, torch)
+    gbs = n * d * 4 / (ms * 1e-3) / 1e9
+    pts.append({"kernel": "lb_f32_fast (+ finalize)", "workload": f"lb_microbench N={n:,} D={d}, one node",
+                "bytes_per_launch": n * d * 4, "ms": ms, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                "frac": gbs / hbm_peak, "timed": "kc_lower_bounds call, CUDA events, 200 launches"})
+    Xs, ws = synth.make_workload("batched_solve", n=10_000_000, seed=2 + rank)
+    kc = kcm.KCenter(torch.from_numpy(Xs).to(dev), ws.k)
+    rng = np.random.default_rng(5)
+    c = rng.integers(0, Xs.shape[0], size=ws.k)
+    lo = (Xs[c] - 0.5)[None].astype(np.float32)
+    hi = (Xs[c] + 0.5)[None].astype(np.float32)
+    lo_t, hi_t = torch.from_numpy(lo).to(dev), torch.from_numpy(hi).to(dev)
+    lb = torch.empty(1, dtype=torch.float64, device=dev)
+    for name, ids in (("root list (all samples in order)", np.arange(Xs.shape[0], dtype=np.uint32)),
+                      ("sorted 25 % subset", np.sort(rng.choice(Xs.shape[0], Xs.shape[0] // 4,
+                                                                replace=False)).astype(np.uint32))):
+        ids_t = torch.from_numpy(ids.view(np.int32)).to(dev)
+        for _ in range(3):
+            kcm.kc_lower_bounds_subset(kc.h, ids_t, lo_t, hi_t, lb)
+        kms = [kcm.kc_lower_bounds_subset(kc.h, ids_t, lo_t, hi_t, lb, want_kernel_ms=True) for _ in range(30)]
+        ms = float(np.median(kms))
+        byts = len(ids) * (4 + 4 * ws.d)
+        gbs = byts / (ms * 1e-3) / 1e9
+        pts.append({"kernel": "seg_lb_f32 (+ key reset, finalize)",
+                    "workload": f"batched_solve N={Xs.shape[0]:,} D={ws.d} K={ws.k}, one node, {name}",
+                    "bytes_per_launch": byts, "ms": ms, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                    "frac": gbs / hbm_peak, "timed": "kernel_ms of kc_lower_bounds_subset, median of 30"})
+        del ids_t
+    kc.close()
+    return pts
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def measured_peaks():
@@ -167,29 +261,45 @@ def cpu_oracle_rate(X, lo, hi, n_sample):
     return lo.shape[0] * n_sample / dt, dt
 
 
+def cpu_oracle_rate_all_cores(X, lo, hi, n_sample):
+    """The same oracle bound loop over all host cores (OpenMP, same results):
+    (evals/s, seconds, threads used)."""
+    import oracle
+    Xs = np.ascontiguousarray(X[:n_sample], dtype=np.float64)
+    oracle.lower_bounds_par(Xs[:1000], lo[:2], hi[:2])
+    t = time.perf_counter()
+    _, _, nt = oracle.lower_bounds_par(Xs, lo, hi)
+    dt = time.perf_counter() - t
+    return lo.shape[0] * n_sample / dt, dt, nt
+
+
 def run_reference(args, ws, rank):
-    """The CPU oracle as the reference arm, rank 0 only."""
+    """The CPU oracle as the reference arm, rank 0 only: its bound loop over
+    all host cores (OpenMP; the same values as the serial loop) on a bounded
+    sample of the workload per step."""
     if rank != 0:
         return
     X, w = synth.make_workload(WORKLOAD, n=args.n)
     lo, hi = synth.nested_boxes(X, w.k, B_NODES, seed=1)
-    n_sample = 16_384
+    n_sample = min(131_072, X.shape[0])
     for _ in range(args.warmup):
-        cpu_oracle_rate(X, lo, hi, 2048)
+        cpu_oracle_rate_all_cores(X, lo, hi, 4096)
     t = time.perf_counter()
     evals = 0
+    nt = 1
     for _ in range(args.steps):
-        r, dt = cpu_oracle_rate(X, lo, hi, n_sample)
+        r, dt, nt = cpu_oracle_rate_all_cores(X, lo, hi, n_sample)
         evals += B_NODES * n_sample
     el = time.perf_counter() - t
     v = evals / el
-    sample = f"{B_NODES} nested nodes x first {n_sample} samples per step (FP64 oracle, one core)"
+    sample = (f"{B_NODES} nested nodes x first {n_sample} samples per step (FP64 oracle, OpenMP over {nt} "
+              f"threads, {cpu_model()})")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict(X.shape[0], w),
-        "cpu_baseline": {"value": v, "unit": "evals/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "evals/s", "cores": nt, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -287,10 +397,14 @@ def main():
            "d2h_bytes_per_step": int(lbh.numel() * 8 + argh.numel() * 8),
            "includes": "kc_create upload of X from pinned host memory, boxes host->device, results device->host"}
 
-    # ---- roofline of the dominant kernel (the float lower-bound kernel)
+    # ---- roofline of the dominant kernel (the float lower-bound kernel),
+    # beside the measured FP32 throughput of its instruction mix (untimed)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    probe = fp32_probe(kcm, stream.cuda_stream)
     roofline = lb_roofline(ms, n, w.d, w.k, B_NODES, sms, ck.get("sm_mhz"),
-                           measured_peaks().get("sm_max_mhz", 2070.0), (tuned_st, tuned_chunk))
+                           measured_peaks().get("sm_max_mhz", 2070.0), (tuned_st, tuned_chunk), probe)
+    hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
+    hbm = None if args.no_hbm_points else hbm_points(kcm, torch, dev, stream, h, lod, hid, n, w.d, hbm_peak, rank)
 
     # ---- time to a certified optimum (kc_solve, tol 1e-12) on the
     # batched-solve recipe, data resident in HBM; every rank solves its own
@@ -306,7 +420,9 @@ def main():
         torch.cuda.synchronize()
         secs = r["seconds"]
         secs = max_over_ranks(secs, ws)
-        solve = {"workload": f"batched_solve: N={args.solve_n:,} D={ws_.d} K={ws_.k} float32, weights .6/.3/.1",
+        solve = {"workload": f"batched_solve: N={args.solve_n:,} D={ws_.d} K={ws_.k} float32, weights .6/.3/.1, "
+                             f"seed {2 + rank}",
+                 "time_limit_s": args.solve_time_limit,
                  "metric": "time to certified optimum (tol 1e-12)", "seconds": secs,
                  "certified": r["status"] == 0, "objective": r["objective"], "lower_bound": r["lower_bound"],
                  "gap": r["gap"], "nodes": int(r["nodes"]), "batches": int(r["batches"]),
@@ -345,14 +461,23 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
         "clocks": ck, "e2e": e2e, "gpu_launches": int(launches) * ws, "roofline": roofline,
     }
+    if hbm is not None:
+        line["hbm_points"] = hbm
     if solve is not None:
         line["solve"] = solve
     if learned is not None:
         line["learned_order"] = learned
     if rank == 0 and not args.no_cpu_baseline:
+        model = cpu_model()
+        rate_p, dt_p, nt = cpu_oracle_rate_all_cores(X, lo, hi, 2_000_000)
+        line["cpu_baseline"] = {"value": rate_p, "unit": "evals/s", "cores": nt, "kind": "oracle",
+                                "cpu": model,
+                                "sample": f"{B_NODES} nested nodes x first 2,000,000 samples ({dt_p:.1f} s, FP64, "
+                                          f"OpenMP over {nt} threads)"}
         rate, dt = cpu_oracle_rate(X, lo, hi, 200_000)
-        line["cpu_baseline"] = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{B_NODES} nested nodes x first 200,000 samples ({dt:.1f} s, FP64, one core)"}
+        line["cpu_baseline_1core"] = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle", "cpu": model,
+                                      "sample": f"{B_NODES} nested nodes x first 200,000 samples ({dt:.1f} s, FP64, "
+                                                "one core)"}
     kcm.kc_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)

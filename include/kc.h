@@ -127,15 +127,23 @@ kc_status kc_lower_bounds(kc_ctx *ctx, const void *lo, const void *hi, int32_t B
  *   lb_out, lb_raw_out, argmax_out  device, as in kc_lower_bounds (the last
  *              two may be NULL).
  *   stream     cudaStream_t the work is ordered on.
+ * Every non-NULL array must be device (or managed) memory of the current
+ * GPU; anything else -- a host array in particular -- returns KC_EINVAL
+ * before any launch (checked with cudaPointerGetAttributes, which allocates
+ * nothing).  If a CUDA error is already pending in the calling thread the
+ * call returns KC_ECUDA at once, launches nothing and leaves that error in
+ * place for its owner.
  * Scratch is one fixed array in the library (512 partial results for each of
  * 256 nodes, 1 MiB, kept by every GPU that loads the library until the
  * process exits); nodes are processed 256 at a time and B may be at most
  * 4096 (larger B returns KC_EINVAL).  The first call on a device looks up the
- * array's device address with that device current; make that first call
- * before any stream capture.  Every call reuses the same array, so calls
- * that can overlap on the GPU (different streams, no ordering between them)
- * race and must not be issued.  Returns KC_EINVAL for bad sizes, KC_ECUDA if a
- * CUDA call fails.  Nothing is written to an error string.
+ * array's device address with that device current and keeps it for the
+ * process; make that first call before any stream capture, and do not call
+ * the entry point on a device after cudaDeviceReset (the kept address would
+ * be stale).  Every call reuses the same array, so calls that can overlap on
+ * the GPU (different streams, no ordering between them) race and must not be
+ * issued.  Returns KC_EINVAL for bad sizes or pointers, KC_ECUDA if a CUDA
+ * call fails.  Nothing is written to an error string.
  */
 kc_status kc_lower_bounds_noalloc(const float *X, int64_t N, int64_t ld, int32_t D, int32_t K,
                                   const float *lo, const float *hi, int32_t B, double *lb_out,
@@ -176,6 +184,60 @@ kc_status kc_upper_bound(kc_ctx *ctx, const int64_t *centers, int32_t S, double 
  * objective (Eq. 1) of the chosen set, or NULL.
  */
 kc_status kc_fft(kc_ctx *ctx, int64_t start, int64_t *centers_out, double *obj_out);
+
+/*
+ * kc_fft_multi -- Algorithm 2 from S start samples at once (the paper's
+ * heuristic baseline runs FFT from many random starts and keeps the best,
+ * Section 6): set s starts at starts[s] and repeatedly adds the sample
+ * farthest (in double precision, smallest index on ties) from its chosen
+ * points until K are chosen.  Each of the K - 1 passes over the samples
+ * serves all S sets.  Every set equals what kc_fft returns for its start.
+ *   starts       [S] int64 sample indices in [0, N); 0 <= S <= 65536.
+ *   centers_out  [S][K] int64.
+ *   obj_out      [S] double objective (Eq. 1) of each set, or NULL.
+ */
+kc_status kc_fft_multi(kc_ctx *ctx, const int64_t *starts, int32_t S, int64_t *centers_out, double *obj_out);
+
+/*
+ * kc_lower_bounds_subset -- the closed-form lower bound of kc_lower_bounds
+ * (Section 3.1, Eqs. 9-11) of B nodes over a subset of the samples given by
+ * their indices (the reduced data set that sample reduction leaves,
+ * Section 4.2): beta(M) = max over s in ids of min_k beta_s^k.  Each
+ * sample's coordinates are gathered by index; all B nodes share each
+ * gathered tile.
+ *   ids        [n] uint32 sample indices (any order, repeats allowed); every
+ *              index must be < N (checked with one pass over the ids:
+ *              KC_EINVAL otherwise).  n = 0 gives bound 0 and argmax -1.
+ *   lo, hi     [B][K][D] float boxes, 0 <= B <= 4096.
+ *   lb_out, lb_raw_out, argmax_out  as in kc_lower_bounds (the argmax is a
+ *              sample index, smallest on ties).
+ *   kernel_ms_out  host float or NULL: the device time of the bound launch
+ *              (key reset, the gather-and-bound kernel and its finalize),
+ *              measured with CUDA events on the context's stream; the call
+ *              then waits for it.
+ * Float data with D <= 8 only (KC_EINVAL otherwise).
+ */
+kc_status kc_lower_bounds_subset(kc_ctx *ctx, const uint32_t *ids, int64_t n, const void *lo, const void *hi,
+                                 int32_t B, double *lb_out, double *lb_raw_out, int64_t *argmax_out,
+                                 float *kernel_ms_out);
+
+/*
+ * kc_fp32_probe -- measures the FP32 arithmetic throughput of the current GPU
+ * that bounds the float lower-bound kernel (a measurement aid; the paper has
+ * no counterpart).  Every thread of a full-GPU launch runs independent chains
+ * of one instruction mix with no memory traffic; the fastest of five timed
+ * launches (CUDA events on `stream`) is reported as FP32 lane operations per
+ * second, counting a packed f32x2 subtraction or fused multiply-add as two
+ * lane operations and a 3-input max.f32 as one.
+ *   mode  0: packed fused multiply-adds (fma.rn.f32x2) only;
+ *         1: 3-input maxima (max.f32) only;
+ *         2: the bound kernel's clamp-distance term: per two attributes two
+ *            packed subtractions, two 3-input maxima and one packed fused
+ *            multiply-add (4 lane operations per attribute).
+ *   lane_ops_per_s  receives the rate; ms_out (or NULL) the launch time.
+ * Allocates and frees a small device buffer.
+ */
+kc_status kc_fp32_probe(int32_t mode, void *stream, double *lane_ops_per_s, float *ms_out);
 
 /*
  * kc_tighten -- cluster assignment and bounds tightening of B nodes given an

@@ -27,7 +27,7 @@ _lib = None
 MAXK, MAXD, MAXREPS = 16, 64, 50
 
 
-GCC_FLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+GCC_FLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-fopenmp"]
 
 
 def build(force=False):
@@ -107,6 +107,7 @@ def lib():
                 "kco_root_box": (_I32, [_P, _I64, _I32, _P, _P]),
                 "kco_lower_bound": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P]),
                 "kco_lower_bounds": (_I32, [_P, _I64, _I32, _I32, _P, _P, _I32, _P, _P, _P]),
+                "kco_lower_bounds_par": (_I32, [_P, _I64, _I32, _I32, _P, _P, _I32, _P, _P]),
                 "kco_beta_matrix": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
                 "kco_alpha_s": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
                 "kco_objective": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P]),
@@ -171,6 +172,19 @@ def lower_bounds(X, lo, hi, active=None):
     m = _mask(active)
     lib().kco_lower_bounds(_ptr(X), n, d, k, _ptr(lo), _ptr(hi), B, _ptr(m), _ptr(beta), _ptr(arg))
     return beta, arg
+
+
+def lower_bounds_par(X, lo, hi):
+    """lower_bounds (no mask) over all host cores (OpenMP); equal to the
+    serial result.  Returns (beta, argmax, threads used)."""
+    X, lo, hi = _f64(X), _f64(lo), _f64(hi)
+    n, d = X.shape
+    B, k, _ = lo.shape
+    beta = np.empty(B); arg = np.empty(B, dtype=np.int64)
+    nt = lib().kco_lower_bounds_par(_ptr(X), n, d, k, _ptr(lo), _ptr(hi), B, _ptr(beta), _ptr(arg))
+    if nt < 0:
+        raise MemoryError("lower_bounds_par: allocation failed")
+    return beta, arg, nt
 
 
 def beta_matrix(X, lo, hi):

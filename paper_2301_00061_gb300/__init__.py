@@ -22,7 +22,8 @@ from . import build as _build
 __all__ = [
     "KCError", "KC_F32", "KC_F64", "KC_ROW_MAJOR", "KC_COL_MAJOR", "SolveOpts", "Result",
     "kc_create", "kc_destroy", "kc_last_error", "kc_set_stream", "kc_launch_count", "kc_root_box",
-    "kc_lower_bounds", "kc_lower_bounds_noalloc", "kc_autotune", "kc_upper_bound", "kc_fft", "kc_tighten", "kc_sample_reduction",
+    "kc_lower_bounds", "kc_lower_bounds_noalloc", "kc_autotune", "kc_upper_bound", "kc_fft", "kc_fft_multi",
+    "kc_lower_bounds_subset", "kc_fp32_probe", "kc_tighten", "kc_sample_reduction",
     "kc_solve_defaults", "kc_solve", "KCenter", "library_path", "kc_mlp_create", "kc_mlp_destroy",
     "kc_mlp_get_params", "kc_mlp_forward", "kc_mlp_grad", "kc_mlp_train", "kc_set_scorer", "Scorer",
 ]
@@ -85,6 +86,9 @@ def _load():
         "kc_autotune": (I32, [P, P, P, I32, P, P, P]),
         "kc_upper_bound": (I32, [P, P, I32, P, P]),
         "kc_fft": (I32, [P, I64, P, P]),
+        "kc_fft_multi": (I32, [P, P, I32, P, P]),
+        "kc_lower_bounds_subset": (I32, [P, P, I64, P, P, I32, P, P, P, P]),
+        "kc_fp32_probe": (I32, [I32, P, P, P]),
         "kc_tighten": (I32, [P, P, P, I32, D, P, I32, P, P, P, P, P, P]),
         "kc_sample_reduction": (I32, [P, P, P, I32, P, I32, D, D, P, P]),
         "kc_solve_defaults": (None, [C.POINTER(SolveOpts)]),
@@ -201,8 +205,30 @@ def kc_autotune(h, lo, hi):
 
 
 def kc_lower_bounds_noalloc(X, N, ld, D, K, lo, hi, lb, lb_raw=None, argmax=None, stream=None):
-    """X: device float32 tensor holding X[a*ld + s]; lo, hi (B, K, D) device."""
+    """X: CUDA float32 tensor holding X[a*ld + s] (at least D*ld values);
+    lo, hi: CUDA float32 (B, K, D); lb, lb_raw: CUDA float64 with at least B
+    values, argmax: CUDA int64 with at least B values (the last two may be
+    None).  Every array must be a CUDA tensor: the entry point only takes
+    device memory."""
+    def cuda_tensor(t, name, dtype_name, min_numel):
+        if not (_is_torch(t) and t.is_cuda):
+            raise TypeError(f"kc_lower_bounds_noalloc: {name} must be a CUDA tensor")
+        if not str(t.dtype).endswith(dtype_name):
+            raise TypeError(f"kc_lower_bounds_noalloc: {name} must be {dtype_name}, got {t.dtype}")
+        if t.numel() < min_numel:
+            raise ValueError(f"kc_lower_bounds_noalloc: {name} holds {t.numel()} values, needs {min_numel}")
+
+    if lo.ndim != 3 or tuple(hi.shape) != tuple(lo.shape) or lo.shape[1] != int(K) or lo.shape[2] != int(D):
+        raise ValueError(f"kc_lower_bounds_noalloc: lo, hi must have shape (B, {int(K)}, {int(D)})")
     B = lo.shape[0]
+    cuda_tensor(X, "X", "float32", int(D) * int(ld))
+    cuda_tensor(lo, "lo", "float32", 0)
+    cuda_tensor(hi, "hi", "float32", 0)
+    cuda_tensor(lb, "lb", "float64", B)
+    if lb_raw is not None:
+        cuda_tensor(lb_raw, "lb_raw", "float64", B)
+    if argmax is not None:
+        cuda_tensor(argmax, "argmax", "int64", B)
     st = _lib.kc_lower_bounds_noalloc(_ptr(X), int(N), int(ld), int(D), int(K), _ptr(lo), _ptr(hi), B, _ptr(lb),
                                       _ptr(lb_raw), _ptr(argmax), _stream_ptr(stream))
     if st != 0:
@@ -215,6 +241,34 @@ def kc_upper_bound(h, centers, ub, worst=None):
 
 def kc_fft(h, start, centers, obj=None):
     _check(h, _lib.kc_fft(h, int(start), _ptr(centers), _ptr(obj)))
+
+
+def kc_fft_multi(h, starts, centers, obj=None):
+    """starts (S,) int64 -> centers (S, K) int64, obj (S,) float64 or None."""
+    _check(h, _lib.kc_fft_multi(h, _ptr(starts), starts.shape[0], _ptr(centers), _ptr(obj)))
+
+
+def kc_lower_bounds_subset(h, ids, lo, hi, lb, lb_raw=None, argmax=None, want_kernel_ms=False):
+    """ids (n,) uint32 (or int32 holding indices < 2^31); returns the bound
+    launch's device time in ms when want_kernel_ms, else None."""
+    if not (str(ids.dtype).endswith("uint32") or str(ids.dtype).endswith("int32")):
+        raise TypeError(f"ids must be uint32, got {ids.dtype}")
+    ms = C.c_float(-1.0)
+    _check(h, _lib.kc_lower_bounds_subset(h, _ptr(ids), int(ids.shape[0]), _ptr(lo), _ptr(hi), lo.shape[0],
+                                          _ptr(lb), _ptr(lb_raw), _ptr(argmax),
+                                          C.byref(ms) if want_kernel_ms else None))
+    return ms.value if want_kernel_ms else None
+
+
+def kc_fp32_probe(mode, stream=None):
+    """FP32 lane operations per second of the current GPU for one
+    instruction mix (0 packed FMA, 1 three-input max, 2 the bound kernel's
+    clamp-distance term); returns (rate, ms)."""
+    r, ms = C.c_double(), C.c_float()
+    st = _lib.kc_fp32_probe(int(mode), _stream_ptr(stream), C.byref(r), C.byref(ms))
+    if st != 0:
+        raise KCError(st, "kc_fp32_probe failed")
+    return r.value, ms.value
 
 
 def kc_tighten(h, lo, hi, alpha, seeds=None, ball_cap=0, lo_out=None, hi_out=None, counts=None,
@@ -407,6 +461,25 @@ class KCenter:
         obj = self._alloc(like, (1,), "f64")
         kc_fft(self.h, start, c, obj)
         return c, obj
+
+    def fft_multi(self, starts):
+        """Farthest first traversal from every start of `starts` (S,) int64
+        at once -> (centers (S, K), objectives (S,))."""
+        S = starts.shape[0]
+        c = self._alloc(starts, (S, self.K), "i64")
+        obj = self._alloc(starts, (S,), "f64")
+        kc_fft_multi(self.h, starts, c, obj)
+        return c, obj
+
+    def lower_bounds_subset(self, ids, lo, hi):
+        """Lower bounds of B nodes over the samples named by `ids` (uint32)
+        -> (lb, raw, argmax), each (B,)."""
+        B = lo.shape[0]
+        lb = self._alloc(lo, (B,), "f64")
+        raw = self._alloc(lo, (B,), "f64")
+        arg = self._alloc(lo, (B,), "i64")
+        kc_lower_bounds_subset(self.h, ids, lo, hi, lb, raw, arg)
+        return lb, raw, arg
 
     def tighten(self, lo, hi, alpha, seeds=None, ball_cap=0):
         """Cluster assignment and bounds tightening of B nodes given the upper

@@ -340,3 +340,158 @@ kc_status kc_fft(kc_ctx *c, int64_t start, int64_t *centers_out, double *obj_out
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Farthest first traversal from S starts at once, and lower bounds over a
+// caller-given subset of the samples.
+
+namespace kc {
+namespace {
+
+// centers [S][K] with the first t filled -> packed [S][t]
+__global__ void fft_pack_kernel(const int64_t *__restrict__ C, int S, int K, int t, int64_t *__restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S * t; i += gridDim.x * blockDim.x)
+        out[i] = C[(size_t)(i / t) * K + (i % t)];
+}
+
+// centers[s][t] = arg[s]; t = 0 seeds the sets with the starts
+__global__ void fft_put_kernel(int64_t *__restrict__ C, int S, int K, int t, const int64_t *__restrict__ arg)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x)
+        C[(size_t)s * K + t] = arg[s];
+}
+
+// largest id of a list (ordered max into *out, which starts at 0)
+__global__ void max_id_kernel(const uint32_t *__restrict__ ids, int64_t n, unsigned *__restrict__ out)
+{
+    unsigned m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = ids[i] > m ? ids[i] : m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned w = __shfl_xor_sync(0xffffffffu, m, o);
+        m = w > m ? w : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+}  // namespace
+}  // namespace kc
+
+extern "C" {
+
+kc_status kc_fft_multi(kc_ctx *c, const int64_t *starts, int32_t S, int64_t *centers_out, double *obj_out)
+{
+    if (!c) return KC_EINVAL;
+    if (S < 0 || S > 65536) return set_err(c, KC_EINVAL, "kc_fft_multi: S=%d outside [0, 65536]", S);
+    if (S == 0) return KC_OK;
+    if (!starts || !centers_out) return set_err(c, KC_EINVAL, "kc_fft_multi: NULL argument");
+    KC_TRY(check_centers(c, starts, (size_t)S));
+    const int K = c->K;
+    Stager sg(c);
+    const int is = sg.add(starts, (size_t)S * 8, true);
+    const int ic = sg.add(centers_out, (size_t)S * K * 8, false);
+    const int io = sg.add(obj_out, (size_t)S * 8, false);
+    KC_TRY(sg.begin());
+    const size_t packed = (size_t)S * K * 8, argb = (size_t)S * 8;
+    KC_TRY(ensure(c, c->work, packed + argb + (size_t)S * 8 + 512));
+    char *w = static_cast<char *>(c->work.p);
+    int64_t *T = reinterpret_cast<int64_t *>(w);
+    int64_t *arg = reinterpret_cast<int64_t *>(w + ((packed + 255) & ~(size_t)255));
+    double *val = reinterpret_cast<double *>(w + ((packed + 255) & ~(size_t)255) + ((argb + 255) & ~(size_t)255));
+    int64_t *C = static_cast<int64_t *>(sg.dev(ic));
+    const int grid = std::max(1, std::min(c->num_sms * 4, (S * K + 255) / 256));
+    fft_put_kernel<<<grid, 256, 0, c->stream>>>(C, S, K, 0, static_cast<const int64_t *>(sg.dev(is)));
+    KC_TRY(after_launch(c, "fft start"));
+    // Algorithm 2 for every start at once: the t-th point of set s is the
+    // sample farthest from its first t points (one pass over the samples
+    // serves all S sets)
+    for (int t = 1; t < K; ++t) {
+        fft_pack_kernel<<<grid, 256, 0, c->stream>>>(C, S, K, t, T);
+        KC_TRY(after_launch(c, "fft pack"));
+        KC_TRY(launch_objective(c, full_view(c), T, S, t, __builtin_huge_val(), val, arg));
+        fft_put_kernel<<<grid, 256, 0, c->stream>>>(C, S, K, t, arg);
+        KC_TRY(after_launch(c, "fft put"));
+    }
+    if (obj_out)
+        KC_TRY(launch_objective(c, full_view(c), C, S, K, __builtin_huge_val(), static_cast<double *>(sg.dev(io)),
+                                nullptr));
+    return sg.finish();
+}
+
+kc_status kc_lower_bounds_subset(kc_ctx *c, const uint32_t *ids, int64_t n, const void *lo, const void *hi, int32_t B,
+                                 double *lb_out, double *lb_raw_out, int64_t *argmax_out, float *kernel_ms_out)
+{
+    if (!c) return KC_EINVAL;
+    if (B < 0 || B > 4096) return set_err(c, KC_EINVAL, "kc_lower_bounds_subset: B=%d outside [0, 4096]", B);
+    if (n < 0 || n > c->N) return set_err(c, KC_EINVAL, "kc_lower_bounds_subset: n=%lld outside [0, N]", (long long)n);
+    if (c->dt != KC_F32) return set_err(c, KC_EINVAL, "kc_lower_bounds_subset: float data only");
+    if (c->D > 8) return set_err(c, KC_EINVAL, "kc_lower_bounds_subset: D <= 8 (got %d)", c->D);
+    if (B == 0) return KC_OK;
+    if (!lo || !hi || !lb_out || (n > 0 && !ids)) return set_err(c, KC_EINVAL, "kc_lower_bounds_subset: NULL argument");
+    const size_t box = (size_t)B * c->K * c->D * c->esize;
+    Stager sg(c);
+    const int iid = sg.add(n > 0 ? ids : nullptr, (size_t)n * 4, true);
+    const int ilo = sg.add(lo, box, true), ihi = sg.add(hi, box, true);
+    const int ilb = sg.add(lb_out, (size_t)B * 8, false);
+    const int iraw = sg.add(lb_raw_out, (size_t)B * 8, false);
+    const int iarg = sg.add(argmax_out, (size_t)B * 8, false);
+    KC_TRY(sg.begin());
+    const uint32_t *dids = static_cast<const uint32_t *>(sg.dev(iid));
+    // the batch descriptor: one group (every node shares the subset), then
+    // scratch for the per-node keys and the id check
+    const int LT = list_tile();
+    const size_t desc = 512, keys_off = desc, chk_off = keys_off + (((size_t)B * 8 + 255) & ~(size_t)255);
+    KC_TRY(ensure(c, c->work, chk_off + 256));
+    char *w = static_cast<char *>(c->work.p);
+    unsigned *dmax = reinterpret_cast<unsigned *>(w + chk_off);
+    if (n > 0) {
+        // every id must name a sample: one pass over the ids, checked on the host
+        KC_CUDA(c, cudaMemsetAsync(dmax, 0, 4, c->stream));
+        max_id_kernel<<<std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8)), 256, 0,
+                        c->stream>>>(dids, n, dmax);
+        KC_TRY(after_launch(c, "subset id check"));
+        unsigned hmax = 0;
+        KC_CUDA(c, cudaMemcpyAsync(&hmax, dmax, 4, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaStreamSynchronize(c->stream));
+        if ((int64_t)hmax >= c->N)
+            return set_err(c, KC_EINVAL, "kc_lower_bounds_subset: id %u outside [0, N)", hmax);
+    }
+    int64_t hd[7] = {0, n, 0, (n + LT - 1) / LT, 0, 0, 0};   // seg_off, seg_n, tile_prefix[2], node_start[2]
+    int *ns = reinterpret_cast<int *>(&hd[4]);
+    ns[0] = 0;
+    ns[1] = B;
+    KC_CUDA(c, cudaMemcpyAsync(w, hd, sizeof(hd), cudaMemcpyHostToDevice, c->stream));
+    const int64_t *dd = reinterpret_cast<const int64_t *>(w);
+    ListBatch L;
+    L.pool = dids;
+    L.seg_off = dd;
+    L.seg_n = dd + 1;
+    L.tile_prefix = dd + 2;
+    L.node_start = reinterpret_cast<const int *>(dd + 4);
+    L.B = 1;
+    L.W = hd[3];
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (kernel_ms_out) {
+        KC_CUDA(c, cudaEventCreate(&e0));
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            return set_err(c, KC_ECUDA, "kc_lower_bounds_subset: cudaEventCreate failed");
+        }
+        cudaEventRecord(e0, c->stream);
+    }
+    kc_status st = launch_seg_lb(c, L, sg.dev(ilo), sg.dev(ihi), B, reinterpret_cast<unsigned long long *>(w + keys_off),
+                                 static_cast<double *>(sg.dev(ilb)), static_cast<double *>(sg.dev(iraw)),
+                                 static_cast<int64_t *>(sg.dev(iarg)));
+    if (kernel_ms_out) {
+        cudaEventRecord(e1, c->stream);
+        if (st == KC_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(kernel_ms_out, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    KC_TRY(st);
+    return sg.finish();
+}
+
+}  // extern "C"

@@ -713,9 +713,28 @@ extern "C" kc_status kc_lower_bounds_noalloc(const float *X, int64_t N, int64_t 
     if (K < 1 || K > kMaxK || D < 1 || D > kMaxD || N < 0 || ld < N || N > 4294967294ll) return KC_EINVAL;
     if (B < 0 || B > kNoAllocMaxNodes) return KC_EINVAL;   // more nodes than the fixed scratch is sized for
     if (B == 0) return KC_OK;
+    // An error already pending in this thread belongs to earlier work: report
+    // it without clearing it (cudaPeekAtLastError) and launch nothing.
+    if (cudaPeekAtLastError() != cudaSuccess) return KC_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return KC_ECUDA;
+    // Every array must be device memory of the current GPU: a host array
+    // would make the kernels read or write through a host address.
+    // cudaPointerGetAttributes allocates nothing.
+    {
+        const void *args[6] = {X, lo, hi, lb_out, lb_raw_out, argmax_out};
+        for (const void *p : args) {
+            if (!p) continue;
+            cudaPointerAttributes a;
+            if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+                cudaGetLastError();   // the error this query just raised
+                return KC_EINVAL;
+            }
+            if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != dev)
+                return KC_EINVAL;
+        }
+    }
     // The host-side name of a __device__ array is not a device address: look
     // the address up once per device, with that device current.
     void *scratch = g_noalloc_ptr[dev].load();

@@ -48,15 +48,21 @@ def test_clock_summary_of_nvidia_smi_rows():
 
 
 def test_lower_bound_roofline_record():
-    """Roofline arithmetic of the benchmark line: 3 K D FP32 lane operations
-    per node x sample against SMs x 128 lanes x clock; the DRAM traffic of a
-    full launch scaled from the N = 5e6 capture."""
+    """Roofline arithmetic of the benchmark line: 4KD + K FP32 lane
+    operations per node x sample (packed subtraction 2, 3-input max 1, half a
+    packed FMA 1 per cluster and attribute; one min or max per cluster)
+    against SMs x 128 lanes x clock; the measured probe rate beside it; the
+    DRAM traffic of a full launch scaled from the N = 5e6 capture."""
     import bench
-    r = bench.lb_roofline(11.5, 10_000_000, 8, 5, 256, 152, 2070.0, 2070.0, (4, 256))
-    achieved = 3 * 5 * 8 * 256 * 1e7 / 11.5e-3 / 1e12
+    r = bench.lb_roofline(11.5, 10_000_000, 8, 5, 256, 152, 2070.0, 2070.0, (4, 256),
+                          probe={"fma2_tops": 40.0, "max3_tops": 39.0, "lb_mix_tops": 38.0})
+    achieved = (4 * 5 * 8 + 5) * 256 * 1e7 / 11.5e-3 / 1e12
+    assert r["ops_per_eval"] == 165
     assert abs(r["achieved"] - achieved) < 1e-9 and abs(r["peak"] - 152 * 128 * 2070e6 / 1e12) < 1e-9
-    assert abs(r["frac"] - achieved / r["peak"]) < 1e-12 and 0.6 < r["frac"] < 0.7
+    assert abs(r["frac"] - achieved / r["peak"]) < 1e-12 and 0.9 < r["frac"] < 0.92
+    assert abs(r["frac_of_probe"] - achieved / 38.0) < 1e-12
     assert r["traffic"] == 2 * 160_141_568 + 3_646_720 and r["bound"] == "alu"
     assert abs(r["hbm_gbs"] - 1e7 * 8 * 4 / 11.5e-3 / 1e9) < 1e-9
     other = bench.lb_roofline(11.5, 10_000_000, 8, 5, 256, 152, None, 1965.0, (2, 256))
     assert other["traffic"] is None and "fallback" in other["peak_basis"] and "1965" in other["peak_basis"]
+    assert "frac_of_probe" not in other

@@ -187,3 +187,54 @@ def test_full_size_microbench_sampled_nodes():
         ref, _ = oracle.lower_bound(X, lo[b], hi[b])
         assert lb[b] <= ref and lb[b] >= ref * (1 - REL)
     assert np.all(np.diff(raw) >= 0)
+
+
+@pytest.mark.parametrize("dtype,d,k", [(np.float32, 4, 3), (np.float64, 2, 4), (np.float32, 8, 5)])
+def test_fft_multi_matches_oracle_per_start(dtype, d, k):
+    """Algorithm 2 from 100 seeded starts in one call (the paper's 100-trial
+    FFT baseline): every set equals the oracle's FFT from its start --
+    identical indices, bit-equal double objective."""
+    X = _mix(20_011, d, k, seed=30 + d, dtype=dtype)
+    starts = np.random.default_rng(d).integers(0, X.shape[0], size=100).astype(np.int64)
+    starts[:3] = [0, X.shape[0] - 1, starts[3]]          # both ends and a repeated start
+    kc = KCenter(_t(X), k)
+    c, obj = kc.fft_multi(_t(starts))
+    torch.cuda.synchronize()
+    c, obj = c.cpu().numpy(), obj.cpu().numpy()
+    for s, st in enumerate(starts):
+        ref, refobj = oracle.fft(X, k, int(st))
+        assert np.array_equal(c[s], ref), (s, st, c[s], ref)
+        assert obj[s] == refobj, (s, obj[s], refobj)
+    single, sobj = kc.fft(int(starts[5]), like=_t(X))
+    assert np.array_equal(single.cpu().numpy(), c[5]) and float(sobj[0]) == obj[5]
+
+
+@pytest.mark.parametrize("d,k", [(4, 3), (2, 4), (8, 2)])
+def test_lower_bounds_subset_matches_oracle(d, k):
+    """Bounds over a sample subset given by index (unsorted, with repeats,
+    ragged against the 1024-entry tile): the certified bound lies within
+    1e-6 below the oracle's double value over exactly those samples, the
+    argmax is a sample of the subset attaining it within the float error;
+    an empty subset gives 0; an index >= N is refused."""
+    X = _mix(50_000, d, k, seed=60 + d, dtype=np.float32)
+    rng = np.random.default_rng(d)
+    ids = rng.choice(X.shape[0], size=33_333, replace=True).astype(np.uint32)
+    lo, hi = synth.random_boxes(X, k, 40, seed=k, frac_lo=0.0, frac_hi=0.4)
+    kc = KCenter(_t(X), k)
+    lb, raw, arg = kc.lower_bounds_subset(_t(ids.view(np.int32)), _t(lo), _t(hi))
+    torch.cuda.synchronize()
+    lb, raw, arg = lb.cpu().numpy(), raw.cpu().numpy(), arg.cpu().numpy()
+    sub = X[np.unique(ids)]
+    ref, _ = oracle.lower_bounds(sub, lo, hi)
+    assert np.all(lb <= ref) and np.all(lb >= ref * (1 - REL))
+    assert np.all(np.isin(arg, ids))
+    for b in range(0, 40, 7):
+        v = oracle.beta_matrix(X[arg[b]:arg[b] + 1], lo[b], hi[b]).min()
+        assert v >= ref[b] * (1 - 1e-6) - 1e-30
+    e_lb, e_raw, e_arg = kc.lower_bounds_subset(_t(np.zeros(0, np.int32)), _t(lo[:2]), _t(hi[:2]))
+    assert float(e_lb[0]) == 0.0 and int(e_arg[0]) == -1
+    bad = ids[:10].copy()
+    bad[7] = X.shape[0]
+    with pytest.raises(KCError) as e:
+        kc.lower_bounds_subset(_t(bad.view(np.int32)), _t(lo), _t(hi))
+    assert e.value.status == 1

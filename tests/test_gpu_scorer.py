@@ -66,6 +66,46 @@ def test_training_fits_a_teacher():
     assert abs(mlp.loss(sc.params(), X, T, M) - l1) <= 1e-3 * max(1.0, l1)
 
 
+@pytest.mark.parametrize("steps", [1, 2, 5])
+def test_adam_steps_match_oracle(steps):
+    """kc_mlp_train with one batch holding every sample (so the batch order
+    cannot matter) takes `steps` Adam steps (Kingma & Ba, Algorithm 1: lr
+    1e-3, beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected moments).  The
+    oracle repeats them: the FP64 gradient on the bf16-rounded weights of
+    the float32 master parameters, mlp.adam_step, the parameters stored back
+    as float32.  At step 1 every update is +-lr times g / (|g| + eps), so a
+    wrong bias correction, a misplaced epsilon or a stale bf16 refresh moves
+    a parameter by a large part of lr.  Tolerance: 2 % of lr per step plus
+    two float32 ulps where the oracle's gradient is at least 1e-2 of the
+    largest one at every step (its sign and the ratios of successive steps
+    are then fixed by the FP32 gradient, whose error is far below 1e-4 of the
+    largest gradient); elsewhere the Adam step bound, 3 lr per step."""
+    theta0 = mlp.init_params(21)
+    X, T, M = _data(500, 21)
+    sc = Scorer(theta0)
+    sc.train(X, T, M, epochs=steps, batch=len(X), lr=1e-3, seed=5)
+    got = sc.params().astype(np.float64)
+
+    theta = theta0.astype(np.float32)
+    m = np.zeros(mlp.NPARAM)
+    v = np.zeros(mlp.NPARAM)
+    well = np.ones(mlp.NPARAM, bool)
+    for t in range(1, steps + 1):
+        _, g = mlp.grad(theta, X, T, M)
+        well &= np.abs(g) >= 1e-2 * np.max(np.abs(g))
+        new, m, v = mlp.adam_step(theta.astype(np.float64), m, v, g, t, lr=1e-3)
+        theta = new.astype(np.float32)
+    ref = theta.astype(np.float64)
+    moved = np.abs(ref - theta0.astype(np.float64))
+    assert np.median(moved[well]) > 0.8e-3 * steps      # the steps did move the parameters
+    diff = np.abs(got - ref)
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    tight = diff <= 0.02 * 1e-3 * steps + 2 * ulp
+    assert np.all(tight[well]), (np.max(diff[well]), int(np.sum(~tight[well])))
+    assert np.all(diff <= 3e-3 * steps), np.max(diff)
+    assert well.mean() > 0.3
+
+
 def test_learned_order_keeps_the_optimum():
     """Any scorer only changes the order of nodes and the branching variable;
     every prune still uses the exact bound.  Here the output layer is zero and

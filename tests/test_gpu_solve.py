@@ -136,6 +136,125 @@ def test_tighten_f32_exact_on_unambiguous_inputs(d, k):
     _compare_tighten(X, lo, hi, alpha, None, g, exact_cand=False)
 
 
+def _step_a_clear(X64, lo, hi, alpha, band=3e-6):
+    """No center-based (Lemma 1) decision lies within `band` of alpha."""
+    for b in range(lo.shape[0]):
+        bm = oracle.beta_matrix(X64, lo[b], hi[b])
+        if np.any(np.abs(bm - alpha) <= band * alpha):
+            return False
+    return True
+
+
+def _ambiguous_ball_alpha(X, lo, hi, alpha0):
+    """An alpha at which the center-based assignment, and so the
+    representatives, are decided the same in float and double, but some
+    sample s of a box-BT box M'^k lies within sqrt(alpha) of every
+    representative of k except one, j, with ||x_s - x_j||^2 just above alpha
+    (by 1e-7 relative): the double rule drops s from S_+^k, while the float
+    evaluation (error bound ~1e-6 relative) cannot prove it outside.
+    Returns (alpha, [(node, k, s)]) or None."""
+    X64 = X.astype(np.float64)
+    alpha = alpha0
+    for _ in range(40):
+        if _step_a_clear(X64, lo, hi, alpha):
+            best = None
+            for b in range(lo.shape[0]):
+                r = oracle.tighten(X64, lo[b], hi[b], alpha, is_f32=True)
+                if r["status"] == 1:
+                    continue
+                for k, reps in enumerate(r["reps"]):
+                    if not reps:
+                        continue
+                    inb = np.all((X64 >= r["box_bt_lo"][k]) & (X64 <= r["box_bt_hi"][k]), axis=1)
+                    idx = np.flatnonzero(inb)
+                    dd = ((X64[idx, None, :] - X64[np.array(reps)][None, :, :]) ** 2).sum(2)   # (n_in, R)
+                    over = dd > alpha
+                    one = (over.sum(1) == 1)
+                    gap = np.where(over, dd / alpha - 1.0, np.inf).min(1)
+                    ok = one & (gap < 1e-4) & np.all(np.where(over, True, dd <= alpha * (1 - 3e-6)), axis=1)
+                    for i in np.flatnonzero(ok):
+                        cand = (gap[i], b, k, int(idx[i]), float(dd[i][over[i]][0]))
+                        if best is None or cand[0] < best[0]:
+                            best = cand
+            if best is not None:
+                a2 = best[4] * (1 - 1e-7)
+                # moving alpha to a2 must not change the representatives or
+                # any other decision of the center-based rule
+                if _step_a_clear(X64, lo, hi, a2):
+                    same = all(oracle.tighten(X64, lo[b], hi[b], a2, is_f32=True)["reps"] ==
+                               oracle.tighten(X64, lo[b], hi[b], alpha, is_f32=True)["reps"]
+                               for b in range(lo.shape[0]))
+                    if same:
+                        return a2, [(best[1], best[2], best[3])]
+        alpha *= 1.0000373
+    return None
+
+
+@pytest.mark.parametrize("d,k", [(2, 3), (4, 3)])
+def test_tighten_f32_ambiguous_ball_decisions_are_conservative(d, k):
+    """Float tightening where float and double decisions differ: alpha is
+    placed within the rounding band of a ball-membership test (see
+    _ambiguous_ball_alpha).  The kernels take an exclusion only where the
+    float evaluation proves it, so against the double oracle: every status 1
+    is the oracle's status 1; where the oracle finds the node feasible, the
+    tightened boxes contain the oracle's and the counts |S_+^k| are at least
+    the oracle's; at the planted pair the count is strictly larger (the
+    sample the oracle drops is kept)."""
+    X = _blobs(4_003, d, k, seed=300 + d * 7 + k, dtype=np.float32)
+    c, fobj = oracle.fft(X, k, 1)
+    lo, hi = _nodes_around(X, c, 12, seed=d + 40)
+    found = _ambiguous_ball_alpha(X, lo, hi, fobj * 0.71)
+    assert found is not None, "no ambiguous ball decision could be placed"
+    alpha, planted = found
+    kc = KCenter(_t(X), k)
+    g = kc.tighten(_t(lo), _t(hi), alpha)
+    torch.cuda.synchronize()
+    st, glo, ghi = g["status"].cpu().numpy(), g["lo"].cpu().numpy(), g["hi"].cpu().numpy()
+    gcnt, glb = g["count"].cpu().numpy(), g["lb"].cpu().numpy()
+    for b in range(lo.shape[0]):
+        r = oracle.tighten(X, lo[b], hi[b], alpha, is_f32=True)
+        assert glb[b] <= r["beta"] and glb[b] >= r["beta"] * (1 - 1e-6)
+        if st[b] == 1:
+            assert r["status"] == 1, b
+        if r["status"] == 1:
+            continue
+        assert st[b] != 1, b
+        assert np.all(glo[b] <= r["lo"].astype(np.float32)) and np.all(ghi[b] >= r["hi"].astype(np.float32)), b
+        assert np.all(gcnt[b] >= r["count"]), (b, gcnt[b], r["count"])
+    for b, j, s_ in planted:
+        r = oracle.tighten(X, lo[b], hi[b], alpha, is_f32=True)
+        if r["status"] != 1 and st[b] != 1:
+            assert gcnt[b, j] > r["count"][j], (b, j, s_, gcnt[b], r["count"])
+
+
+def test_tighten_f32_exact_at_one_million_samples():
+    """The batched-solve recipe (D=4, K=3, weights .6/.3/.1) at N = 1e6, where
+    the shared-set tightening kernels merge the partial keys of thousands of
+    CTAs per node.  At this size thousands of decision values lie within
+    1e-3 of any alpha, so no alpha keeps them all outside the float error
+    band; instead the coordinates are rounded to multiples of 1/4 and the
+    node boxes outward to that grid.  Every clamp and sample distance is then
+    a multiple of 1/16 computed exactly in float, and alpha is an odd multiple
+    of 1/32, so float and double take every decision alike and the outputs
+    must equal the double oracle's exactly (statuses, boxes, counts;
+    candidates -- nearest to a box-BT midpoint, which is off the grid --
+    within the float argmin's error)."""
+    X, w = synth.make_workload("batched_solve", n=1_000_000)
+    X = (np.round(X.astype(np.float64) * 4) / 4).astype(np.float32)
+    c, fobj = oracle.fft(X, w.k, 0)
+    lo, hi = _nodes_around(X, c, 8, seed=77, scale=(0.05, 0.5))
+    lo = (np.floor(lo.astype(np.float64) * 4) / 4).astype(np.float32)
+    hi = (np.ceil(hi.astype(np.float64) * 4) / 4).astype(np.float32)
+    kc = KCenter(_t(X), w.k)
+    n_feasible = 0
+    for f in (0.83, 0.95):
+        alpha = (np.round(fobj * f * 16) + 0.5) / 16
+        g = kc.tighten(_t(lo), _t(hi), alpha)
+        torch.cuda.synchronize()
+        n_feasible += _compare_tighten(X, lo, hi, alpha, None, g, exact_cand=False)
+    assert n_feasible >= 8
+
+
 def test_tighten_root_and_ragged_sizes():
     """Root node (all boxes = M0): bound 0, nothing assigned (boxes equal)."""
     X = _blobs(1_037, 2, 3, seed=4, dtype=np.float64)

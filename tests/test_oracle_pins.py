@@ -465,3 +465,27 @@ def test_box_bt_bounds_contain_the_real_interval():
         rt = float(np.sqrt(alpha))
         assert float(M - lv) - rt <= 8 * np.spacing(rt) + 4 * np.spacing(abs(float(M)) + 1.0)
         assert float(hv - m) - rt <= 8 * np.spacing(rt) + 4 * np.spacing(abs(float(m)) + 1.0)
+
+
+def test_parallel_lower_bounds_equal_serial():
+    """The all-cores variant of the bound loop (the timed CPU baseline) gives
+    the serial loop's values and argmax bit for bit: random data, ties from
+    duplicated rows (the smallest index must win across blocks), fewer
+    samples than blocks, and a single sample."""
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(5_003, 3))
+    X[4000] = X[17]                      # a tie across blocks
+    lo = rng.normal(size=(9, 2, 3)) - 0.5
+    hi = lo + rng.uniform(0.1, 1.0, size=(9, 2, 3))
+    for Xs in (X, X[:5], X[:1]):
+        a, b = oracle.lower_bounds(Xs, lo, hi)
+        c, d, nt = oracle.lower_bounds_par(Xs, lo, hi)
+        assert nt >= 1
+        assert np.array_equal(a, c) and np.array_equal(b, d)
+    # a box around the duplicated pair's far side: both copies attain the max
+    lo2 = np.full((1, 1, 3), -50.0); hi2 = np.full((1, 1, 3), -49.0)
+    far = np.argmax(oracle.beta_matrix(X, lo2[0], hi2[0])[:, 0])
+    X2 = X.copy(); X2[4999] = X2[far]
+    a, b = oracle.lower_bounds(X2, lo2, hi2)
+    c, d, _ = oracle.lower_bounds_par(X2, lo2, hi2)
+    assert b[0] == d[0] == min(far, 4999) and a[0] == c[0]
