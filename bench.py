@@ -188,22 +188,42 @@ def time_events(fn, iters, stream, torch):
     return e0.elapsed_time(e1) / iters
 
 
-def hbm_points(kcm, torch, dev, stream, h, lod, hid, n, d, hbm_peak, rank):
+def one_node_point(kcm, torch, dev, stream, h, lo4, hi4, n, d, k, name, hbm_peak, iters):
+    """HBM record of kc_lower_bounds on ONE node over all n samples (4D bytes
+    per sample).  Beside it, the arithmetic time of one node's pass measured
+    as (t(B = 4) - t(B = 1)) / 3: when it exceeds bytes / peak HBM bandwidth,
+    the one-node pass is bound by instruction throughput, not by HBM."""
+    def timed(B):
+        lb = torch.empty(B, dtype=torch.float64, device=dev)
+        lo, hi = lo4[:B].contiguous(), hi4[:B].contiguous()
+        for _ in range(5):
+            kcm.kc_lower_bounds(h, lo, hi, lb)
+        return time_events(lambda: kcm.kc_lower_bounds(h, lo, hi, lb), iters, stream, torch)
+    ms1, ms4 = timed(1), timed(4)
+    gbs = n * d * 4 / (ms1 * 1e-3) / 1e9
+    return {"kernel": "lb_f32_fast (+ finalize)", "workload": f"{name} N={n:,} D={d} K={k}, one node",
+            "bytes_per_launch": n * d * 4, "ms": ms1, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+            "frac": gbs / hbm_peak, "timed": f"kc_lower_bounds call incl. finalize, CUDA events, {iters} launches",
+            "arith_ms_per_node": (ms4 - ms1) / 3, "hbm_ms_at_peak": n * d * 4 / (hbm_peak * 1e9) * 1e3}
+
+
+def hbm_points(kcm, torch, dev, stream, h, lod, hid, n, d, k, hbm_peak, rank, learned=None):
     """Where the HBM ceiling binds: the bound of ONE node (B = 1) over the
-    lower-bound microbenchmark data (4D bytes per sample, 4KD+K lane ops:
-    near the ridge), and the per-node-list gather kernel with one node over
-    the batched-solve recipe (N = 1e7, D = 4): the root list (every sample,
-    ids in order) and a sorted 25 % subset (4 + 4D bytes per entry)."""
-    pts = []
-    lb1 = torch.empty(1, dtype=torch.float64, device=dev)
-    lo1, hi1 = lod[:1].contiguous(), hid[:1].contiguous()
-    for _ in range(5):
-        kcm.kc_lower_bounds(h, lo1, hi1, lb1)
-    ms = time_events(lambda: kcm.kc_lower_bounds(h, lo1, hi1, lb1), 200, stream, torch)
-    gbs = n * d * 4 / (ms * 1e-3) / 1e9
-    pts.append({"kernel": "lb_f32_fast (+ finalize)", "workload": f"lb_microbench N={n:,} D={d}, one node",
-                "bytes_per_launch": n * d * 4, "ms": ms, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
-                "frac": gbs / hbm_peak, "timed": "kc_lower_bounds call, CUDA events, 200 launches"})
+    lower-bound microbenchmark data (32 bytes and 165 lane operations per
+    sample: near the ridge) and over the learned-order data (N = 1e8, D = 2,
+    K = 4: 8 bytes and 36 lane operations per sample), and the per-node-list
+    gather kernel with one node over the batched-solve recipe (N = 1e7,
+    D = 4): the root list (every sample, ids in order) and a sorted 25 %
+    subset (4 + 4D bytes per entry)."""
+    pts = [one_node_point(kcm, torch, dev, stream, h, lod[:4].contiguous(), hid[:4].contiguous(), n, d, k,
+                          "lb_microbench", hbm_peak, 200)]
+    if learned is not None:
+        kl, Xl, wl = learned
+        c = np.random.default_rng(9).integers(0, Xl.shape[0], size=(4, wl.k))
+        lo = torch.from_numpy((Xl[c] - 0.25).astype(np.float32)).to(dev)
+        hi = torch.from_numpy((Xl[c] + 0.25).astype(np.float32)).to(dev)
+        pts.append(one_node_point(kcm, torch, dev, stream, kl.h, lo, hi, Xl.shape[0], wl.d, wl.k, "learned_order",
+                                  hbm_peak, 50))
     Xs, ws = synth.make_workload("batched_solve", n=10_000_000, seed=2 + rank)
     kc = kcm.KCenter(torch.from_numpy(Xs).to(dev), ws.k)
     rng = np.random.default_rng(5)
@@ -404,7 +424,12 @@ def main():
     roofline = lb_roofline(ms, n, w.d, w.k, B_NODES, sms, ck.get("sm_mhz"),
                            measured_peaks().get("sm_max_mhz", 2070.0), (tuned_st, tuned_chunk), probe)
     hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
-    hbm = None if args.no_hbm_points else hbm_points(kcm, torch, dev, stream, h, lod, hid, n, w.d, hbm_peak, rank)
+    learned_data = None
+    if args.learned_n > 0:
+        Xl, wl = synth.make_workload("learned_order", n=args.learned_n, seed=3 + rank)
+        learned_data = (kcm.KCenter(torch.from_numpy(Xl).to(dev), wl.k), Xl, wl)
+    hbm = None if args.no_hbm_points else hbm_points(kcm, torch, dev, stream, h, lod, hid, n, w.d, w.k, hbm_peak,
+                                                      rank, learned_data)
 
     # ---- time to a certified optimum (kc_solve, tol 1e-12) on the
     # batched-solve recipe, data resident in HBM; every rank solves its own
@@ -435,9 +460,9 @@ def main():
     learned = None
     if args.learned_n > 0:
         from paper_2301_00061_gb300 import scorer as kc_scorer
-        Xl, wl = synth.make_workload("learned_order", n=args.learned_n, seed=3 + rank)
-        kc = kcm.KCenter(torch.from_numpy(Xl).to(dev), wl.k)
+        kc, Xl, wl = learned_data
         del Xl
+        learned_data = None
         sc = kcm.Scorer(kc_scorer.load())
         kc.set_scorer(sc)
         res = {}

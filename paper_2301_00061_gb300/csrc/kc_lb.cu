@@ -52,6 +52,53 @@ __device__ __forceinline__ void load_box(const uint64_t *p, uint64_t (&bx)[D])
     }
 }
 
+// Every node's running maximum over one thread's ST samples px (packed
+// (x, -x) per attribute; when not `full`, samples s0 + j >= n are ignored),
+// merged into the warp's keys mine[b] (value bits, ~position): a warp
+// reduces with shuffles only when one of its lanes may beat the warp's best.
+template <int D, int K, int ST>
+__device__ __forceinline__ void eval_nodes(const uint64_t (&px)[ST][D], bool full, int64_t s0, int64_t n,
+                                           const uint64_t *sbox, int B, unsigned long long *mine, int lane)
+{
+    constexpr int KD = K * D;
+    for (int b = 0; b < B; ++b) {
+        const uint64_t *bb = sbox + (size_t)b * KD;
+        float best[ST];
+#pragma unroll
+        for (int j = 0; j < ST; ++j) best[j] = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            uint64_t bx[D];
+            load_box<D>(bb + k * D, bx);
+#pragma unroll
+            for (int j = 0; j < ST; ++j) best[j] = fminf(best[j], box_dist_f32<D>(px[j], bx));
+        }
+        if (!full) {
+#pragma unroll
+            for (int j = 0; j < ST; ++j)
+                if (s0 + j >= n) best[j] = -1.f;
+        }
+        float m = best[0];
+#pragma unroll
+        for (int j = 1; j < ST; ++j) m = fmaxf(m, best[j]);
+        const unsigned long long cur = mine[b];
+        const bool maybe = m >= key_val(cur);
+        if (__any_sync(0xffffffffu, maybe)) {
+            unsigned long long key = 0ull;
+            if (maybe) {
+                int jm = 0;
+#pragma unroll
+                for (int j = ST - 1; j >= 0; --j)
+                    if (best[j] == m) jm = j;
+                key = key_max(m, (uint32_t)(s0 + jm));
+            }
+            key = warp_max_u64(key);
+            if (lane == 0 && key > cur) mine[b] = key;
+            __syncwarp();
+        }
+    }
+}
+
 // Float lower bound, compile-time D and K.  Shared memory: B*K*D packed
 // boxes + (warps x B) running-best keys.
 template <int D, int K, int ST>
@@ -92,42 +139,7 @@ lb_f32_fast(const float *__restrict__ X, int64_t ld, int64_t n, const float *__r
                     px[j][a] = pk(v, -v);
                 }
         }
-        for (int b = 0; b < B; ++b) {
-            const uint64_t *bb = sbox + (size_t)b * KD;
-            float best[ST];
-#pragma unroll
-            for (int j = 0; j < ST; ++j) best[j] = __int_as_float(0x7f800000);
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                uint64_t bx[D];
-                load_box<D>(bb + k * D, bx);
-#pragma unroll
-                for (int j = 0; j < ST; ++j) best[j] = fminf(best[j], box_dist_f32<D>(px[j], bx));
-            }
-            if (!full) {
-#pragma unroll
-                for (int j = 0; j < ST; ++j)
-                    if (s0 + j >= n) best[j] = -1.f;
-            }
-            float m = best[0];
-#pragma unroll
-            for (int j = 1; j < ST; ++j) m = fmaxf(m, best[j]);
-            const unsigned long long cur = mine[b];
-            const bool maybe = m >= key_val(cur);
-            if (__any_sync(0xffffffffu, maybe)) {
-                unsigned long long key = 0ull;
-                if (maybe) {
-                    int jm = 0;
-#pragma unroll
-                    for (int j = ST - 1; j >= 0; --j)
-                        if (best[j] == m) jm = j;
-                    key = key_max(m, (uint32_t)(s0 + jm));
-                }
-                key = warp_max_u64(key);
-                if (lane == 0 && key > cur) mine[b] = key;
-                __syncwarp();
-            }
-        }
+        eval_nodes<D, K, ST>(px, full, s0, n, sbox, B, mine, lane);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < B; b += kThreads) {
