@@ -300,9 +300,9 @@ kc_status launch_seg_objective(kc_ctx *c, const ListBatch &L, const int64_t *cen
                                unsigned long long *keys, unsigned long long *vmax, float *thr, double *val);
 kc_status launch_seg_filter(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B,
                             const float *beta_dn_dev, double alpha, const void *repx, const int *nreps, int RM,
-                            const int *rmap, uint32_t *out_pool, const int64_t *out_off, unsigned long long *out_n,
-                            const int *cvar, const float *csplit, unsigned long long *ckeys, double *child_lb,
-                            double *child_raw);
+                            const int *rmap, uint32_t *out_pool, const int64_t *out_off, const int64_t *out_cap,
+                            unsigned long long *out_n, const int *cvar, const float *csplit,
+                            unsigned long long *ckeys, double *child_lb, double *child_raw);
 // Tightening of B nodes, each over its own list (float data).
 kc_status launch_tighten_list(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, double alpha,
                               const int64_t *seeds_dev, int ball_cap, void *lo_out, void *hi_out, int64_t *counts,

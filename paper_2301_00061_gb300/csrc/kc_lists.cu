@@ -260,7 +260,9 @@ seg_obj_exact(const float *__restrict__ X, int64_t ld, ListBatch L, const float 
 // is redundant for the lower bound (farthest-corner value proved below beta_b)
 // and for the upper bound (outside every box, or some representative of each
 // box that holds it proved farther than alpha).  Output: appended to the
-// node's region out_pool[out_off[b] ...], count in out_n[b] (unordered tiles).
+// node's region out_pool[out_off[b] ...], count in out_n[b] (unordered tiles);
+// out_off[b] < 0 (or out_pool NULL) counts node b's survivors without writing;
+// with out_cap, entries at positions >= out_cap[b] are counted, not written.
 // With ckeys, the lower bounds of node b's two children over the surviving
 // samples come out of the same pass: child 0 has hi[cvar[b]] = csplit[2b],
 // child 1 has lo[cvar[b]] = csplit[2b + 1], all other bounds as node b's boxes
@@ -271,8 +273,8 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
                const float *__restrict__ hi, int K, int D, const float *__restrict__ beta_dn, float infl, float slack,
                float t_alpha, const float *__restrict__ repx, const int *__restrict__ nreps, int RM,
                const int *__restrict__ rmap, uint32_t *__restrict__ out_pool, const int64_t *__restrict__ out_off,
-               unsigned long long *__restrict__ out_n, const int *__restrict__ cvar, const float *__restrict__ csplit,
-               unsigned long long *__restrict__ ckeys)
+               const int64_t *__restrict__ out_cap, unsigned long long *__restrict__ out_n,
+               const int *__restrict__ cvar, const float *__restrict__ csplit, unsigned long long *__restrict__ ckeys)
 {
     // out_pool NULL: count the surviving samples only
     __shared__ uint64_t sbox[kMaxK * DMAX];
@@ -378,8 +380,9 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
                 unsigned long long base = 0ull;
                 if (lane == 0) base = atomicAdd(&out_n[b], (unsigned long long)__popc(bal));
                 base = __shfl_sync(0xffffffffu, base, 0);
-                if (keep && out_pool)
-                    out_pool[out_off[b] + (int64_t)(base + __popc(bal & ((1u << lane) - 1u)))] = id;
+                const int64_t pos = (int64_t)(base + __popc(bal & ((1u << lane) - 1u)));
+                if (keep && out_pool && out_off[b] >= 0 && (!out_cap || pos < out_cap[b]))
+                    out_pool[out_off[b] + pos] = id;
             }
         }
         if (ckeys) {
@@ -524,9 +527,9 @@ kc_status launch_seg_objective(kc_ctx *c, const ListBatch &L, const int64_t *cen
 
 kc_status launch_seg_filter(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B,
                             const float *beta_dn_dev, double alpha, const void *repx, const int *nreps, int RM,
-                            const int *rmap, uint32_t *out_pool, const int64_t *out_off, unsigned long long *out_n,
-                            const int *cvar, const float *csplit, unsigned long long *ckeys, double *child_lb,
-                            double *child_raw)
+                            const int *rmap, uint32_t *out_pool, const int64_t *out_off, const int64_t *out_cap,
+                            unsigned long long *out_n, const int *cvar, const float *csplit,
+                            unsigned long long *ckeys, double *child_lb, double *child_raw)
 {
     if (c->D > kListMaxD) return set_err(c, KC_EINVAL, "list kernels: D <= %d (got %d)", kListMaxD, c->D);
     if (B <= 0) return KC_OK;
@@ -547,7 +550,7 @@ kc_status launch_seg_filter(kc_ctx *c, const ListBatch &L, const void *lo, const
                                                  static_cast<const float *>(lo), static_cast<const float *>(hi), c->K,
                                                  c->D, beta_dn_dev, infl, slack, t_alpha,
                                                  static_cast<const float *>(repx), nreps, RM, rmap, out_pool, out_off,
-                                                 out_n, cvar, csplit, ckeys);
+                                                 out_cap, out_n, cvar, csplit, ckeys);
     KC_TRY(after_launch(c, "list filter"));
     if (ckeys) {
         keys_finalize<<<(2 * B + 127) / 128, 128, 0, c->stream>>>(ckeys, 2 * B, deflate_factor(KC_F32, c->D),

@@ -74,6 +74,8 @@ struct Node {
     int64_t group = 0;       // its ancestor at depth 8 (itself above that depth)
     float prio = 0.f;        // learned priority (ties of equal keys: smaller first)
     int list = -1;           // handle of its surviving-sample list (per-node list mode)
+    int8_t fwait = 0;        // generations still to skip list filtering (after filters that dropped little)
+    int8_t fstreak = 0;      // consecutive such filters along the path
 };
 
 template <typename T>
@@ -435,14 +437,14 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     const int kSlots = 6;   // batch, its refinement, upper bounds, filter, children, their refinement
     const size_t l_keys = (size_t)kSlots * slot_bytes, l_vmax = l_keys + (size_t)Bmax * 8;
     const size_t l_thr = l_vmax + (size_t)Bmax * 8, l_beta = l_thr + (size_t)Bmax * 4;
-    const size_t l_off = l_beta + (size_t)Bmax * 4, l_n = l_off + (size_t)Bmax * 8;
+    const size_t l_off = l_beta + (size_t)Bmax * 4, l_cap = l_off + (size_t)Bmax * 8, l_n = l_cap + (size_t)Bmax * 8;
     const size_t l_cvar = l_n + (size_t)Bmax * 8, l_csplit = l_cvar + (size_t)Bmax * 4;
     const size_t l_ckeys = l_csplit + (size_t)2 * Bmax * 4, l_clb = l_ckeys + (size_t)2 * Bmax * 8;
     const size_t l_craw = l_clb + (size_t)2 * Bmax * 8;
     const size_t l_end = l_craw + (size_t)2 * Bmax * 8 + 256;
     unsigned long long *d_keys = nullptr, *d_vmax = nullptr, *d_outn = nullptr, *d_ckeys = nullptr;
     float *d_thr = nullptr, *d_beta = nullptr, *d_csplit = nullptr;
-    int64_t *d_outoff = nullptr;
+    int64_t *d_outoff = nullptr, *d_outcap = nullptr;
     int *d_cvar = nullptr;
     double *d_clb = nullptr, *d_craw = nullptr;
     int root_list = -1;
@@ -454,6 +456,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         d_thr = reinterpret_cast<float *>(lb + l_thr);
         d_beta = reinterpret_cast<float *>(lb + l_beta);
         d_outoff = reinterpret_cast<int64_t *>(lb + l_off);
+        d_outcap = reinterpret_cast<int64_t *>(lb + l_cap);
         d_outn = reinterpret_cast<unsigned long long *>(lb + l_n);
         d_cvar = reinterpret_cast<int *>(lb + l_cvar);
         d_csplit = reinterpret_cast<float *>(lb + l_csplit);
@@ -553,7 +556,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     if (o.log_path && !log_file) return set_err(c, KC_EINVAL, "kc_solve: cannot open log_path '%s'", o.log_path);
     FILE *log = log_file.get();
     double prof[5] = {0, 0, 0, 0, 0};
-    double tA = 0;
+    double tA = 0, last_trace = t0;
 
     auto prune_threshold = [&]() { return alpha - tol * alpha; };
     auto drop_list = [&](Node<T> &nd) {
@@ -648,22 +651,37 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         }
         if (!live.empty()) {
             const int S = (int)live.size();
+            // evaluation order: nodes whose lists hold at least a quarter of
+            // the samples first -- their sets are evaluated over all samples
+            // in one pass that every set shares -- then the others, each over
+            // its own list (its candidate lies in the node's boxes, where every
+            // dropped sample is nearer to it than the node's bound, so the
+            // list's maximum is the full-data objective)
+            std::vector<int> ev(live);
+            int S_long = 0;
+            if (lists) {
+                std::stable_partition(ev.begin(), ev.end(),
+                                      [&](int b) { return list_n(batch[b].list) * 4 >= c->N; });
+                for (int b : ev) S_long += list_n(batch[b].list) * 4 >= c->N ? 1 : 0;
+            }
             for (int i = 0; i < S; ++i)
-                for (int k = 0; k < K; ++k) h_sets[(size_t)i * K + k] = h_cand[(size_t)live[i] * K + k];
+                for (int k = 0; k < K; ++k) h_sets[(size_t)i * K + k] = h_cand[(size_t)ev[i] * K + k];
             KC_CUDA(c, cudaMemcpyAsync(d_sets, h_sets, (size_t)S * K * 8, cudaMemcpyHostToDevice, c->stream));
             if (lists) {
-                // over the node's own list: its candidate lies in the node's
-                // boxes, where every dropped sample is nearer to it than the
-                // node's bound, so the maximum is the full-data objective
-                ListBatch Lu;
-                KC_TRY(make_lb(2, S, [&](int i) { return batch[live[i]].list; }, nullptr, &Lu, nullptr));
-                KC_TRY(launch_seg_objective(c, Lu, d_sets, S, alpha, d_keys, d_vmax, d_thr, d_val));
+                if (S_long > 0) KC_TRY(launch_objective(c, full_view(c), d_sets, S_long, K, alpha, d_val, nullptr));
+                if (S > S_long) {
+                    ListBatch Lu;
+                    KC_TRY(make_lb(2, S - S_long, [&](int i) { return batch[ev[S_long + i]].list; }, nullptr, &Lu,
+                                   nullptr));
+                    KC_TRY(launch_seg_objective(c, Lu, d_sets + (size_t)S_long * K, S - S_long, alpha, d_keys, d_vmax,
+                                                d_thr, d_val + S_long));
+                }
             } else {
                 KC_TRY(launch_objective(c, cur, d_sets, S, K, alpha, d_val, nullptr));
             }
             KC_CUDA(c, cudaMemcpyAsync(h_val, d_val, (size_t)S * 8, cudaMemcpyDeviceToHost, c->stream));
             KC_CUDA(c, cudaStreamSynchronize(c->stream));
-            for (int i = 0; i < S; ++i) h_ub[live[i]] = h_val[i];
+            for (int i = 0; i < S; ++i) h_ub[ev[i]] = h_val[i];
             for (int i = 0; i < S; ++i)
                 if (h_val[i] < alpha) {
                     alpha = h_val[i];
@@ -811,21 +829,59 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         // The filter also bounds the children over the surviving samples
         // (flb/fraw[2 * row + side]); fused_row[i]: node i's row, or -1.
         std::vector<int> kid_list(NB, -1), fused_row(NB, -1);
+        std::vector<int8_t> kid_fwait(NB, 0), kid_fstreak(NB, 0);
         std::vector<double> flb, fraw;
         if (lists && NB > 0 && o.i_sr > 0 && batches % o.i_sr == 0) {
-            std::vector<int> fi, rows;
-            std::vector<int64_t> offs;
+            std::vector<int> fi, rows, cand;
+            std::vector<int64_t> offs, caps;
             std::vector<float> bdn;
+            const int64_t room = arena.cap - arena.used;
             for (int i = 0; i < NB; ++i) {
+                const Node<T> &nd = batch[br[i]];
+                kid_list[i] = nd.list;
+                kid_fwait[i] = nd.fwait > 0 ? (int8_t)(nd.fwait - 1) : (int8_t)0;
+                kid_fstreak[i] = nd.fstreak;
+                const int64_t n = list_n(nd.list);
+                if (n < 2 * LT || nd.fwait > 0) continue;
+                if (n > 4 * room) {
+                    // no room for what a filter of this list would keep: skip it
+                    // (and the next generation's) instead of scanning in vain
+                    kid_fwait[i] = 1;
+                    continue;
+                }
+                cand.push_back(i);
+            }
+            // a filter writes its survivors straight into a region as long as
+            // its list while those regions fit in half the free arena; beyond
+            // that the longest lists are counted first (no output) and written
+            // in a second pass once their survivors' number is known
+            std::vector<char> counted(NB, 0);
+            {
+                int64_t total = 0;
+                for (int i : cand) total += list_n(batch[br[i]].list);
+                std::vector<int> byn(cand);
+                std::stable_sort(byn.begin(), byn.end(), [&](int x, int y) {
+                    return list_n(batch[br[x]].list) > list_n(batch[br[y]].list);
+                });
+                const int64_t budget = (arena.cap - arena.used) / 2;
+                for (int i : byn) {
+                    if (total <= budget) break;
+                    counted[i] = 1;
+                    total -= list_n(batch[br[i]].list);
+                }
+            }
+            for (int i : cand) {
                 const int b = br[i];
-                kid_list[i] = batch[b].list;
                 const int64_t n = list_n(batch[b].list);
-                if (n < 2 * LT) continue;
-                const int64_t off = arena.alloc(n);
-                if (off < 0) continue;
+                int64_t off = -1;
+                if (!counted[i]) {
+                    off = arena.alloc(n);
+                    if (off < 0) counted[i] = 1;
+                }
                 fi.push_back(i);
                 rows.push_back(b);
                 offs.push_back(off);
+                caps.push_back(off >= 0 ? n : 0);
                 float f = (float)batch[b].key;
                 if ((double)f > batch[b].key) f = nextafterf(f, -1.f);
                 bdn.push_back(f);
@@ -840,6 +896,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 KC_CUDA(c, cudaMemcpyAsync(d_lhi, h_lhi.data(), (size_t)nf * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
                 KC_CUDA(c, cudaMemcpyAsync(d_beta, bdn.data(), (size_t)nf * 4, cudaMemcpyHostToDevice, c->stream));
                 KC_CUDA(c, cudaMemcpyAsync(d_outoff, offs.data(), (size_t)nf * 8, cudaMemcpyHostToDevice, c->stream));
+                KC_CUDA(c, cudaMemcpyAsync(d_outcap, caps.data(), (size_t)nf * 8, cudaMemcpyHostToDevice, c->stream));
                 // the children's split (branching variable and value, as below)
                 std::vector<int> cvar(nf);
                 std::vector<float> csplit((size_t)2 * nf);
@@ -859,8 +916,8 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 KC_TRY(make_lb(3, nf, [&](int q) { return batch[rows[q]].list; }, rows.data(), &Lf, &rows_dev));
                 const bool bt = o.use_bt != 0;
                 KC_TRY(launch_seg_filter(c, Lf, d_llo, d_lhi, nf, d_beta, alpha, bt ? c->vs.repx : nullptr,
-                                         bt ? c->vs.nreps : nullptr, c->vs.RM, rows_dev, arena.ids(), d_outoff, d_outn,
-                                         d_cvar, d_csplit, d_ckeys, d_clb, d_craw));
+                                         bt ? c->vs.nreps : nullptr, c->vs.RM, rows_dev, arena.ids(), d_outoff,
+                                         d_outcap, d_outn, d_cvar, d_csplit, d_ckeys, d_clb, d_craw));
                 std::vector<unsigned long long> kept(nf);
                 flb.resize((size_t)2 * nf);
                 fraw.resize((size_t)2 * nf);
@@ -869,16 +926,81 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 KC_CUDA(c, cudaMemcpyAsync(fraw.data(), d_craw, (size_t)2 * nf * 8, cudaMemcpyDeviceToHost, c->stream));
                 KC_CUDA(c, cudaStreamSynchronize(c->stream));
                 for (int q = 0; q < nf; ++q) fused_row[fi[q]] = q;
+                std::vector<int> second;   // counted filters worth writing: rows q
                 for (int q = 0; q < nf; ++q) {
+                    const int i = fi[q];
                     const int64_t n = list_n(batch[rows[q]].list), m = (int64_t)kept[q];
                     if ((double)m > 0.95 * (double)n) {
-                        arena.release(offs[q], n);
+                        if (offs[q] >= 0) arena.release(offs[q], n);
+                        else {
+                            // a long list that barely shrinks: its descendants skip
+                            // 1, 3, 7, 15 generations of filtering after 1, 2, 3, 4+
+                            // such filters in a row
+                            const int st = std::min(4, kid_fstreak[i] + 1);
+                            kid_fstreak[i] = (int8_t)st;
+                            kid_fwait[i] = (int8_t)((1 << st) - 1);
+                        }
                         continue;
                     }
-                    arena.release(offs[q] + m, n - m);
-                    kid_list[fi[q]] = arena.make(offs[q], m);
-                    filtered += 1;
-                    dropped += n - m;
+                    kid_fstreak[i] = 0;
+                    if (offs[q] >= 0) {
+                        arena.release(offs[q] + m, n - m);
+                        kid_list[i] = arena.make(offs[q], m);
+                        filtered += 1;
+                        dropped += n - m;
+                    } else {
+                        second.push_back(q);
+                    }
+                }
+                if (!second.empty()) {
+                    // write the counted filters' survivors (same decisions as the
+                    // counting pass; each region holds exactly its count)
+                    std::vector<int> rows2, q2;
+                    std::vector<int64_t> offs2, caps2;
+                    std::vector<float> bdn2;
+                    for (int q : second) {
+                        const int64_t m = (int64_t)kept[q];
+                        const int64_t off = arena.alloc(m);
+                        if (off < 0) continue;   // no room: the children keep the parent's list
+                        q2.push_back(q);
+                        rows2.push_back(rows[q]);
+                        offs2.push_back(off);
+                        caps2.push_back(m);
+                        bdn2.push_back(bdn[q]);
+                    }
+                    const int n2 = (int)q2.size();
+                    if (n2 > 0) {
+                        for (int t = 0; t < n2; ++t) {
+                            std::memcpy(&h_llo[(size_t)t * KD], h_lo2 + (size_t)rows2[t] * KD, KD * sizeof(T));
+                            std::memcpy(&h_lhi[(size_t)t * KD], h_hi2 + (size_t)rows2[t] * KD, KD * sizeof(T));
+                        }
+                        KC_CUDA(c, cudaMemcpyAsync(d_llo, h_llo.data(), (size_t)n2 * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+                        KC_CUDA(c, cudaMemcpyAsync(d_lhi, h_lhi.data(), (size_t)n2 * KD * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+                        KC_CUDA(c, cudaMemcpyAsync(d_beta, bdn2.data(), (size_t)n2 * 4, cudaMemcpyHostToDevice, c->stream));
+                        KC_CUDA(c, cudaMemcpyAsync(d_outoff, offs2.data(), (size_t)n2 * 8, cudaMemcpyHostToDevice, c->stream));
+                        KC_CUDA(c, cudaMemcpyAsync(d_outcap, caps2.data(), (size_t)n2 * 8, cudaMemcpyHostToDevice, c->stream));
+                        ListBatch L2;
+                        const int *rows2_dev = nullptr;
+                        KC_TRY(make_lb(3, n2, [&](int t) { return batch[rows2[t]].list; }, rows2.data(), &L2, &rows2_dev));
+                        KC_TRY(launch_seg_filter(c, L2, d_llo, d_lhi, n2, d_beta, alpha, bt ? c->vs.repx : nullptr,
+                                                 bt ? c->vs.nreps : nullptr, c->vs.RM, rows2_dev, arena.ids(), d_outoff,
+                                                 d_outcap, d_outn, nullptr, nullptr, nullptr, nullptr, nullptr));
+                        std::vector<unsigned long long> kept2(n2);
+                        KC_CUDA(c, cudaMemcpyAsync(kept2.data(), d_outn, (size_t)n2 * 8, cudaMemcpyDeviceToHost, c->stream));
+                        KC_CUDA(c, cudaStreamSynchronize(c->stream));
+                        for (int t = 0; t < n2; ++t) {
+                            const int q = q2[t];
+                            const int64_t n = list_n(batch[rows[q]].list), m = (int64_t)kept[q];
+                            if ((int64_t)kept2[t] != m) {
+                                // cannot happen (identical decisions); keep the parent's list
+                                arena.release(offs2[t], m);
+                                continue;
+                            }
+                            kid_list[fi[q]] = arena.make(offs2[t], m);
+                            filtered += 1;
+                            dropped += n - m;
+                        }
+                    }
                 }
             }
         }
@@ -911,6 +1033,8 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 ch.depth = nd.depth + 1;
                 ch.group = ch.depth <= 8 ? ch.id : nd.group;
                 ch.list = kid_list[i];
+                ch.fwait = kid_fwait[i];
+                ch.fstreak = kid_fstreak[i];
                 if (lists) arena.ref(ch.list);
                 kids.push_back(std::move(ch));
                 kid_fused.push_back(fused_row[i] >= 0 ? 2 * fused_row[i] + side : -1);
@@ -1092,10 +1216,14 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             KC_CUDA(c, cudaStreamSynchronize(c->stream));
             prof[4] += now_s() - tA;
             tA = now_s();
-            if (batches % 100 == 0)
-                fprintf(stderr, "[kc_solve] batch %lld visits %lld open %zu alpha %.17g beta %.17g active %lld\n",
-                        (long long)batches, (long long)visits, heap.size(), alpha,
-                        heap.empty() ? alpha : heap.front().key, (long long)(lists ? arena.used : cur.n));
+            if (batches % 100 == 0 || tA - last_trace >= 10.0) {
+                last_trace = tA;
+                const double beta = heap.empty() ? alpha : std::min(heap.front().key, alpha);
+                fprintf(stderr, "[kc_solve] t %.1f s batch %lld visits %lld open %zu alpha %.17g beta %.17g gap %.3e "
+                                "active %lld\n",
+                        tA - t0, (long long)batches, (long long)visits, heap.size(), alpha, beta,
+                        alpha > 0 ? (alpha - beta) / alpha : 0.0, (long long)(lists ? arena.used : cur.n));
+            }
         }
     }
     log_file.reset();

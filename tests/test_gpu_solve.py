@@ -358,6 +358,26 @@ def test_solve_lists_with_a_full_arena():
     assert tight["samples_dropped"] < roomy["samples_dropped"]
 
 
+def test_solve_counted_filters_in_a_small_arena():
+    """With the list arena holding little more than the root list, the
+    longest lists of a batch are filtered in two passes (survivors counted,
+    then written into a region of exactly that size), and filters that drop
+    little make the descendants skip filtering for a few generations.  The
+    certified optimum is the one of a solve with room for every list and of
+    the shared-set mode."""
+    X = synth.make_workload("batched_solve", n=2_000_000)[0]
+    kc = KCenter(_t(X), 3)
+    lim = dict(tol=1e-12, time_limit_s=120.0)
+    tight = kc.solve(lists=1, arena_mb=10, **lim)
+    roomy = kc.solve(lists=1, **lim)
+    shared = kc.solve(lists=0, **lim)
+    kc.close()
+    assert tight["status"] == roomy["status"] == shared["status"] == 0
+    assert tight["objective"] == roomy["objective"] == shared["objective"]
+    assert oracle.objective(X, tight["centers"])[0] == tight["objective"]
+    assert tight["lists_filtered"] > 0 and tight["samples_dropped"] > 0
+
+
 def test_solve_plain_bb_and_no_sample_reduction():
     X = _blobs(800, 2, 3, seed=11, dtype=np.float64)
     for kw in (dict(use_bt=0, i_sr=0), dict(use_bt=1, i_sr=0), dict(use_bt=1, i_sr=1, batch=8)):
