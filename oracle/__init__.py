@@ -108,6 +108,7 @@ def lib():
                 "kco_lower_bound": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P, _P]),
                 "kco_lower_bounds": (_I32, [_P, _I64, _I32, _I32, _P, _P, _I32, _P, _P, _P]),
                 "kco_lower_bounds_par": (_I32, [_P, _I64, _I32, _I32, _P, _P, _I32, _P, _P]),
+                "kco_witness_values": (_I32, [_P, _I64, _I32, _I32, _P, _P, _I64, _P, _P]),
                 "kco_beta_matrix": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
                 "kco_alpha_s": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
                 "kco_objective": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P]),
@@ -326,3 +327,108 @@ def solve(X, k, tol=1e-12, use_bt=True, use_sr=True, i_sr=1, ball_cap=50, is_f32
         "active_final": r.active_final,
         "fft_objective": r.fft_objective,
     }
+
+
+def witness_values(X, lo, hi, wit):
+    """min_k beta_w^k of M nodes (lo, hi of shape (M, K, D)) at their witness
+    samples wit (M,); -1 where wit < 0."""
+    X, lo, hi = _f64(X), _f64(lo), _f64(hi)
+    n, d = X.shape
+    M, k, _ = lo.shape
+    w = np.ascontiguousarray(wit, dtype=np.int64)
+    out = np.empty(M)
+    lib().kco_witness_values(_ptr(X), n, d, k, _ptr(lo), _ptr(hi), M, _ptr(w), _ptr(out))
+    return out
+
+
+def replay(X, records, objective, centers, tol, is_f32=None, rebound_limit=64):
+    """Certificate replay (O5) of a logged branch and bound solve.
+
+    ``records``: the solver's log as parsed JSON objects (an iterable of dicts,
+    or a path to the JSON-lines file): lines with "child" describe a bounded
+    child (parent, key, pruned, witness "w", boxes "lo"/"hi" flattened
+    [K][D]); lines with "id" a branched node (its bound "lb").  Checks:
+      (i)   the objective of ``centers`` over all N samples (Eq. 1, FP64)
+            equals ``objective``;
+      (ii)  every pruned child holds no solution below objective * (1 - tol):
+            its witness sample's closed-form value (Section 3.1) reaches that
+            threshold, which proves beta(M) does; where it does not (or there
+            is no witness), beta(M) is re-evaluated over ALL samples on the
+            host cores (at most ``rebound_limit`` such nodes);
+      (iii) the two children of every branched node partition its boxes:
+            equal except at one coordinate, split into [lo, m] and
+            [succ(m), hi] with succ the next value of the data type
+            (Section 3.3), and each child's key is at least its parent's
+            bound.
+    Returns a dict of counts; ``ok`` is True when every check passed."""
+    import json
+    if is_f32 is None:
+        is_f32 = np.asarray(X).dtype == np.float32
+    if isinstance(records, (str, bytes, os.PathLike)):
+        with open(records) as f:
+            records = [json.loads(line) for line in f]
+    kids = [r for r in records if "child" in r]
+    nodes = {r["id"]: r for r in records if "id" in r}
+    out = {"children": len(kids), "branched": len(nodes)}
+    # (i)
+    obj, _ = objective_fn(X, centers)
+    out["objective_ok"] = obj == objective
+    # (ii)
+    thr = objective - tol * objective
+    pruned = [r for r in kids if r["pruned"]]
+    out["pruned"] = len(pruned)
+    ok_prune = True
+    n_rebound = 0
+    if pruned:
+        nd = np.asarray(X).shape[1]
+        lo = np.array([r["lo"] for r in pruned], dtype=np.float64)
+        hi = np.array([r["hi"] for r in pruned], dtype=np.float64)
+        k = lo.shape[1] // nd
+        lo = lo.reshape(len(pruned), k, nd)
+        hi = hi.reshape(len(pruned), k, nd)
+        wit = np.array([r.get("w", -1) for r in pruned], dtype=np.int64)
+        v = witness_values(X, lo, hi, wit)
+        bad = np.flatnonzero(~(v >= thr))
+        out["witness_proved"] = int(len(pruned) - len(bad))
+        n_rebound = len(bad)
+        if n_rebound > rebound_limit:
+            ok_prune = False
+        elif n_rebound:
+            beta, _, _ = lower_bounds_par(X, lo[bad], hi[bad])
+            ok_prune = bool(np.all(beta >= thr))
+    out["rebound"] = n_rebound
+    out["prunes_ok"] = ok_prune
+    # (iii)
+    dt = np.float32 if is_f32 else np.float64
+    by_parent = {}
+    for r in kids:
+        by_parent.setdefault(r["parent"], []).append(r)
+    part_ok = True
+    for pid, pair in by_parent.items():
+        if len(pair) != 2:
+            part_ok = False
+            break
+        c0, c1 = sorted(pair, key=lambda r: r["child"])
+        lo0, hi0 = np.array(c0["lo"], dt), np.array(c0["hi"], dt)
+        lo1, hi1 = np.array(c1["lo"], dt), np.array(c1["hi"], dt)
+        split = np.flatnonzero((lo0 != lo1) | (hi0 != hi1))
+        if len(split) != 1:
+            part_ok = False
+            break
+        i = split[0]
+        if not (lo0[i] <= hi0[i] < lo1[i] <= hi1[i] and lo1[i] == np.nextafter(hi0[i], dt(np.inf))):
+            part_ok = False
+            break
+        if not (np.array_equal(np.delete(lo0, i), np.delete(lo1, i)) and
+                np.array_equal(np.delete(hi0, i), np.delete(hi1, i))):
+            part_ok = False
+            break
+        if pid in nodes and min(c0["key"], c1["key"]) < nodes[pid]["lb"]:
+            part_ok = False
+            break
+    out["partition_ok"] = part_ok
+    out["ok"] = bool(out["objective_ok"] and ok_prune and part_ok)
+    return out
+
+
+objective_fn = objective

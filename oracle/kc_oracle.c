@@ -192,6 +192,28 @@ int kco_lower_bounds_par(const double *X, int64_t N, int D, int K, const double 
     return nt;
 }
 
+/* Certificate replay (O5), pruned nodes: for node m with boxes lo/hi + m*K*D
+ * and witness sample wit[m], out[m] = min_k beta_{wit}^k(M^k), the closed
+ * form of Section 3.1 at that one sample.  beta(M) is a maximum over samples,
+ * so beta(M) >= out[m]: out[m] >= threshold proves that the node holds no
+ * solution below the threshold without evaluating the other samples.
+ * out[m] = -1 when wit[m] < 0 (no witness). */
+int kco_witness_values(const double *X, int64_t N, int D, int K, const double *lo, const double *hi, int64_t M,
+                       const int64_t *wit, double *out)
+{
+    for (int64_t m = 0; m < M; ++m) {
+        if (wit[m] < 0 || wit[m] >= N) { out[m] = -1.0; continue; }
+        const double *x = X + wit[m] * D;
+        double v = INFINITY;
+        for (int k = 0; k < K; ++k) {
+            double b = kco_beta_sk(x, lo + (m * K + k) * D, hi + (m * K + k) * D, D);
+            if (b < v) v = b;
+        }
+        out[m] = v;
+    }
+    return 0;
+}
+
 /* The matrix beta_s^k (N x K, row major): test helper for the closed form. */
 int kco_beta_matrix(const double *X, int64_t N, int D, int K, const double *lo, const double *hi,
                     double *out)

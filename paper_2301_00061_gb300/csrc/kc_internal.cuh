@@ -294,15 +294,17 @@ int list_tile();
 kc_status launch_iota(kc_ctx *c, uint32_t *p, int64_t n);
 kc_status launch_seg_lb(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, unsigned long long *keys,
                         double *lb, double *raw, int64_t *arg);
+// wit (nullable, device [B]): the sample attaining each refined value (wid:
+// device scratch [B]), found by a second pass over the lists.
 kc_status launch_seg_refine(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, const double *raw_host,
-                            float *thr_dev, unsigned long long *vmax, double *out);
+                            float *thr_dev, unsigned long long *vmax, double *out, unsigned *wid, int64_t *wit);
 kc_status launch_seg_objective(kc_ctx *c, const ListBatch &L, const int64_t *centers, int B, double alpha_cut,
                                unsigned long long *keys, unsigned long long *vmax, float *thr, double *val);
 kc_status launch_seg_filter(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B,
                             const float *beta_dn_dev, double alpha, const void *repx, const int *nreps, int RM,
                             const int *rmap, uint32_t *out_pool, const int64_t *out_off, const int64_t *out_cap,
                             unsigned long long *out_n, const int *cvar, const float *csplit,
-                            unsigned long long *ckeys, double *child_lb, double *child_raw);
+                            unsigned long long *ckeys, double *child_lb, double *child_raw, int64_t *child_arg);
 // Tightening of B nodes, each over its own list (float data).
 kc_status launch_tighten_list(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, double alpha,
                               const int64_t *seeds_dev, int ball_cap, void *lo_out, void *hi_out, int64_t *counts,

@@ -115,8 +115,12 @@ template <int DMAX>
 __global__ void __launch_bounds__(256)
 seg_refine_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float *__restrict__ lo,
                const float *__restrict__ hi, int K, int D, const float *__restrict__ thr,
-               unsigned long long *__restrict__ vmax)
+               unsigned long long *__restrict__ vmax, const unsigned long long *__restrict__ vfound,
+               unsigned *__restrict__ wid)
 {
+    // vfound NULL: the ordered double maximum into vmax; otherwise a second
+    // pass over the same samples: the smallest id whose double value equals
+    // vfound[b] into wid[b] (the sample attaining the refined bound)
     __shared__ uint64_t sbox[kMaxK * DMAX];
     const int Dp = (D + 1) & ~1;
     for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
@@ -155,11 +159,20 @@ seg_refine_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
                     }
                     if (acc < e) e = acc;
                 }
-                atomicMax(&vmax[b], ord_f64(e));
+                if (!vfound) atomicMax(&vmax[b], ord_f64(e));
+                else if (ord_f64(e) == vfound[b]) atomicMin(&wid[b], id);
             }
         }
         __syncthreads();
     }
+}
+
+__global__ void wid_finalize(const unsigned *__restrict__ wid, const unsigned long long *__restrict__ v, int B,
+                             int64_t *__restrict__ wit)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    wit[b] = (v[b] && wid[b] != 0xFFFFFFFFu) ? (int64_t)wid[b] : -1;
 }
 
 // Objective screen: float max over node b's list of min_k ||x - c_k||^2.
@@ -472,7 +485,7 @@ kc_status launch_seg_lb(kc_ctx *c, const ListBatch &L, const void *lo, const voi
 // whose float value is below a threshold derived from raw (with the float and
 // double error bounds) cannot attain the maximum and are skipped.
 kc_status launch_seg_refine(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, const double *raw_host,
-                            float *thr_dev, unsigned long long *vmax, double *out)
+                            float *thr_dev, unsigned long long *vmax, double *out, unsigned *wid, int64_t *wit)
 {
     if (c->D > kListMaxD) return set_err(c, KC_EINVAL, "list kernels: D <= %d (got %d)", kListMaxD, c->D);
     if (B <= 0) return KC_OK;
@@ -490,12 +503,26 @@ kc_status launch_seg_refine(kc_ctx *c, const ListBatch &L, const void *lo, const
         const int g = grid_items(c, L.W);
         seg_refine_f32<8><<<g, 256, 0, c->stream>>>(static_cast<const float *>(c->X), c->ldx, L,
                                                     static_cast<const float *>(lo), static_cast<const float *>(hi),
-                                                    c->K, c->D, thr_dev, vmax);
+                                                    c->K, c->D, thr_dev, vmax, nullptr, nullptr);
         KC_TRY(after_launch(c, "list refinement"));
     }
     vmax_finalize<<<(B + 127) / 128, 128, 0, c->stream>>>(vmax, B, deflate_factor(KC_F64, c->D),
                                                           underflow_slack(KC_F64, c->D), out, nullptr);
-    return after_launch(c, "list refinement finalize");
+    KC_TRY(after_launch(c, "list refinement finalize"));
+    if (wit) {
+        // the sample attaining each refined value (a second pass over the lists)
+        KC_CUDA(c, cudaMemsetAsync(wid, 0xFF, (size_t)B * 4, c->stream));
+        if (L.W > 0) {
+            const int g = grid_items(c, L.W);
+            seg_refine_f32<8><<<g, 256, 0, c->stream>>>(static_cast<const float *>(c->X), c->ldx, L,
+                                                        static_cast<const float *>(lo), static_cast<const float *>(hi),
+                                                        c->K, c->D, thr_dev, nullptr, vmax, wid);
+            KC_TRY(after_launch(c, "list refinement witness"));
+        }
+        wid_finalize<<<(B + 127) / 128, 128, 0, c->stream>>>(wid, vmax, B, wit);
+        KC_TRY(after_launch(c, "list refinement witness finalize"));
+    }
+    return KC_OK;
 }
 
 // Objective of B candidate sets (centers [B][K] ids, device), each over its own
@@ -529,7 +556,7 @@ kc_status launch_seg_filter(kc_ctx *c, const ListBatch &L, const void *lo, const
                             const float *beta_dn_dev, double alpha, const void *repx, const int *nreps, int RM,
                             const int *rmap, uint32_t *out_pool, const int64_t *out_off, const int64_t *out_cap,
                             unsigned long long *out_n, const int *cvar, const float *csplit,
-                            unsigned long long *ckeys, double *child_lb, double *child_raw)
+                            unsigned long long *ckeys, double *child_lb, double *child_raw, int64_t *child_arg)
 {
     if (c->D > kListMaxD) return set_err(c, KC_EINVAL, "list kernels: D <= %d (got %d)", kListMaxD, c->D);
     if (B <= 0) return KC_OK;
@@ -555,7 +582,7 @@ kc_status launch_seg_filter(kc_ctx *c, const ListBatch &L, const void *lo, const
     if (ckeys) {
         keys_finalize<<<(2 * B + 127) / 128, 128, 0, c->stream>>>(ckeys, 2 * B, deflate_factor(KC_F32, c->D),
                                                                   underflow_slack(KC_F32, c->D), child_lb, child_raw,
-                                                                  nullptr);
+                                                                  child_arg);
         KC_TRY(after_launch(c, "list filter: children's bounds"));
     }
     return KC_OK;

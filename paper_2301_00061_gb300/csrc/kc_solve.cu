@@ -74,6 +74,7 @@ struct Node {
     int64_t group = 0;       // its ancestor at depth 8 (itself above that depth)
     float prio = 0.f;        // learned priority (ties of equal keys: smaller first)
     int list = -1;           // handle of its surviving-sample list (per-node list mode)
+    int64_t wit = -1;        // a sample whose distance to the node's boxes attains `key` (-1: none known)
     int8_t fwait = 0;        // generations still to skip list filtering (after filters that dropped little)
     int8_t fstreak = 0;      // consecutive such filters along the path
 };
@@ -397,7 +398,8 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     const size_t e_feat = e_pts + (((size_t)Bmax * D * sizeof(T) + 255) & ~(size_t)255);
     const size_t e_out = e_feat + (size_t)Bmax * 12 * 4, e_lbox = e_out + (size_t)Bmax * 2 * 4 + 256;
     const size_t e_llb = e_lbox + 2 * (size_t)4 * Bmax * KD * sizeof(T), e_raw = e_llb + (size_t)4 * Bmax * 8;
-    const size_t e_ref = e_raw + (size_t)Bmax * 8, extra_bytes = e_ref + (size_t)Bmax * 8 + 256;
+    const size_t e_ref = e_raw + (size_t)Bmax * 8, e_kar = e_ref + (size_t)Bmax * 8, e_rfw = e_kar + (size_t)Bmax * 8;
+    const size_t extra_bytes = e_rfw + (size_t)Bmax * 8 + 256;
     KC_TRY(ensure(c, sb.extra, extra_bytes));
     char *xb = static_cast<char *>(sb.extra.p);
     int64_t *d_arg = reinterpret_cast<int64_t *>(xb + e_arg);
@@ -410,6 +412,8 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     double *d_llb = reinterpret_cast<double *>(xb + e_llb);
     double *d_raw = reinterpret_cast<double *>(xb + e_raw);
     double *d_ref = reinterpret_cast<double *>(xb + e_ref);
+    int64_t *d_kar = reinterpret_cast<int64_t *>(xb + e_kar);   // children's bound witnesses
+    int64_t *d_rfw = reinterpret_cast<int64_t *>(xb + e_rfw);   // refined bounds' witnesses
     std::vector<int64_t> h_arg(Bmax), h_cnt((size_t)Bmax * K);
     std::vector<T> h_pts((size_t)Bmax * D);
     std::vector<float> h_feat((size_t)Bmax * 12), h_out((size_t)Bmax * 2);
@@ -417,6 +421,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     std::vector<double> h_ub(Bmax);
 
     std::vector<double> h_raw(Bmax), h_ref(Bmax);
+    std::vector<int64_t> h_refw(Bmax), h_kar(Bmax);
     // Float data: a bound whose float value cannot decide the prune (its
     // certified value is below the threshold, the float value plus its error
     // bound is not) is re-evaluated in double over the same samples (the
@@ -440,13 +445,16 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     const size_t l_off = l_beta + (size_t)Bmax * 4, l_cap = l_off + (size_t)Bmax * 8, l_n = l_cap + (size_t)Bmax * 8;
     const size_t l_cvar = l_n + (size_t)Bmax * 8, l_csplit = l_cvar + (size_t)Bmax * 4;
     const size_t l_ckeys = l_csplit + (size_t)2 * Bmax * 4, l_clb = l_ckeys + (size_t)2 * Bmax * 8;
-    const size_t l_craw = l_clb + (size_t)2 * Bmax * 8;
-    const size_t l_end = l_craw + (size_t)2 * Bmax * 8 + 256;
+    const size_t l_craw = l_clb + (size_t)2 * Bmax * 8, l_carg = l_craw + (size_t)2 * Bmax * 8;
+    const size_t l_wid = l_carg + (size_t)2 * Bmax * 8;
+    const size_t l_end = l_wid + (size_t)Bmax * 4 + 256;
     unsigned long long *d_keys = nullptr, *d_vmax = nullptr, *d_outn = nullptr, *d_ckeys = nullptr;
     float *d_thr = nullptr, *d_beta = nullptr, *d_csplit = nullptr;
     int64_t *d_outoff = nullptr, *d_outcap = nullptr;
     int *d_cvar = nullptr;
     double *d_clb = nullptr, *d_craw = nullptr;
+    int64_t *d_carg = nullptr;
+    unsigned *d_wid = nullptr;
     int root_list = -1;
     if (lists) {
         KC_TRY(ensure(c, sb.lists, l_end));
@@ -463,6 +471,8 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         d_ckeys = reinterpret_cast<unsigned long long *>(lb + l_ckeys);
         d_clb = reinterpret_cast<double *>(lb + l_clb);
         d_craw = reinterpret_cast<double *>(lb + l_craw);
+        d_carg = reinterpret_cast<int64_t *>(lb + l_carg);
+        d_wid = reinterpret_cast<unsigned *>(lb + l_wid);
         if (cudaMallocHost(&sb.lpin, (size_t)kSlots * slot_bytes) != cudaSuccess) {
             sb.lpin = nullptr;
             cudaGetLastError();
@@ -536,11 +546,12 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         if (list_of) {
             ListBatch L;
             KC_TRY(make_lb(slot, n, [&](int i) { return (*list_of)(amb[i]); }, nullptr, &L, nullptr));
-            KC_TRY(launch_seg_refine(c, L, d_llo, d_lhi, n, amb_raw.data(), d_thr, d_vmax, d_ref));
+            KC_TRY(launch_seg_refine(c, L, d_llo, d_lhi, n, amb_raw.data(), d_thr, d_vmax, d_ref, d_wid, d_rfw));
         } else {
-            KC_TRY(launch_lower_bounds_refine(c, vw, d_llo, d_lhi, n, amb_raw.data(), d_ref, nullptr, nullptr));
+            KC_TRY(launch_lower_bounds_refine(c, vw, d_llo, d_lhi, n, amb_raw.data(), d_ref, nullptr, d_rfw));
         }
         KC_CUDA(c, cudaMemcpyAsync(h_ref.data(), d_ref, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaMemcpyAsync(h_refw.data(), d_rfw, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
         KC_CUDA(c, cudaStreamSynchronize(c->stream));
         return KC_OK;
     };
@@ -637,12 +648,19 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         amb.clear();
         for (int b = 0; b < Bp; ++b) {
             h_ub[b] = __builtin_huge_val();
-            batch[b].key = std::max(h_lb[b], batch[b].key);
+            if (h_lb[b] > batch[b].key) {
+                batch[b].key = h_lb[b];
+                batch[b].wit = h_arg[b];
+            }
             if (h_st[b] != 1 && ambiguous(batch[b].key, h_raw[b])) amb.push_back(b);
         }
         if (!amb.empty()) {
             KC_TRY(refine_nodes(cur, h_lo, h_hi, h_raw.data(), lists ? &batch_list : nullptr, 1));
-            for (size_t i = 0; i < amb.size(); ++i) batch[amb[i]].key = std::max(batch[amb[i]].key, h_ref[i]);
+            for (size_t i = 0; i < amb.size(); ++i)
+                if (h_ref[i] > batch[amb[i]].key) {
+                    batch[amb[i]].key = h_ref[i];
+                    batch[amb[i]].wit = h_refw[i];
+                }
             refined += (int64_t)amb.size();
         }
         for (int b = 0; b < Bp; ++b) {
@@ -831,6 +849,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         std::vector<int> kid_list(NB, -1), fused_row(NB, -1);
         std::vector<int8_t> kid_fwait(NB, 0), kid_fstreak(NB, 0);
         std::vector<double> flb, fraw;
+        std::vector<int64_t> farg;
         if (lists && NB > 0 && o.i_sr > 0 && batches % o.i_sr == 0) {
             std::vector<int> fi, rows, cand;
             std::vector<int64_t> offs, caps;
@@ -917,13 +936,15 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 const bool bt = o.use_bt != 0;
                 KC_TRY(launch_seg_filter(c, Lf, d_llo, d_lhi, nf, d_beta, alpha, bt ? c->vs.repx : nullptr,
                                          bt ? c->vs.nreps : nullptr, c->vs.RM, rows_dev, arena.ids(), d_outoff,
-                                         d_outcap, d_outn, d_cvar, d_csplit, d_ckeys, d_clb, d_craw));
+                                         d_outcap, d_outn, d_cvar, d_csplit, d_ckeys, d_clb, d_craw, d_carg));
                 std::vector<unsigned long long> kept(nf);
                 flb.resize((size_t)2 * nf);
                 fraw.resize((size_t)2 * nf);
+                farg.resize((size_t)2 * nf);
                 KC_CUDA(c, cudaMemcpyAsync(kept.data(), d_outn, (size_t)nf * 8, cudaMemcpyDeviceToHost, c->stream));
                 KC_CUDA(c, cudaMemcpyAsync(flb.data(), d_clb, (size_t)2 * nf * 8, cudaMemcpyDeviceToHost, c->stream));
                 KC_CUDA(c, cudaMemcpyAsync(fraw.data(), d_craw, (size_t)2 * nf * 8, cudaMemcpyDeviceToHost, c->stream));
+                KC_CUDA(c, cudaMemcpyAsync(farg.data(), d_carg, (size_t)2 * nf * 8, cudaMemcpyDeviceToHost, c->stream));
                 KC_CUDA(c, cudaStreamSynchronize(c->stream));
                 for (int q = 0; q < nf; ++q) fused_row[fi[q]] = q;
                 std::vector<int> second;   // counted filters worth writing: rows q
@@ -984,7 +1005,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                         KC_TRY(make_lb(3, n2, [&](int t) { return batch[rows2[t]].list; }, rows2.data(), &L2, &rows2_dev));
                         KC_TRY(launch_seg_filter(c, L2, d_llo, d_lhi, n2, d_beta, alpha, bt ? c->vs.repx : nullptr,
                                                  bt ? c->vs.nreps : nullptr, c->vs.RM, rows2_dev, arena.ids(), d_outoff,
-                                                 d_outcap, d_outn, nullptr, nullptr, nullptr, nullptr, nullptr));
+                                                 d_outcap, d_outn, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr));
                         std::vector<unsigned long long> kept2(n2);
                         KC_CUDA(c, cudaMemcpyAsync(kept2.data(), d_outn, (size_t)n2 * 8, cudaMemcpyDeviceToHost, c->stream));
                         KC_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1027,6 +1048,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 else ch.lo[bi] = succ;
                 ch.key = nd.key;
                 ch.pkey = nd.key;
+                ch.wit = nd.wit;   // the parent's witness is at least as far from the child's smaller boxes
                 ch.prio = prio[i];
                 ch.id = next_id++;
                 ch.parent = nd.id;
@@ -1043,6 +1065,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         // bound the children as they are created (Algorithm 1, Bounding); only
         // those below the incumbent enter the open set
         std::vector<double> klb((size_t)Bmax), kraw((size_t)Bmax);
+        std::vector<int64_t> kwit((size_t)Bmax);
         for (size_t k0 = 0; k0 < kids.size(); k0 += (size_t)Bmax) {
             const int nk = (int)std::min(kids.size() - k0, (size_t)Bmax);
             for (int q = 0; q < nk; ++q) {
@@ -1058,6 +1081,7 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 if (f >= 0) {
                     klb[q] = flb[f];
                     kraw[q] = fraw[f];
+                    kwit[q] = farg[f];
                 } else {
                     sub.push_back(q);
                 }
@@ -1073,27 +1097,35 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 if (lists) {
                     ListBatch Lk;
                     KC_TRY(make_lb(4, ns, [&](int t) { return kids[k0 + sub[t]].list; }, nullptr, &Lk, nullptr, true));
-                    KC_TRY(launch_seg_lb(c, Lk, d_lo, d_hi, ns, d_keys, d_lb, d_raw, nullptr));
+                    KC_TRY(launch_seg_lb(c, Lk, d_lo, d_hi, ns, d_keys, d_lb, d_raw, d_kar));
                 } else {
-                    KC_TRY(launch_lower_bounds_view(c, cur, d_lo, d_hi, ns, d_lb, d_raw, nullptr, 0));
+                    KC_TRY(launch_lower_bounds_view(c, cur, d_lo, d_hi, ns, d_lb, d_raw, d_kar, 0));
                 }
                 KC_CUDA(c, cudaMemcpyAsync(h_lb, d_lb, (size_t)ns * 8, cudaMemcpyDeviceToHost, c->stream));
                 KC_CUDA(c, cudaMemcpyAsync(h_raw.data(), d_raw, (size_t)ns * 8, cudaMemcpyDeviceToHost, c->stream));
+                KC_CUDA(c, cudaMemcpyAsync(h_kar.data(), d_kar, (size_t)ns * 8, cudaMemcpyDeviceToHost, c->stream));
                 KC_CUDA(c, cudaStreamSynchronize(c->stream));
                 for (int t = 0; t < ns; ++t) {
                     klb[sub[t]] = h_lb[t];
                     kraw[sub[t]] = h_raw[t];
+                    kwit[sub[t]] = h_kar[t];
                 }
             }
             amb.clear();
             for (int q = 0; q < nk; ++q) {
-                kids[k0 + q].key = std::max(kids[k0 + q].key, klb[q]);
+                if (klb[q] > kids[k0 + q].key) {
+                    kids[k0 + q].key = klb[q];
+                    kids[k0 + q].wit = kwit[q];
+                }
                 if (ambiguous(kids[k0 + q].key, kraw[q])) amb.push_back(q);
             }
             if (!amb.empty()) {
                 KC_TRY(refine_nodes(cur, h_lo, h_hi, kraw.data(), lists ? &kid_of : nullptr, 5));
                 for (size_t i = 0; i < amb.size(); ++i)
-                    kids[k0 + amb[i]].key = std::max(kids[k0 + amb[i]].key, h_ref[i]);
+                    if (h_ref[i] > kids[k0 + amb[i]].key) {
+                        kids[k0 + amb[i]].key = h_ref[i];
+                        kids[k0 + amb[i]].wit = h_refw[i];
+                    }
                 refined += (int64_t)amb.size();
             }
             for (int q = 0; q < nk; ++q) {
@@ -1102,11 +1134,14 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 if (log) {
                     // every bounded child: its boxes and certified bound, for
                     // checking bounds and prunes against a double evaluation
-                    fprintf(log, "{\"child\":%lld,\"parent\":%lld,\"key\":%.17g,\"pruned\":%d,\"lo\":[",
-                            (long long)ch.id, (long long)ch.parent, ch.key, ch.key >= prune_threshold() ? 1 : 0);
-                    for (int i = 0; i < KD; ++i) fprintf(log, i ? ",%.9g" : "%.9g", (double)ch.lo[i]);
+                    fprintf(log, "{\"child\":%lld,\"parent\":%lld,\"key\":%.17g,\"pruned\":%d,\"w\":%lld,\"lo\":[",
+                            (long long)ch.id, (long long)ch.parent, ch.key, ch.key >= prune_threshold() ? 1 : 0,
+                            (long long)ch.wit);
+                    // 9 significant digits round-trip a float, 17 a double
+                    const char *f0 = sizeof(T) == 4 ? "%.9g" : "%.17g", *f1 = sizeof(T) == 4 ? ",%.9g" : ",%.17g";
+                    for (int i = 0; i < KD; ++i) fprintf(log, i ? f1 : f0, (double)ch.lo[i]);
                     fprintf(log, "],\"hi\":[");
-                    for (int i = 0; i < KD; ++i) fprintf(log, i ? ",%.9g" : "%.9g", (double)ch.hi[i]);
+                    for (int i = 0; i < KD; ++i) fprintf(log, i ? f1 : f0, (double)ch.hi[i]);
                     fprintf(log, "]}\n");
                 }
                 if (ch.key >= prune_threshold()) {

@@ -473,6 +473,10 @@ def test_full_size_bounds_and_prunes_replayed(tmp_path):
             assert np.array_equal(np.delete(lo0, i), np.delete(lo1, i)) and np.array_equal(np.delete(hi0, i), np.delete(hi1, i))
             if pid in nodes:
                 assert min(c0["key"], c1["key"]) >= nodes[pid]["lb"], (name, pid)
+        rep = oracle.replay(X, str(log), g["objective"], g["centers"], 1e-12)
+        # prunes are taken against the incumbent of their time, never below
+        # the final objective: sound against it in a stopped solve too
+        assert rep["ok"] and rep["rebound"] == 0, rep
         for r in sample:
             lo = np.array(r["lo"], np.float32).reshape(w.k, w.d)
             hi = np.array(r["hi"], np.float32).reshape(w.k, w.d)
@@ -480,6 +484,26 @@ def test_full_size_bounds_and_prunes_replayed(tmp_path):
             assert r["key"] <= beta and r["key"] >= beta * (1 - 1e-6), (name, r["child"], r["key"], beta)
             if r["pruned"]:
                 assert beta >= alpha * (1 - 1e-12), (name, r["child"], beta, alpha)
+
+
+def test_certificate_replay_at_one_hundred_million_samples(tmp_path):
+    """The learned-order recipe at its full size (N = 1e8, D = 2, K = 4,
+    4 blobs + 1 % outliers) solved to the 1e-12 certificate with every bounded
+    child logged, then replayed by the oracle (O5): the FP64 objective of the
+    returned centers over all 1e8 samples equals the reported one; EVERY
+    pruned child is proved prunable (its logged witness sample's closed-form
+    value reaches objective * (1 - 1e-12), else a re-bound over all samples);
+    every branched node's children partition its boxes."""
+    X, w = synth.make_workload("learned_order")
+    kc = KCenter(_t(X), w.k)
+    log = tmp_path / "c4.jsonl"
+    g = kc.solve(tol=1e-12, log_path=str(log))
+    kc.close()
+    assert g["status"] == 0
+    r = oracle.replay(X, str(log), g["objective"], g["centers"], 1e-12)
+    print(r)
+    assert r["ok"], r
+    assert r["pruned"] > 10_000 and r["witness_proved"] >= r["pruned"] - r["rebound"]
 
 
 def test_solve_degenerate_and_edge_inputs():
