@@ -379,10 +379,13 @@ def replay(X, records, objective, centers, tol, is_f32=None, rebound_limit=64):
     out["pruned"] = len(pruned)
     ok_prune = True
     n_rebound = 0
+    dt = np.float32 if is_f32 else np.float64
     if pruned:
         nd = np.asarray(X).shape[1]
-        lo = np.array([r["lo"] for r in pruned], dtype=np.float64)
-        hi = np.array([r["hi"] for r in pruned], dtype=np.float64)
+        # the log prints boxes with just enough digits to name their values in
+        # the data's type: parse them in that type, then promote exactly
+        lo = np.array([r["lo"] for r in pruned], dtype=dt).astype(np.float64)
+        hi = np.array([r["hi"] for r in pruned], dtype=dt).astype(np.float64)
         k = lo.shape[1] // nd
         lo = lo.reshape(len(pruned), k, nd)
         hi = hi.reshape(len(pruned), k, nd)
@@ -399,7 +402,6 @@ def replay(X, records, objective, centers, tol, is_f32=None, rebound_limit=64):
     out["rebound"] = n_rebound
     out["prunes_ok"] = ok_prune
     # (iii)
-    dt = np.float32 if is_f32 else np.float64
     by_parent = {}
     for r in kids:
         by_parent.setdefault(r["parent"], []).append(r)

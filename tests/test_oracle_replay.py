@@ -107,3 +107,25 @@ def test_witness_values_are_the_closed_form_at_the_witness():
         assert v == min(oracle.beta_sk(X[w], lo[0, 0], hi[0, 0]), oracle.beta_sk(X[w], lo[0, 1], hi[0, 1]))
         assert v <= oracle.lower_bound(X, lo[0], hi[0])[0]
     assert oracle.witness_values(X, lo, hi, np.array([-1]))[0] == -1.0
+
+
+def test_replay_reads_float_boxes_in_float():
+    """Boxes of float data are logged with 9 significant digits (enough to
+    name a float exactly, not a double): the replay must parse them as floats.
+    A prune whose bound equals the threshold only at the float bounds is
+    accepted."""
+    # sample 0 lies right of box 0, whose upper end 7.395677089691162f prints
+    # as 7.39567709: read as a double that end moves right and the distance
+    # shrinks below the bound
+    X = np.array([[20.0, 3.0], [7.395677089691162, 3.0], [-20.0, -20.0]], np.float32)
+    lo = np.array([[[7.395677089691162, 3.0], [-20.0, -20.0]]], np.float32)
+    hi = lo.copy()
+    beta, arg = oracle.lower_bound(X, lo[0], hi[0])
+    assert arg == 0
+    fmt = lambda a: [float("%.9g" % v) for v in a.ravel()]   # noqa: E731
+    recs = [{"id": 1, "lb": 0.0},
+            {"child": 2, "parent": 1, "key": beta, "pruned": 1, "w": 0, "lo": fmt(lo), "hi": fmt(hi)},
+            {"child": 3, "parent": 1, "key": 0.0, "pruned": 0, "w": 0,
+             "lo": fmt(lo), "hi": fmt(np.nextafter(hi, np.float32(np.inf)))}]
+    r = oracle.replay(X, recs, beta, np.array([1, 2]), tol=0.0, is_f32=True, rebound_limit=0)
+    assert r["pruned"] == 1 and r["witness_proved"] == 1 and r["prunes_ok"]
