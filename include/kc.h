@@ -267,11 +267,12 @@ kc_status kc_fp32_probe(int32_t mode, void *stream, double *lane_ops_per_s, floa
  *   lb_out          [B] double certified lower bound of the input boxes, or NULL.
  *   status          [B] int8: 0 feasible, 1 proved to hold no solution of
  *                   value <= alpha, 2 leaf (every tightened box is a point).
- * ball_cap <= 0 selects the default of 50.
- * Shapes: float data K <= 4 with D <= 4, or K <= 2 with D <= 8; double data
- * K <= 4 with D <= 4 (the kernels keep a node's boxes in registers and
- * per-warp shared memory sized at compile time).  Other shapes return
- * KC_EINVAL.
+ * ball_cap <= 0 selects the default of 50; at most min(ball_cap, 2D + 1, 50)
+ * representatives are used (the cap binds from D = 25 on).
+ * Shapes: float data any K <= 16 and D <= 64 (K <= 4 with D <= 4 and K <= 2
+ * with D <= 8 run kernels with the node's state in registers, compiled per
+ * shape; the others kernels whose node state lives in shared memory sized at
+ * launch); double data K <= 4 with D <= 4.  Other shapes return KC_EINVAL.
  */
 kc_status kc_tighten(kc_ctx *ctx, const void *lo, const void *hi, int32_t B, double alpha,
                      const int64_t *seeds, int32_t ball_cap, void *lo_out, void *hi_out,
@@ -395,8 +396,9 @@ void kc_solve_defaults(kc_solve_opts *opt);
  * overrides opt->tol when >= 0.  Returns KC_OK at optimality within tol,
  * KC_ETIMEOUT / KC_ELIMIT (with *out filled) at a limit, KC_EINVAL for
  * options out of range, KC_ENOMEM when the list arena or buffers do not fit.
- * Shapes: those of kc_tighten (float K <= 4 with D <= 4, or K <= 2 with
- * D <= 8; double K <= 4 with D <= 4); other shapes return KC_EINVAL.
+ * Shapes: those of kc_tighten (float K <= 16, D <= 64; double K <= 4 with
+ * D <= 4); other shapes return KC_EINVAL.  Float data with D > 8 scan one
+ * shared sample set (no per-node lists) without sample reduction.
  */
 kc_status kc_solve(kc_ctx *ctx, double tol, const kc_solve_opts *opt, kc_result *out);
 

@@ -150,6 +150,17 @@ inline View full_view(const kc_ctx *c)
     return v;
 }
 
+// Thresholds of the float proofs in the tightening kernels: a distance d
+// evaluated as d' satisfies d' (1 - g) <= d <= d' / (1 - g).
+struct Margins {
+    float defl, infl, slack;     // float evaluation of a D-term distance
+    float alpha_up, four_up;     // alpha and 4 alpha rounded up to float
+    float beta_dn;               // beta_glob rounded down to float
+    // single-compare proofs: a float distance d' > t_alpha proves d > alpha,
+    // d' > t_four proves d > 4 alpha (t = RU((RU(target) + slack) / defl * (1 + 1e-6)))
+    float t_alpha, t_four;
+};
+
 // Per-node sample-id lists of a batch of nodes (device arrays).  Nodes that
 // share one list form a group: group g's list is pool[seg_off[g] ..
 // seg_off[g] + seg_n[g]) and its nodes are node_start[g] .. node_start[g + 1]
@@ -209,6 +220,17 @@ kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const vo
 kc_status launch_sample_reduction_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int M,
                                        const void *repx, const int *nreps, int R, double beta_glob, double alpha,
                                        uint8_t *mask, unsigned long long *n_active);
+
+// Passes A and B of the float tightening for any K <= 16, D <= 64 (kc_wide.cu;
+// the workspace and finalize kernels are kc_visit.cu's).
+kc_status launch_wide_a(kc_ctx *c, const View &v, const ListBatch *L, const float *lo, const float *hi, int B,
+                        const Margins &mg, unsigned long long *lbkey, unsigned long long *amax,
+                        unsigned long long *amin, unsigned *flags);
+kc_status launch_wide_b(kc_ctx *c, const View &v, const ListBatch *L, const float *lo, const float *hi, int B,
+                        const Margins &mg, const float *blo, const float *bhi, const float *repx, const int *nreps,
+                        const int *allhave, const int64_t *seeds, int RM, unsigned long long *cnt,
+                        unsigned long long *cand, unsigned *smax, unsigned *smin, unsigned *jmax, unsigned *jmin,
+                        unsigned *flags);
 
 // Coordinates of representative ids [M][K][R] (-1 = unused) -> repx, nreps.
 kc_status launch_gather_reps(kc_ctx *c, int M, int R, const int64_t *reps, void *repx, int *nreps);

@@ -436,7 +436,9 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
     int64_t refined = 0, filtered = 0, dropped = 0;
 
     // ---- per-node surviving-sample lists (float data)
-    const bool lists = o.lists != 0 && c->dt == KC_F32;
+    // per-node lists: float data with D <= 8 (the list kernels' register
+    // tiles); wider data scan one shared sample set
+    const bool lists = o.lists != 0 && c->dt == KC_F32 && c->D <= 8;
     const int LT = list_tile();
     const size_t slot_bytes = ((size_t)3 * (Bmax + 1) * 8 + (size_t)(2 * Bmax + 1) * 4 + 255) & ~(size_t)255;
     const int kSlots = 6;   // batch, its refinement, upper bounds, filter, children, their refinement
@@ -1158,7 +1160,8 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
 
         if (o.verbose) { prof[3] += now_s() - tA; tA = now_s(); }
         // 5. sample reduction against the hull of the open nodes (Algorithm 5)
-        if (!lists && o.i_sr > 0 && batches % o.i_sr == 0 && !heap.empty() && heap.front().key < prune_threshold()) {
+        if (!lists && o.i_sr > 0 && c->D <= 8 && batches % o.i_sr == 0 && !heap.empty() &&
+            heap.front().key < prune_threshold()) {
             // one hull box per group of open nodes (a group = the descendants of
             // one node at depth 8): every node's box lies inside its group's
             // hull, so redundancy against the hulls implies it against the nodes

@@ -180,14 +180,6 @@ __device__ __forceinline__ bool proved_lt(float dhat, float infl, float slack, f
     return __fadd_ru(__fmul_ru(dhat, infl), slack) < t_dn;
 }
 
-struct Margins {
-    float defl, infl, slack;     // float evaluation of a D-term distance
-    float alpha_up, four_up;     // alpha and 4 alpha rounded up to float
-    float beta_dn;               // beta_glob rounded down to float
-    // single-compare proofs: a float distance d' > t_alpha proves d > alpha,
-    // d' > t_four proves d > 4 alpha (t = RU((RU(target) + slack) / defl * (1 + 1e-6)))
-    float t_alpha, t_four;
-};
 
 // ------------------------------------------------------------ pass A
 //
@@ -1141,6 +1133,81 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     return KC_OK;
 }
 
+// The wide path (float data, K <= 16, D <= 64): the workspace, finalize
+// kernels and outputs of tighten_impl, passes A and B from kc_wide.cu, and
+// min(ball_cap, 2D + 1, 50) representatives per cluster.
+kc_status tighten_wide(kc_ctx *c, const View &v, const void *lo_, const void *hi_, int B, double alpha,
+                       const int64_t *seeds, int cap, void *lo_out_, void *hi_out_, int64_t *counts, int64_t *cand_out,
+                       double *lb, double *lb_raw, int64_t *lbarg, int8_t *status, VisitScratch *vs,
+                       const ListBatch *L = nullptr)
+{
+    using T = float;
+    using KY = unsigned long long;
+    const int K_ = c->K, D = c->D;
+    const int RM = std::max(1, reps_cap(D, cap));
+    const T *lo = static_cast<const T *>(lo_);
+    const T *hi = static_cast<const T *>(hi_);
+    const size_t KD = (size_t)B * K_ * D, BK = (size_t)B * K_;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_lbkey = take(B * sizeof(KY)), o_amax = take(KD * sizeof(KY)), o_amin = take(KD * sizeof(KY));
+    const size_t o_flags = take(B * 4), o_blo = take(KD * sizeof(T)), o_bhi = take(KD * sizeof(T));
+    const size_t o_reps = take(BK * RM * 8), o_nreps = take(BK * 4), o_repx = take(BK * RM * D * sizeof(T));
+    const size_t o_have = take(B * 4), o_cnt = take(BK * 8), o_smax = take(KD * 4);
+    const size_t o_smin = take(KD * 4), o_jmax = take(KD * 4);
+    const size_t o_jmin = take(KD * 4), o_cand = take(BK * sizeof(KY));
+    KC_TRY(ensure(c, vs->buf, off));
+    char *w = static_cast<char *>(vs->buf.p);
+    KY *lbkey = reinterpret_cast<KY *>(w + o_lbkey), *amax = reinterpret_cast<KY *>(w + o_amax);
+    KY *amin = reinterpret_cast<KY *>(w + o_amin), *cand = reinterpret_cast<KY *>(w + o_cand);
+    unsigned *flags = reinterpret_cast<unsigned *>(w + o_flags);
+    T *blo = reinterpret_cast<T *>(w + o_blo), *bhi = reinterpret_cast<T *>(w + o_bhi);
+    int64_t *reps = reinterpret_cast<int64_t *>(w + o_reps);
+    int *nreps = reinterpret_cast<int *>(w + o_nreps), *have = reinterpret_cast<int *>(w + o_have);
+    T *repx = reinterpret_cast<T *>(w + o_repx);
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(w + o_cnt);
+    unsigned *smax = reinterpret_cast<unsigned *>(w + o_smax), *smin = reinterpret_cast<unsigned *>(w + o_smin);
+    unsigned *jmax = reinterpret_cast<unsigned *>(w + o_jmax), *jmin = reinterpret_cast<unsigned *>(w + o_jmin);
+    KC_CUDA(c, cudaMemsetAsync(w, 0, o_smin, c->stream));
+    KC_CUDA(c, cudaMemsetAsync(w + o_smin, 0xFF, o_jmax - o_smin, c->stream));
+    KC_CUDA(c, cudaMemsetAsync(w + o_jmax, 0, o_jmin - o_jmax, c->stream));
+    KC_CUDA(c, cudaMemsetAsync(w + o_jmin, 0xFF, o_cand - o_jmin, c->stream));
+    KC_CUDA(c, cudaMemsetAsync(w + o_cand, 0, off - o_cand, c->stream));
+
+    const Margins mg = make_margins(c, alpha, 0.0);
+    const double r_up = nextafter(std::sqrt(alpha), __builtin_huge_val());
+    KC_TRY(launch_wide_a(c, v, L, lo, hi, B, mg, lbkey, amax, amin, flags));
+    FinA fa;
+    fa.seeds = seeds;
+    fa.ids = L ? nullptr : v.ids;
+    fa.r_up = r_up;
+    fa.alpha = alpha;
+    fa.defl = deflate_factor(c->dt, D);
+    fa.slack = underflow_slack(c->dt, D);
+    fa.seed_defl = 1.0 - gamma_n(f64_roundings(D), kU64);
+    fa.cap = RM;
+    fa.RM = RM;
+    finalize_a_kernel<T><<<(B + 127) / 128, 128, 0, c->stream>>>(
+        B, K_, D, lo, hi, lbkey, amax, amin, flags, static_cast<const T *>(c->X), c->ldx, fa, blo, bhi, reps, nreps,
+        repx, have, lb, lb_raw, lbarg);
+    KC_TRY(after_launch(c, "tighten finalize A"));
+    KC_TRY(launch_wide_b(c, v, L, lo, hi, B, mg, blo, bhi, repx, nreps, have, seeds, RM, cnt, cand, smax, smin, jmax,
+                         jmin, flags));
+    finalize_b_kernel<T><<<(B + 127) / 128, 128, 0, c->stream>>>(B, K_, D, cnt, smax, smin, jmax, jmin, cand, flags,
+                                                                L ? nullptr : v.ids, r_up, static_cast<T *>(lo_out_),
+                                                                static_cast<T *>(hi_out_), counts, cand_out, status);
+    KC_TRY(after_launch(c, "tighten finalize B"));
+    vs->reps = reps;
+    vs->nreps = nreps;
+    vs->repx = repx;
+    vs->RM = RM;
+    return KC_OK;
+}
+
 }  // namespace
 
 kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int B, double alpha,
@@ -1149,8 +1216,6 @@ kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const vo
                               VisitScratch *vs)
 {
     if (B <= 0) return KC_OK;
-    if (c->D > 8 || c->K > 8)
-        return set_err(c, KC_EINVAL, "kc_tighten: supported for D <= 8 and K <= 8 (got D=%d, K=%d)", c->D, c->K);
     const int cap = ball_cap > 0 ? ball_cap : 50;
     if (c->dt == KC_F32) {
         if (c->K == 3 && c->D == 3)
@@ -1168,7 +1233,8 @@ kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const vo
         if (c->K <= 2 && c->D <= 8)
             return tighten_impl<float, 2, 8, 17>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
                                                  lb, lb_raw, lbarg, status, vs);
-        return set_err(c, KC_EINVAL, "kc_tighten: float data supported for K <= 4 with D <= 4, or K <= 2 with D <= 8 (K=%d, D=%d)", c->K, c->D);
+        return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb, lb_raw, lbarg,
+                            status, vs);
     }
     if (c->K <= 4 && c->D <= 2)
         return tighten_impl<double, 4, 2, 5>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
@@ -1203,7 +1269,8 @@ kc_status launch_tighten_list(kc_ctx *c, const ListBatch &L, const void *lo, con
     if (c->K <= 2 && c->D <= 8)
         return tighten_impl<float, 2, 8, 17>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
                                              lb_raw, lbarg, status, vs, &L);
-    return set_err(c, KC_EINVAL, "kc_tighten: float data supported for K <= 4 with D <= 4, or K <= 2 with D <= 8");
+    return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb, lb_raw, lbarg,
+                        status, vs, &L);
 }
 
 kc_status launch_sample_reduction_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int M,

@@ -534,8 +534,9 @@ def test_solve_degenerate_and_edge_inputs():
         assert "kc_solve" in str(e.value), (bad, str(e.value))
     with pytest.raises(KCError):
         kc.solve(tol=1.5)
-    # shapes without a tightening instantiation are refused, not run
-    kc5 = KCenter(_t(_blobs(200, 2, 5, seed=1, dtype=np.float32)), 5)
+    # shapes without a tightening kernel (double data beyond K = 4 or D = 4)
+    # are refused, not run
+    kc5 = KCenter(_t(_blobs(200, 2, 5, seed=1, dtype=np.float64)), 5)
     with pytest.raises(KCError) as e:
         kc5.solve(tol=1e-12)
     assert e.value.status == 1 and "kc_tighten" in str(e.value)

@@ -1,0 +1,113 @@
+"""The float tightening kernels for shapes without a compile-time
+instantiation (any K <= 16, D <= 64; node state in shared memory) against
+the FP64 oracle, and the solver on such shapes (Section 4.1, Algorithms 3-4;
+Algorithm 1).
+
+Tightening inputs sit on a grid: coordinates are multiples of 1/4 and node
+boxes are rounded outward to that grid, so every clamp and sample distance
+is a multiple of 1/16 computed exactly in float (D <= 64, coordinates below
+64 in magnitude), and alpha is an odd multiple of 1/32: float and double
+take every decision alike and statuses, boxes and counts must equal the
+oracle's (candidates, nearest to an off-grid midpoint, within the float
+argmin's error).  The representatives are min(ball_cap, 2D + 1, 50) per
+cluster on both sides, so D = 29 exercises the cap of 50.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2301_00061_gb300 import KCenter  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _blobs(n, d, k, seed, dtype=np.float32):
+    return synth.gaussian_mixture(n, d, (1 / k,) * k, (1.0,) * k, (1.0,) * k, 10.0, seed, dtype=dtype)
+
+
+def _grid_case(n, d, k, seed, B, scale):
+    X = (np.round(_blobs(n, d, k, seed).astype(np.float64) * 4) / 4).astype(np.float32)
+    c, fobj = oracle.fft(X, k, 0)
+    rng = np.random.default_rng(seed)
+    lo0, hi0 = X.min(0).astype(np.float64), X.max(0).astype(np.float64)
+    lo = np.empty((B, k, d))
+    hi = np.empty((B, k, d))
+    for b in range(B):
+        for j in range(k):
+            # box j holds the FFT center j, so for alpha >= the FFT objective the
+            # node holds a solution and cannot be proved infeasible
+            w = rng.uniform(*scale, size=d) * (hi0 - lo0)
+            ctr = X[c[j]].astype(np.float64)
+            lo[b, j] = np.clip(ctr - rng.uniform(0.2, 0.8, size=d) * w, lo0, hi0)
+            hi[b, j] = np.clip(lo[b, j] + w, lo0, hi0)
+    lo = (np.floor(lo * 4) / 4).astype(np.float32)
+    hi = (np.ceil(hi * 4) / 4).astype(np.float32)
+    return X, c, fobj, lo, hi
+
+
+def _compare(X, lo, hi, alpha, seeds, g, cap):
+    st, glo, ghi = g["status"].cpu().numpy(), g["lo"].cpu().numpy(), g["hi"].cpu().numpy()
+    gcnt, gcand, glb = g["count"].cpu().numpy(), g["cand"].cpu().numpy(), g["lb"].cpu().numpy()
+    feasible = 0
+    for b in range(lo.shape[0]):
+        r = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=True, ball_cap=cap)
+        assert glb[b] <= r["beta"] and glb[b] >= r["beta"] * (1 - 1.5e-6), (b, glb[b], r["beta"])
+        assert st[b] == r["status"], (b, st[b], r["status"])
+        if r["status"] == 1:
+            continue
+        feasible += 1
+        assert np.array_equal(glo[b], r["lo"].astype(np.float32)), b
+        assert np.array_equal(ghi[b], r["hi"].astype(np.float32)), b
+        assert np.array_equal(gcnt[b], r["count"]), (b, gcnt[b], r["count"])
+        for j in range(lo.shape[1]):
+            mid = 0.5 * (r["box_bt_lo"][j] + r["box_bt_hi"][j])
+            x = X[gcand[b, j]].astype(np.float64)
+            assert np.all(x >= r["box_bt_lo"][j]) and np.all(x <= r["box_bt_hi"][j])
+            dg = ((x - mid) ** 2).sum()
+            do = ((X[r["cand"][j]].astype(np.float64) - mid) ** 2).sum()
+            assert dg <= do * (1 + 1e-5) + 1e-9 * (1 + ((r["box_bt_hi"][j] - r["box_bt_lo"][j]) ** 2).sum())
+    return feasible
+
+
+@pytest.mark.parametrize("n,d,k,cap,seeded", [
+    (6_000, 12, 3, 50, False), (6_000, 16, 5, 50, True), (4_000, 29, 3, 9, False), (4_000, 29, 3, 25, False),
+    (4_000, 29, 3, 50, True), (8_000, 2, 5, 50, False), (6_000, 6, 3, 50, False), (3_000, 64, 2, 50, False)])
+def test_wide_tighten_exact_on_grid(n, d, k, cap, seeded):
+    X, c, fobj, lo, hi = _grid_case(n, d, k, seed=d + k, B=10, scale=(0.05, 0.5))
+    kc = KCenter(_t(X), k)
+    seeds = np.array(c, np.int64) if seeded else None
+    feasible = 0
+    for f in (0.8, 0.95, 1.02, 1.2):
+        alpha = (np.round(fobj * f * 16) + 0.5) / 16
+        g = kc.tighten(_t(lo), _t(hi), alpha, seeds=None if seeds is None else _t(seeds), ball_cap=cap)
+        torch.cuda.synchronize()
+        feasible += _compare(X, lo, hi, alpha, seeds, g, cap)
+    assert feasible >= 5
+
+
+@pytest.mark.parametrize("n,d,k,seed", [(1_500, 12, 3, 1), (1_500, 16, 3, 1), (1_000, 29, 3, 1), (2_000, 2, 5, 1),
+                                        (1_500, 3, 6, 1)])
+def test_wide_solve_matches_oracle(n, d, k, seed):
+    """Solves on the wide shapes (D > 8: one shared sample set without sample
+    reduction; K = 5, 6 with D <= 8: per-node lists) reach the oracle's
+    certified optimum; the objective is the exact double value of the
+    returned centers."""
+    X = _blobs(n, d, k, seed)
+    kc = KCenter(_t(X), k)
+    g = kc.solve(tol=1e-12, time_limit_s=120.0)
+    r = oracle.solve(X, k, tol=1e-12)
+    assert g["status"] == 0 and r["status"] == 0
+    assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
+    assert oracle.objective(X, g["centers"])[0] == g["objective"]
