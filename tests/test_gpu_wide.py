@@ -57,13 +57,22 @@ def _grid_case(n, d, k, seed, B, scale):
     return X, c, fobj, lo, hi
 
 
+def _lb_rel_gap(d):
+    """Proved relative gap of a certified float bound: 2 gamma_n, n = ceil(D/2) + 3
+    roundings, gamma_n = n u / (1 - n u), u = 2^-24 (below 1e-6 up to D = 10)."""
+    n = (d + 1) // 2 + 3
+    u = 2.0 ** -24
+    return 2 * n * u / (1 - n * u)
+
+
 def _compare(X, lo, hi, alpha, seeds, g, cap):
+    rel = _lb_rel_gap(X.shape[1])
     st, glo, ghi = g["status"].cpu().numpy(), g["lo"].cpu().numpy(), g["hi"].cpu().numpy()
     gcnt, gcand, glb = g["count"].cpu().numpy(), g["cand"].cpu().numpy(), g["lb"].cpu().numpy()
     feasible = 0
     for b in range(lo.shape[0]):
         r = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=True, ball_cap=cap)
-        assert glb[b] <= r["beta"] and glb[b] >= r["beta"] * (1 - 1.5e-6), (b, glb[b], r["beta"])
+        assert glb[b] <= r["beta"] and glb[b] >= r["beta"] * (1 - rel), (b, glb[b], r["beta"])
         assert st[b] == r["status"], (b, st[b], r["status"])
         if r["status"] == 1:
             continue
