@@ -46,7 +46,9 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--n", type=int, default=None, help="override N (testing only)")
+    p.add_argument("--n", type=int, default=None, help="override N (testing and profiling only)")
+    p.add_argument("--nodes", type=int, default=None,
+                   help="override the nodes per step (profiling only; the metric's workload has 256)")
     p.add_argument("--solve-n", type=int, default=10_000_000,
                    help="N of the batched-solve workload timed to a certified optimum (0: skip)")
     p.add_argument("--no-hbm-points", action="store_true")
@@ -150,7 +152,7 @@ def lb_roofline(ms, n, d, k, b, sms, sm_mhz_sampled, sm_mhz_fallback, shape, pro
     peak = sms * 128 * f_mhz * 1e6 / 1e12
     traffic = None
     if tuple(shape) == (4, 256) and b == 256 and d == 8 and k == 5:
-        traffic = 160_141_568 * (n / 5e6) + 3_646_720
+        traffic = 160_336_896 * (n / 5e6) + 3_938_304
     basis = "median SM clock sampled" if sm_mhz_sampled else "no clock sample: fallback clock"
     rec = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
            "traffic": traffic, "ops_per_eval": ops, "ops_count": "FP32 lane operations, 4KD+K per node x sample",
@@ -361,6 +363,9 @@ def main():
     dev = torch.device("cuda", local)
     import paper_2301_00061_gb300 as kcm
 
+    global B_NODES
+    if args.nodes:
+        B_NODES = args.nodes
     X, w = synth.make_workload(WORKLOAD, n=args.n)
     n = X.shape[0]
     lo, hi = synth.nested_boxes(X, w.k, B_NODES, seed=1 + rank)

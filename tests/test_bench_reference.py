@@ -61,7 +61,7 @@ def test_lower_bound_roofline_record():
     assert abs(r["achieved"] - achieved) < 1e-9 and abs(r["peak"] - 152 * 128 * 2070e6 / 1e12) < 1e-9
     assert abs(r["frac"] - achieved / r["peak"]) < 1e-12 and 0.9 < r["frac"] < 0.92
     assert abs(r["frac_of_probe"] - achieved / 38.0) < 1e-12
-    assert r["traffic"] == 2 * 160_141_568 + 3_646_720 and r["bound"] == "alu"
+    assert r["traffic"] == 2 * 160_336_896 + 3_938_304 and r["bound"] == "alu"
     assert abs(r["hbm_gbs"] - 1e7 * 8 * 4 / 11.5e-3 / 1e9) < 1e-9
     other = bench.lb_roofline(11.5, 10_000_000, 8, 5, 256, 152, None, 1965.0, (2, 256))
     assert other["traffic"] is None and "fallback" in other["peak_basis"] and "1965" in other["peak_basis"]
