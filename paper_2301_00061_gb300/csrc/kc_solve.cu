@@ -953,11 +953,16 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 for (int q = 0; q < nf; ++q) {
                     const int i = fi[q];
                     const int64_t n = list_n(batch[rows[q]].list), m = (int64_t)kept[q];
-                    if ((double)m > 0.95 * (double)n) {
+                    // a counted (long) list is written only when the survivors are
+                    // at most N/16: longer lists stay shared with the parent, so the
+                    // nodes holding them keep sharing each staged tile
+                    const bool worth = offs[q] >= 0 ? (double)m <= 0.95 * (double)n
+                                                    : (double)m <= 0.95 * (double)n && m * 16 <= c->N;
+                    if (!worth) {
                         if (offs[q] >= 0) arena.release(offs[q], n);
                         else {
-                            // a long list that barely shrinks: its descendants skip
-                            // 1, 3, 7, 15 generations of filtering after 1, 2, 3, 4+
+                            // a long list that does not shrink enough: its descendants
+                            // skip 1, 3, 7, 15 generations of filtering after 1, 2, 3, 4+
                             // such filters in a row
                             const int st = std::min(4, kid_fstreak[i] + 1);
                             kid_fstreak[i] = (int8_t)st;
