@@ -178,6 +178,21 @@ kc_status kc_upper_bound(kc_ctx *ctx, const int64_t *centers, int32_t S, double 
                          int64_t *worst_out);
 
 /*
+ * kc_upper_bound_points -- the objective of Eq. 1 at S sets of Kc centers given
+ * as points (not necessarily samples): max_s min_k ||x_s - mu_k||^2 over all N
+ * samples, evaluated as kc_upper_bound does (float data: float screen, double
+ * re-evaluation of the samples that can attain the maximum).  Used where a
+ * center's coordinates are known but the sample is not in this context (the
+ * samples split across several contexts, Section 4.3), and for centers off the
+ * samples.
+ *   pts        [S][Kc][D] of the data type, finite (KC_EINVAL otherwise).
+ *   Kc         centers per set, 1 <= Kc <= 16 (any, not only K); S <= 65536.
+ *   ub_out     [S] double; worst_out [S] int64 or NULL (smallest index on ties).
+ */
+kc_status kc_upper_bound_points(kc_ctx *ctx, const void *pts, int32_t S, int32_t Kc, double *ub_out,
+                                int64_t *worst_out);
+
+/*
  * kc_fft -- Farthest First Traversal, Algorithm 2: start at sample `start`,
  * then repeatedly add the sample farthest (in double precision) from the
  * chosen set until K are chosen.  centers_out: K int64; obj_out: the

@@ -109,6 +109,7 @@ def lib():
                 "kco_lower_bounds": (_I32, [_P, _I64, _I32, _I32, _P, _P, _I32, _P, _P, _P]),
                 "kco_lower_bounds_par": (_I32, [_P, _I64, _I32, _I32, _P, _P, _I32, _P, _P]),
                 "kco_witness_values": (_I32, [_P, _I64, _I32, _I32, _P, _P, _I64, _P, _P]),
+                "kco_objective_points": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
                 "kco_beta_matrix": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
                 "kco_alpha_s": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
                 "kco_objective": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P, _P]),
@@ -214,6 +215,15 @@ def objective(X, centers, active=None):
     v = C.c_double(); arg = C.c_int64()
     m = _mask(active)
     lib().kco_objective(_ptr(X), n, d, c.shape[0], _ptr(c), _ptr(m), C.addressof(v), C.addressof(arg))
+    return v.value, arg.value
+
+
+def objective_points(X, mu):
+    """Eq. 1 at centres given as points mu (K, D): (value, argmax sample)."""
+    X, mu = _f64(X), _f64(mu)
+    n, d = X.shape
+    v = C.c_double(); arg = C.c_int64()
+    lib().kco_objective_points(_ptr(X), n, d, mu.shape[0], _ptr(mu), C.addressof(v), C.addressof(arg))
     return v.value, arg.value
 
 

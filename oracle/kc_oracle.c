@@ -264,6 +264,29 @@ int kco_objective(const double *X, int64_t N, int D, int K, const int64_t *cente
     return 0;
 }
 
+/* Eq. 1 at K centres given as points mu (K x D, row major), which need not be
+ * samples: max_s min_k ||x_s - mu_k||^2 and the sample attaining it. */
+int kco_objective_points(const double *X, int64_t N, int D, int K, const double *mu, double *value,
+                         int64_t *argmax)
+{
+    double best = -1.0;
+    int64_t arg = -1;
+    for (int64_t s = 0; s < N; ++s) {
+        double q = INFINITY;
+        for (int k = 0; k < K; ++k) {
+            double v = sqdist(X + s * D, mu + k * D, D);
+            if (v < q) q = v;
+        }
+        if (q > best) {   /* strictly larger: ties keep the smaller index */
+            best = q;
+            arg = s;
+        }
+    }
+    *value = arg < 0 ? 0.0 : best;
+    if (argmax) *argmax = arg;
+    return 0;
+}
+
 /* Candidate centre of one box (Section 3.2, children): the active sample
  * inside [lo, hi] closest to the box midpoint (lo + hi) / 2.  -1 if the box
  * holds no active sample.  (Reading: candidates are drawn from X cap M^k.) */

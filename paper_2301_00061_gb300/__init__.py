@@ -23,7 +23,7 @@ __all__ = [
     "KCError", "KC_F32", "KC_F64", "KC_ROW_MAJOR", "KC_COL_MAJOR", "SolveOpts", "Result",
     "kc_create", "kc_destroy", "kc_last_error", "kc_set_stream", "kc_launch_count", "kc_root_box",
     "kc_lower_bounds", "kc_lower_bounds_noalloc", "kc_autotune", "kc_upper_bound", "kc_fft", "kc_fft_multi",
-    "kc_lower_bounds_subset", "kc_fp32_probe", "kc_tighten", "kc_sample_reduction",
+    "kc_lower_bounds_subset", "kc_fp32_probe", "kc_upper_bound_points", "kc_tighten", "kc_sample_reduction",
     "kc_solve_defaults", "kc_solve", "KCenter", "library_path", "kc_mlp_create", "kc_mlp_destroy",
     "kc_mlp_get_params", "kc_mlp_forward", "kc_mlp_grad", "kc_mlp_train", "kc_set_scorer", "Scorer",
 ]
@@ -87,6 +87,7 @@ def _load():
         "kc_upper_bound": (I32, [P, P, I32, P, P]),
         "kc_fft": (I32, [P, I64, P, P]),
         "kc_fft_multi": (I32, [P, P, I32, P, P]),
+        "kc_upper_bound_points": (I32, [P, P, I32, I32, P, P]),
         "kc_lower_bounds_subset": (I32, [P, P, I64, P, P, I32, P, P, P, P]),
         "kc_fp32_probe": (I32, [I32, P, P, P]),
         "kc_tighten": (I32, [P, P, P, I32, D, P, I32, P, P, P, P, P, P]),
@@ -237,6 +238,11 @@ def kc_lower_bounds_noalloc(X, N, ld, D, K, lo, hi, lb, lb_raw=None, argmax=None
 
 def kc_upper_bound(h, centers, ub, worst=None):
     _check(h, _lib.kc_upper_bound(h, _ptr(centers), centers.shape[0], _ptr(ub), _ptr(worst)))
+
+
+def kc_upper_bound_points(h, pts, ub, worst=None):
+    """pts (S, Kc, D) in the data type -> ub (S,) float64, worst (S,) int64."""
+    _check(h, _lib.kc_upper_bound_points(h, _ptr(pts), pts.shape[0], pts.shape[1], _ptr(ub), _ptr(worst)))
 
 
 def kc_fft(h, start, centers, obj=None):
@@ -452,6 +458,15 @@ class KCenter:
         ub = self._alloc(centers, (S,), "f64")
         worst = self._alloc(centers, (S,), "i64")
         kc_upper_bound(self.h, centers, ub, worst)
+        return ub, worst
+
+    def upper_bound_points(self, pts):
+        """Objective (Eq. 1) at S sets of centers given as points, pts of
+        shape (S, Kc, D) in the data type -> (value, worst sample), each (S,)."""
+        S = pts.shape[0]
+        ub = self._alloc(pts, (S,), "f64")
+        worst = self._alloc(pts, (S,), "i64")
+        kc_upper_bound_points(self.h, pts, ub, worst)
         return ub, worst
 
     def fft(self, start, like=None):

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
+#include <cmath>
 #include <new>
 
 #include "kc_internal.cuh"
@@ -417,6 +418,36 @@ kc_status kc_fft_multi(kc_ctx *c, const int64_t *starts, int32_t S, int64_t *cen
     if (obj_out)
         KC_TRY(launch_objective(c, full_view(c), C, S, K, __builtin_huge_val(), static_cast<double *>(sg.dev(io)),
                                 nullptr));
+    return sg.finish();
+}
+
+kc_status kc_upper_bound_points(kc_ctx *c, const void *pts, int32_t S, int32_t Kc, double *ub_out, int64_t *worst_out)
+{
+    if (!c) return KC_EINVAL;
+    if (S < 0 || S > 65536) return set_err(c, KC_EINVAL, "kc_upper_bound_points: S=%d outside [0, 65536]", S);
+    if (Kc < 1 || Kc > kMaxK) return set_err(c, KC_EINVAL, "kc_upper_bound_points: Kc=%d outside [1, %d]", Kc, kMaxK);
+    if (S == 0) return KC_OK;
+    if (!pts || !ub_out) return set_err(c, KC_EINVAL, "kc_upper_bound_points: NULL argument");
+    const size_t bytes = (size_t)S * Kc * c->D * c->esize;
+    Stager sg(c);
+    const int ip = sg.add(pts, bytes, true);
+    const int iu = sg.add(ub_out, (size_t)S * 8, false);
+    const int iw = sg.add(worst_out, (size_t)S * 8, false);
+    KC_TRY(sg.begin());
+    {
+        // the points must be finite (checked on the host)
+        std::vector<char> h(bytes);
+        KC_CUDA(c, cudaMemcpyAsync(h.data(), sg.dev(ip), bytes, cudaMemcpyDeviceToHost, c->stream));
+        KC_CUDA(c, cudaStreamSynchronize(c->stream));
+        const size_t m = (size_t)S * Kc * c->D;
+        for (size_t i = 0; i < m; ++i) {
+            const double v = c->dt == KC_F32 ? (double)reinterpret_cast<const float *>(h.data())[i]
+                                             : reinterpret_cast<const double *>(h.data())[i];
+            if (!std::isfinite(v)) return set_err(c, KC_EINVAL, "kc_upper_bound_points: non-finite coordinate");
+        }
+    }
+    KC_TRY(launch_objective(c, full_view(c), nullptr, S, Kc, __builtin_huge_val(), static_cast<double *>(sg.dev(iu)),
+                            static_cast<int64_t *>(sg.dev(iw)), sg.dev(ip)));
     return sg.finish();
 }
 

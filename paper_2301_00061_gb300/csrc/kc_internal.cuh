@@ -197,8 +197,10 @@ kc_status autotune_lower_bounds(kc_ctx *c, const void *lo, const void *hi, int B
 // device values [S] (double, exact serial-double value) and argmax [S].
 // alpha_cut: sets whose float screen proves a value >= alpha_cut are not
 // evaluated exactly (their val is set to +inf); pass +inf to evaluate all.
+// pts (nullable, device [S][Kc][D] of the data type): the centers as points
+// instead of sample indices (centers is then ignored).
 kc_status launch_objective(kc_ctx *c, const View &v, const int64_t *centers, int S, int Kc,
-                           double alpha_cut, double *val, int64_t *arg);
+                           double alpha_cut, double *val, int64_t *arg, const void *pts = nullptr);
 
 // Per-attribute min/max of the data; *nonfinite set if any NaN/Inf.
 kc_status launch_root_box(kc_ctx *c, void *lo, void *hi, int *nonfinite_dev);

@@ -34,6 +34,16 @@ __global__ void gather_pairs_f32(const float *__restrict__ X, int64_t ld, int D,
     }
 }
 
+// Center coordinates given as points [S*Kc][D] -> packed float pairs [S*Kc][Dh].
+__global__ void pack_pairs_f32(const float *__restrict__ pts, int D, int Dh, int SK, uint64_t *__restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < SK * Dh; i += gridDim.x * blockDim.x) {
+        const int sk = i / Dh, p = i % Dh;
+        const int a0 = 2 * p, a1 = 2 * p + 1;
+        out[i] = pk(pts[(size_t)sk * D + a0], a1 < D ? pts[(size_t)sk * D + a1] : 0.f);
+    }
+}
+
 // Float screen: per set, the maximum over samples of min_k ||x - c_k||^2.
 template <int DH>
 __global__ void __launch_bounds__(kThreads)
@@ -228,9 +238,10 @@ obj_exact_f32(const float *__restrict__ X, int64_t ld, int64_t n, int D, const u
 template <int DMAX>
 __global__ void __launch_bounds__(kThreads)
 obj_exact_f64(const double *__restrict__ X, int64_t ld, int64_t n, int D, const double *__restrict__ Xfull,
-              int64_t ldf, const int64_t *__restrict__ centers, int S, int Kc, double *__restrict__ pval,
-              uint32_t *__restrict__ ppos)
+              int64_t ldf, const int64_t *__restrict__ centers, const double *__restrict__ pts, int S, int Kc,
+              double *__restrict__ pval, uint32_t *__restrict__ ppos)
 {
+    // centers by sample index from Xfull, or (pts != NULL) as points [S*Kc][D]
     constexpr int NW = kThreads / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     double *sc = reinterpret_cast<double *>(smem);                 // [S][Kc][D]
@@ -238,7 +249,7 @@ obj_exact_f64(const double *__restrict__ X, int64_t ld, int64_t n, int D, const 
     uint32_t *wpos = reinterpret_cast<uint32_t *>(wval + NW * S);
     for (int i = threadIdx.x; i < S * Kc * D; i += kThreads) {
         const int a = i % D, sk = i / D;
-        sc[i] = Xfull[(size_t)a * ldf + centers[sk]];
+        sc[i] = pts ? pts[(size_t)sk * D + a] : Xfull[(size_t)a * ldf + centers[sk]];
     }
     for (int i = threadIdx.x; i < NW * S; i += kThreads) { wval[i] = -1.0; wpos[i] = 0xFFFFFFFFu; }
     __syncthreads();
@@ -352,7 +363,7 @@ double screen_gamma(int D)
 }
 
 kc_status objective_chunk(kc_ctx *c, const View &v, const int64_t *centers, int S, int Kc,
-                          double alpha_cut, double *val, int64_t *arg)
+                          double alpha_cut, double *val, int64_t *arg, const void *pts)
 {
     const int D = c->D;
     const int NW = kThreads / 32;
@@ -374,8 +385,12 @@ kc_status objective_chunk(kc_ctx *c, const View &v, const int64_t *centers, int 
         char *w = static_cast<char *>(c->work.p);
         uint64_t *pairs = reinterpret_cast<uint64_t *>(w);
         float *thr = reinterpret_cast<float *>(w + off_thr);
-        gather_pairs_f32<<<(S * Kc * Dh + 255) / 256, 256, 0, c->stream>>>(
-            static_cast<const float *>(c->X), c->ldx, D, Dh, centers, S * Kc, pairs);
+        if (pts)
+            pack_pairs_f32<<<(S * Kc * Dh + 255) / 256, 256, 0, c->stream>>>(static_cast<const float *>(pts), D, Dh,
+                                                                             S * Kc, pairs);
+        else
+            gather_pairs_f32<<<(S * Kc * Dh + 255) / 256, 256, 0, c->stream>>>(
+                static_cast<const float *>(c->X), c->ldx, D, Dh, centers, S * Kc, pairs);
         KC_TRY(after_launch(c, "gather centers"));
         unsigned long long *keys = reinterpret_cast<unsigned long long *>(w + off_part);
         if (v.n > 0) {
@@ -405,8 +420,8 @@ kc_status objective_chunk(kc_ctx *c, const View &v, const int64_t *centers, int 
         uint32_t *ppos = reinterpret_cast<uint32_t *>(pval + (size_t)g * S);
         if (v.n > 0) {
             k<<<g, kThreads, smem, c->stream>>>(static_cast<const double *>(v.X), v.ld, v.n, D,
-                                                static_cast<const double *>(c->X), c->ldx, centers, S, Kc,
-                                                pval, ppos);
+                                                static_cast<const double *>(c->X), c->ldx, centers,
+                                                static_cast<const double *>(pts), S, Kc, pval, ppos);
             KC_TRY(after_launch(c, "objective f64"));
         }
         obj_finalize<<<(S + 3) / 4, 128, 0, c->stream>>>(pval, ppos, v.n > 0 ? g : 0, S, v.ids, nullptr, val,
@@ -419,7 +434,7 @@ kc_status objective_chunk(kc_ctx *c, const View &v, const int64_t *centers, int 
 }  // namespace
 
 kc_status launch_objective(kc_ctx *c, const View &v, const int64_t *centers, int S, int Kc,
-                           double alpha_cut, double *val, int64_t *arg)
+                           double alpha_cut, double *val, int64_t *arg, const void *pts)
 {
     if (S <= 0) return KC_OK;
     const int D = c->D;
@@ -429,8 +444,9 @@ kc_status launch_objective(kc_ctx *c, const View &v, const int64_t *centers, int
     int chunk = (int)std::max<size_t>(1, cap / per_set);
     for (int s0 = 0; s0 < S; s0 += chunk) {
         const int ns = std::min(chunk, S - s0);
-        KC_TRY(objective_chunk(c, v, centers + (size_t)s0 * Kc, ns, Kc, alpha_cut, val + s0,
-                               arg ? arg + s0 : nullptr));
+        KC_TRY(objective_chunk(c, v, centers ? centers + (size_t)s0 * Kc : nullptr, ns, Kc, alpha_cut, val + s0,
+                               arg ? arg + s0 : nullptr,
+                               pts ? static_cast<const char *>(pts) + (size_t)s0 * Kc * D * c->esize : nullptr));
     }
     return KC_OK;
 }

@@ -238,3 +238,62 @@ def test_lower_bounds_subset_matches_oracle(d, k):
     with pytest.raises(KCError) as e:
         kc.lower_bounds_subset(_t(bad.view(np.int32)), _t(lo), _t(hi))
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_upper_bound_points_matches_oracle(dtype):
+    """Eq. 1 at centers given as points (off the samples, and fewer than K per
+    set): the double value and the worst sample equal the oracle's."""
+    X = _mix(30_011, 3, 4, seed=12, dtype=dtype)
+    rng = np.random.default_rng(3)
+    kc = KCenter(_t(X), 4)
+    for kc_n in (1, 2, 4):
+        pts = rng.uniform(-2, 22, size=(6, kc_n, 3)).astype(dtype)
+        ub, worst = kc.upper_bound_points(_t(pts))
+        torch.cuda.synchronize()
+        for s in range(6):
+            v, a = oracle.objective_points(X, pts[s])
+            assert float(ub[s]) == v and int(worst[s]) == a, (kc_n, s)
+    # at sample points it is the objective of those samples
+    c = np.array([[5, 900, 30_000, 17]], np.int64)
+    ubp, wp = kc.upper_bound_points(_t(X[c[0]][None].copy()))
+    ubc, wc = kc.upper_bound(_t(c))
+    assert float(ubp[0]) == float(ubc[0]) and int(wp[0]) == int(wc[0])
+    with pytest.raises(KCError):
+        bad = np.full((1, 2, 3), np.nan, dtype)
+        kc.upper_bound_points(_t(bad))
+
+
+def test_sharded_calls_with_one_rank_equal_the_library():
+    """The sample-sharded class (Section 4.3) over one gloo rank and the CUDA
+    library: its collectives reduce a single partial result, so root box,
+    lower bounds, objective and FFT equal the library's own calls bit for bit
+    (several ranks are covered on the CPU with the oracle per block)."""
+    import socket
+    import torch.distributed as dist
+    from paper_2301_00061_gb300.shard import ShardedKCenter
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    dist.init_process_group("gloo", rank=0, world_size=1, init_method=f"tcp://127.0.0.1:{port}")
+    try:
+        X = _mix(50_001, 3, 3, seed=41)
+        lo, hi = synth.random_boxes(X, 3, 9, seed=2, frac_lo=0.0, frac_hi=0.4)
+        ref = KCenter(X, 3)
+        sk = ShardedKCenter(X, 3, offset=0, n_total=X.shape[0])
+        rlo, rhi = ref.root_box()
+        slo, shi = sk.root_box()
+        assert np.array_equal(slo, rlo.astype(np.float64)) and np.array_equal(shi, rhi.astype(np.float64))
+        a = ref.lower_bounds(lo, hi)
+        b = sk.lower_bounds(lo, hi)
+        for u, v in zip(a, b):
+            assert np.array_equal(np.asarray(u), np.asarray(v))
+        C = np.array([[1, 2, 3], [40_000, 7, 123]], np.int64)
+        ua, wa = ref.upper_bound(C)
+        ub_, wb = sk.upper_bound(C)
+        assert np.array_equal(ua, ub_) and np.array_equal(wa, wb)
+        cf, of = sk.fft(11)
+        rc, ro = oracle.fft(X, 3, 11)
+        assert np.array_equal(cf, rc) and of == ro
+    finally:
+        dist.destroy_process_group()
