@@ -3,7 +3,8 @@
 Each mutant below turns one spot of the oracle (``oracle/kc_oracle.c`` or
 ``oracle/mlp.py``) into a plausible slip: a dropped term, a wrong sign, index
 or bound, a transposed operand, a wrong tie-break, a looser test.  The pin
-suites (``test_oracle_pins.py``, ``test_oracle_mlp_pins.py``) are run against
+suites (``test_oracle_pins.py`` with ``test_oracle_replay.py``, and
+``test_oracle_mlp_pins.py``) are run against
 each mutant in a child process and must report a failed assertion.  Mutants
 are written to a temporary directory; the committed oracle is never touched.
 
@@ -93,6 +94,13 @@ C_MUTANTS = {
     "candidate_tie_to_largest_index": ("Sec. 3.2", [
         ("if (dm < cdist[k]) { cdist[k] = dm; out->cand[k] = s; }",
          "if (dm <= cdist[k]) { cdist[k] = dm; out->cand[k] = s; }")]),
+    "witness_value_first_cluster_only": ("Sec. 3.1, replay", [
+        ("double b = kco_beta_sk(x, lo + (m * K + k) * D, hi + (m * K + k) * D, D);",
+         "double b = kco_beta_sk(x, lo + (m * K + 0) * D, hi + (m * K + 0) * D, D);")]),
+    "objective_points_first_center_only": ("Eq. 1", [("double v = sqdist(X + s * D, mu + k * D, D);",
+                                                      "double v = sqdist(X + s * D, mu + 0 * D, D);")]),
+    "parallel_merge_later_block_on_ties": ("Eq. 9", [("if (ba[q] >= 0 && (arg < 0 || bv[q] > best))",
+                                                      "if (ba[q] >= 0 && (arg < 0 || bv[q] >= best))")]),
 }
 
 # name -> (what, [(original, planted), ...]) in mlp.py
@@ -138,7 +146,8 @@ def _run_c(tmp, name, edits):
         f.write(_plant(open(C_SRC).read(), edits))
     subprocess.run(["gcc", *oracle.GCC_FLAGS, "-o", so, src, "-lm"], check=True)
     env = dict(os.environ, KCO_ORACLE_LIB=so)
-    return subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", *_PIN_ARGS],
+    return subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "tests/test_oracle_replay.py",
+                           *_PIN_ARGS],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
 
 

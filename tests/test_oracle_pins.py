@@ -489,3 +489,20 @@ def test_parallel_lower_bounds_equal_serial():
     a, b = oracle.lower_bounds(X2, lo2, hi2)
     c, d, _ = oracle.lower_bounds_par(X2, lo2, hi2)
     assert b[0] == d[0] == min(far, 4999) and a[0] == c[0]
+
+
+def test_objective_at_points():
+    """Eq. 1 at centers given as points: at sample points it is the objective
+    of those samples; at other points it equals a scipy distance-matrix
+    evaluation, and the worst sample is the smallest index of the maximum."""
+    from scipy.spatial.distance import cdist
+    rng = np.random.default_rng(8)
+    X = rng.normal(size=(700, 3))
+    c = np.array([3, 250, 699])
+    assert oracle.objective_points(X, X[c]) == oracle.objective(X, c)
+    mu = rng.uniform(-1, 1, size=(2, 3))
+    q = (cdist(X, mu) ** 2).min(1)
+    v, a = oracle.objective_points(X, mu)
+    assert abs(v - q.max()) <= 1e-12 * q.max() and a == int(np.argmax(q))
+    X2 = np.concatenate([X, X[a:a + 1]])          # a duplicate of the worst sample: the first index wins
+    assert oracle.objective_points(X2, mu)[1] == a

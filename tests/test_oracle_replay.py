@@ -102,7 +102,11 @@ def test_witness_values_are_the_closed_form_at_the_witness():
     X, z, c = _setup()
     lo = np.array([[[1.0, 2.0], [6.0, 6.0]]])
     hi = np.array([[[3.0, 4.0], [7.0, 9.0]]])
-    for w in (0, 17, 299):
+    d0 = np.array([oracle.beta_sk(x, lo[0, 0], hi[0, 0]) for x in X])
+    d1 = np.array([oracle.beta_sk(x, lo[0, 1], hi[0, 1]) for x in X])
+    near0, near1 = int(np.argmax(d1 - d0)), int(np.argmax(d0 - d1))   # one sample nearer each box
+    assert d0[near0] < d1[near0] and d1[near1] < d0[near1]
+    for w in (0, near0, near1, 299):
         v = oracle.witness_values(X, lo, hi, np.array([w]))[0]
         assert v == min(oracle.beta_sk(X[w], lo[0, 0], hi[0, 0]), oracle.beta_sk(X[w], lo[0, 1], hi[0, 1]))
         assert v <= oracle.lower_bound(X, lo[0], hi[0])[0]
