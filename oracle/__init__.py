@@ -264,8 +264,11 @@ def bruteforce(X, k):
     return obj.value, c
 
 
-def tighten(X, lo, hi, alpha, seeds=None, active=None, is_f32=False, ball_cap=50):
-    """Cluster assignment + bounds tightening of one node; returns a dict."""
+def tighten(X, lo, hi, alpha, seeds=None, active=None, is_f32=False, ball_cap=0):
+    """Cluster assignment + bounds tightening of one node; returns a dict.
+    ball_cap <= 0: representatives are the seed and the attribute extremes
+    (at most 2D + 1); ball_cap > 0: up to min(ball_cap, 50), the extremes
+    along attribute-pair directions after those."""
     X, lo, hi = _f64(X), _f64(lo), _f64(hi)
     n, d = X.shape
     k = lo.shape[0]
@@ -313,7 +316,7 @@ def sample_reduction(X, lo, hi, beta_glob, alpha, active, reps=None):
     return act.astype(bool)
 
 
-def solve(X, k, tol=1e-12, use_bt=True, use_sr=True, i_sr=1, ball_cap=50, is_f32=None, seed=0,
+def solve(X, k, tol=1e-12, use_bt=True, use_sr=True, i_sr=1, ball_cap=0, is_f32=None, seed=0,
           node_limit=0, time_limit=0.0):
     """Serial FP64 branch and bound (Algorithm 1); returns a dict."""
     if is_f32 is None:

@@ -432,13 +432,18 @@ typedef struct {
     double bhi[KCO_MAXK * KCO_MAXD];
 } kco_tighten_out;
 
-/* Representatives ("balls") of cluster k, from its assigned set: the seed of
- * cluster k (if seeds exist), then for a = 0..D-1 the assigned samples with
- * the smallest and the largest x_a (smallest index on ties), duplicates
- * skipped, at most `cap` of them (reading of the 50-ball cap of Section
- * 4.1.2).  `amin_idx`/`amax_idx` hold those arg-extremes ([D], -1 if none). */
+/* Representatives ("balls") of cluster k, from its assigned set (reading of
+ * the "at most 50 balls" of Section 4.1.2): the seed of cluster k (if seeds
+ * exist), then the assigned samples attaining the minimum and the maximum of
+ * x along a fixed list of directions -- first the D attributes (x_a), then,
+ * when `diag`, the first P = min(D(D-1)/2, 16) attribute pairs a < b in
+ * lexicographic order, each as x_a + x_b and then x_a - x_b -- smallest index
+ * on ties, duplicates skipped, at most `cap` of them.  Arrays hold those
+ * arg-extremes (-1 if none): amin_idx/amax_idx [D], dmin_idx/dmax_idx [2P]
+ * (sum of pair p at 2p, difference at 2p + 1). */
+#define KCO_MAXPAIRS 16
 static int build_reps(int64_t seed_k, const int64_t *amin_idx, const int64_t *amax_idx, int D,
-                      int cap, int64_t *reps)
+                      const int64_t *dmin_idx, const int64_t *dmax_idx, int ndir, int cap, int64_t *reps)
 {
     int n = 0;
 #define KCO_ADD_REP(idx)                                            \
@@ -455,8 +460,30 @@ static int build_reps(int64_t seed_k, const int64_t *amin_idx, const int64_t *am
         KCO_ADD_REP(amin_idx[a]);
         KCO_ADD_REP(amax_idx[a]);
     }
+    for (int q = 0; q < ndir; ++q) {
+        KCO_ADD_REP(dmin_idx[q]);
+        KCO_ADD_REP(dmax_idx[q]);
+    }
 #undef KCO_ADD_REP
     return n;
+}
+
+/* The value of sample x along direction q of the pair list (see build_reps),
+ * in the data's precision: float data add or subtract in float. */
+static double dir_value(const double *x, int D, int q, int is_f32)
+{
+    const int p = q / 2;
+    int a = 0, b = 1, t = p;
+    for (a = 0; a < D - 1; ++a) {
+        if (t < D - 1 - a) { b = a + 1 + t; break; }
+        t -= D - 1 - a;
+    }
+    if (is_f32) {
+        const float fa = (float)x[a], fb = (float)x[b];
+        const float v = (q & 1) ? fa - fb : fa + fb;
+        return (double)v;
+    }
+    return (q & 1) ? x[a] - x[b] : x[a] + x[b];
 }
 
 /* One node's cluster assignment and bounds tightening.
@@ -487,7 +514,13 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
                 int ball_cap, kco_tighten_out *out)
 {
     if (K > KCO_MAXK || D > KCO_MAXD) return 1;
+    /* ball_cap <= 0: the seed and the attribute extremes (at most 2D + 1);
+     * otherwise up to ball_cap (at most 50) with the pair directions after them */
+    const int diag = ball_cap > 0;
+    if (ball_cap <= 0) ball_cap = 2 * D + 1;
     if (ball_cap > KCO_MAXREPS) ball_cap = KCO_MAXREPS;
+    const int npairs = D * (D - 1) / 2 < KCO_MAXPAIRS ? D * (D - 1) / 2 : KCO_MAXPAIRS;
+    const int ndir = diag ? 2 * npairs : 0;
     const int KD = K * D;
     int8_t *asg = (int8_t *)malloc((size_t)N);
     if (!asg) return 2;
@@ -525,6 +558,11 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
             if (kco_beta_sk(X + seeds[k] * D, lo + k * D, hi + k * D, D) > alpha) infeasible = 1;
             asg[seeds[k]] = (int8_t)k;
         }
+    double dmin[KCO_MAXK * 2 * KCO_MAXPAIRS], dmax[KCO_MAXK * 2 * KCO_MAXPAIRS];
+    int64_t dmin_i[KCO_MAXK * 2 * KCO_MAXPAIRS], dmax_i[KCO_MAXK * 2 * KCO_MAXPAIRS];
+    for (int i = 0; i < KCO_MAXK * 2 * KCO_MAXPAIRS; ++i) {
+        dmin[i] = INFINITY; dmax[i] = -INFINITY; dmin_i[i] = -1; dmax_i[i] = -1;
+    }
     for (int64_t s = 0; s < N; ++s) {
         int k = asg[s];
         if (k < 0) continue;
@@ -534,6 +572,12 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
             int i = k * D + a;
             if (x[a] < jmin[i]) { jmin[i] = x[a]; jmin_i[i] = s; }
             if (x[a] > jmax[i]) { jmax[i] = x[a]; jmax_i[i] = s; }
+        }
+        for (int q = 0; q < ndir; ++q) {
+            const double v = dir_value(x, D, q, is_f32);
+            const int i = k * 2 * KCO_MAXPAIRS + q;
+            if (v < dmin[i]) { dmin[i] = v; dmin_i[i] = s; }
+            if (v > dmax[i]) { dmax[i] = v; dmax_i[i] = s; }
         }
     }
     out->beta = beta_arg < 0 ? 0.0 : beta;
@@ -563,6 +607,7 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
     int all_have = 1;
     for (int k = 0; k < K; ++k) {
         out->n_reps[k] = build_reps(seeds ? seeds[k] : -1, jmin_i + k * D, jmax_i + k * D, D,
+                                    dmin_i + k * 2 * KCO_MAXPAIRS, dmax_i + k * 2 * KCO_MAXPAIRS, ndir,
                                     ball_cap, out->reps + k * KCO_MAXREPS);
         if (out->n_reps[k] == 0) all_have = 0;
     }
@@ -714,7 +759,7 @@ typedef struct {
     int32_t use_bt;      /* 1: BB+CF+BT (assignment, tightening); 0: BB+CF */
     int32_t use_sr;      /* sample reduction (Algorithm 5) */
     int32_t i_sr;        /* run sample reduction every i_sr iterations */
-    int32_t ball_cap;    /* representatives per cluster (default 50) */
+    int32_t ball_cap;    /* representatives per cluster: <= 0 the attribute extremes (2D + 1), else up to 50 */
     int32_t is_f32;      /* data are float values promoted to double */
     int64_t seed;        /* FFT start = seed mod N */
     int64_t node_limit;  /* 0: none */

@@ -101,6 +101,12 @@ C_MUTANTS = {
                                                       "double v = sqdist(X + s * D, mu + 0 * D, D);")]),
     "parallel_merge_later_block_on_ties": ("Eq. 9", [("if (ba[q] >= 0 && (arg < 0 || bv[q] > best))",
                                                       "if (ba[q] >= 0 && (arg < 0 || bv[q] >= best))")]),
+    "pair_direction_difference_as_sum": ("Sec. 4.1.2, R11", [("const float v = (q & 1) ? fa - fb : fa + fb;",
+                                                             "const float v = (q & 1) ? fa + fb : fa + fb;")]),
+    "pair_direction_in_double_for_float_data": ("Sec. 4.1.2, R11", [("    if (is_f32) {\n        const float fa",
+                                                                    "    if (0) {\n        const float fa")]),
+    "pair_directions_dropped": ("Sec. 4.1.2, R11", [("for (int q = 0; q < ndir; ++q) {\n        KCO_ADD_REP",
+                                                     "for (int q = 0; q < 0; ++q) {\n        KCO_ADD_REP")]),
 }
 
 # name -> (what, [(original, planted), ...]) in mlp.py
