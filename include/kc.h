@@ -263,7 +263,8 @@ kc_status kc_fp32_probe(int32_t mode, void *stream, double *lane_ops_per_s, floa
  *           over the samples j assigned to k (and the seed of k);
  *   step B  sample-based assignment against the representatives of each
  *           cluster (the seed, then the assigned samples with the smallest
- *           and largest value of each attribute, at most ball_cap):
+ *           and largest value of each attribute, then -- see ball_cap --
+ *           of x_a + x_b and of x_a - x_b for attribute pairs a < b):
  *           ||x_s - x_j||^2 > 4 alpha excludes k (Lemma 2);
  *   ball-BT S_+^k = samples in M'^k within sqrt(alpha) of every
  *           representative of k; M^k_hat = bbox(S_+^k) cap box-BT of the
@@ -282,8 +283,15 @@ kc_status kc_fp32_probe(int32_t mode, void *stream, double *lane_ops_per_s, floa
  *   lb_out          [B] double certified lower bound of the input boxes, or NULL.
  *   status          [B] int8: 0 feasible, 1 proved to hold no solution of
  *                   value <= alpha, 2 leaf (every tightened box is a point).
- * ball_cap <= 0 selects the default of 50; at most min(ball_cap, 2D + 1, 50)
- * representatives are used (the cap binds from D = 25 on).
+ * ball_cap (the representatives' budget, "at most 50 balls" of Section
+ * 4.1.2; ties go to the smaller sample index, duplicates are skipped):
+ *   <= 0            the seed and the attribute extremes: min(2D + 1, 50);
+ *   1 .. 2D + 1     the first ball_cap of those;
+ *   above 2D + 1    (D >= 2, float data only) then the arg-min and arg-max
+ *                   of x_a + x_b and of x_a - x_b (added in float) for the
+ *                   first min(D(D-1)/2, 16) pairs a < b in lexicographic
+ *                   order, up to min(ball_cap, 50) in all; these run on the
+ *                   shared-memory kernels below.  Double data: KC_EINVAL.
  * Shapes: float data any K <= 16 and D <= 64 (K <= 4 with D <= 4 and K <= 2
  * with D <= 8 run kernels with the node's state in registers, compiled per
  * shape; the others kernels whose node state lives in shared memory sized at
@@ -354,7 +362,7 @@ typedef struct {
     double time_limit_s;   /* 0: none */
     int64_t node_limit;    /* 0: none */
     int32_t batch;         /* 0: automatic; nodes bounded per launch */
-    int32_t ball_cap;      /* 50: representatives per cluster */
+    int32_t ball_cap;      /* 0: representatives per cluster, as kc_tighten's ball_cap */
     int32_t i_sr;          /* 1: sample reduction every i_sr batches, 0: off */
     int32_t use_bt;        /* 1: assignment + bounds tightening (BB+CF+BT); 0: BB+CF */
     int32_t order;         /* 0: best bound, max-range branching; 1: learned scorer (kc_set_scorer) */

@@ -18,6 +18,7 @@ namespace kc {
 constexpr int kMaxK = 16;
 constexpr int kMaxD = 64;
 constexpr int kMaxReps = 50;
+constexpr int kMaxPairs = 16;   // attribute pairs a < b along which representatives are taken
 constexpr int kThreads = 256;
 
 // Growable device buffer owned by a context.
@@ -225,9 +226,12 @@ kc_status launch_sample_reduction_view(kc_ctx *c, const View &v, const void *lo,
 
 // Passes A and B of the float tightening for any K <= 16, D <= 64 (kc_wide.cu;
 // the workspace and finalize kernels are kc_visit.cu's).
+// ndir > 0 (at most 32): also the arg-extreme keys of the assigned samples
+// along the attribute-pair directions, dmax / dmin [B][K][ndir].
 kc_status launch_wide_a(kc_ctx *c, const View &v, const ListBatch *L, const float *lo, const float *hi, int B,
                         const Margins &mg, unsigned long long *lbkey, unsigned long long *amax,
-                        unsigned long long *amin, unsigned *flags);
+                        unsigned long long *amin, unsigned *flags, int ndir, unsigned long long *dmax,
+                        unsigned long long *dmin);
 kc_status launch_wide_b(kc_ctx *c, const View &v, const ListBatch *L, const float *lo, const float *hi, int B,
                         const Margins &mg, const float *blo, const float *bhi, const float *repx, const int *nreps,
                         const int *allhave, const int64_t *seeds, int RM, unsigned long long *cnt,

@@ -382,6 +382,11 @@ struct FinA {
     double defl, slack;         // certified lower-bound deflation
     double seed_defl;           // float data: deflation of the seed test (1 for double)
     int cap, RM;
+    // float data, wide path: arg-extreme keys along the attribute-pair
+    // directions [B][K][ndir] (direction q: pair q / 2 of the pairs a < b in
+    // lexicographic order, x_a + x_b for even q, x_a - x_b for odd q)
+    int ndir;
+    const unsigned long long *dmax, *dmin;
 };
 
 template <typename T>
@@ -473,6 +478,35 @@ __global__ void finalize_a_kernel(int B, int K, int D, const T *__restrict__ lo,
                 add(amin_id[a]);
                 add(amax_id[a]);
             }
+        if constexpr (sizeof(T) == 4) {
+            // then the arg-min and arg-max along each pair direction, the seed
+            // taking part as an assigned sample of cluster k
+            int pa = 0, pb = 1;
+            for (int q = 0; q < f.ndir && nonempty && nr < f.cap; ++q) {
+                if (q > 0 && !(q & 1)) {
+                    if (++pb == D) { ++pa; pb = pa + 1; }
+                }
+                const size_t o = ((size_t)b * K + k) * f.ndir + q;
+                float vmx = 0.f, vmn = 0.f;
+                int64_t imx = -1, imn = -1;
+                if (!KT::is_none(f.dmax[o])) {
+                    vmx = KT::vmax(f.dmax[o]);
+                    const int64_t p = KT::pos(f.dmax[o]);
+                    imx = f.ids ? (int64_t)f.ids[p] : p;
+                    vmn = KT::vmin(f.dmin[o]);
+                    const int64_t p2 = KT::pos(f.dmin[o]);
+                    imn = f.ids ? (int64_t)f.ids[p2] : p2;
+                }
+                if (seed >= 0) {
+                    const float xa = Xf[(size_t)pa * ldf + seed], xb = Xf[(size_t)pb * ldf + seed];
+                    const float sv = (q & 1) ? __fsub_rn(xa, xb) : __fadd_rn(xa, xb);
+                    if (imx < 0 || sv > vmx || (sv == vmx && seed < imx)) { vmx = sv; imx = seed; }
+                    if (imn < 0 || sv < vmn || (sv == vmn && seed < imn)) { vmn = sv; imn = seed; }
+                }
+                add(imn);
+                add(imx);
+            }
+        }
         for (int q = nr; q < f.RM; ++q) rp[q] = -1;
         nreps[(size_t)b * K + k] = nr;
         T *rx = repx + ((size_t)b * K + k) * f.RM * D;
@@ -1006,6 +1040,9 @@ Margins make_margins(kc_ctx *c, double alpha, double beta_glob)
 
 int reps_cap(int D, int cap) { return std::min(cap, std::min(kMaxReps, 2 * D + 1)); }
 
+// Attribute-pair directions of the representatives: 2 min(D(D-1)/2, 16).
+int pair_dirs(int D) { return 2 * std::min(D * (D - 1) / 2, kMaxPairs); }
+
 template <typename T, int KM, int DM, int RMX>
 kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi_, int B, double alpha,
                        const int64_t *seeds, int cap, void *lo_out_, void *hi_out_, int64_t *counts, int64_t *cand_out,
@@ -1089,6 +1126,8 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     fa.seed_defl = sizeof(T) == 4 ? 1.0 - gamma_n(f64_roundings(D), kU64) : 1.0;
     fa.cap = std::min(reps_cap(D, cap), RM);
     fa.RM = RM;
+    fa.ndir = 0;
+    fa.dmax = fa.dmin = nullptr;
     finalize_a_kernel<T><<<(B + 127) / 128, 128, 0, c->stream>>>(
         B, K_, D, lo, hi, lbkey, amax, amin, flags, static_cast<const T *>(c->X), c->ldx, fa, blo, bhi, reps, nreps,
         repx, have, lb, lb_raw, lbarg);
@@ -1134,17 +1173,20 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
 }
 
 // The wide path (float data, K <= 16, D <= 64): the workspace, finalize
-// kernels and outputs of tighten_impl, passes A and B from kc_wide.cu, and
-// min(ball_cap, 2D + 1, 50) representatives per cluster.
+// kernels and outputs of tighten_impl, passes A and B from kc_wide.cu.
+// Representatives per cluster: min(cap, 2D + 1, 50) along the attributes, or,
+// with `dirs`, up to min(cap, 50) with the attribute-pair directions after
+// the attributes.
 kc_status tighten_wide(kc_ctx *c, const View &v, const void *lo_, const void *hi_, int B, double alpha,
-                       const int64_t *seeds, int cap, void *lo_out_, void *hi_out_, int64_t *counts, int64_t *cand_out,
-                       double *lb, double *lb_raw, int64_t *lbarg, int8_t *status, VisitScratch *vs,
+                       const int64_t *seeds, int cap, bool dirs, void *lo_out_, void *hi_out_, int64_t *counts,
+                       int64_t *cand_out, double *lb, double *lb_raw, int64_t *lbarg, int8_t *status, VisitScratch *vs,
                        const ListBatch *L = nullptr)
 {
     using T = float;
     using KY = unsigned long long;
     const int K_ = c->K, D = c->D;
-    const int RM = std::max(1, reps_cap(D, cap));
+    const int ndir = dirs ? pair_dirs(D) : 0;
+    const int RM = std::max(1, dirs ? std::min(std::min(cap, kMaxReps), 1 + 2 * D + 2 * ndir) : reps_cap(D, cap));
     const T *lo = static_cast<const T *>(lo_);
     const T *hi = static_cast<const T *>(hi_);
     const size_t KD = (size_t)B * K_ * D, BK = (size_t)B * K_;
@@ -1160,10 +1202,12 @@ kc_status tighten_wide(kc_ctx *c, const View &v, const void *lo_, const void *hi
     const size_t o_have = take(B * 4), o_cnt = take(BK * 8), o_smax = take(KD * 4);
     const size_t o_smin = take(KD * 4), o_jmax = take(KD * 4);
     const size_t o_jmin = take(KD * 4), o_cand = take(BK * sizeof(KY));
+    const size_t o_dmax = take(BK * ndir * sizeof(KY)), o_dmin = take(BK * ndir * sizeof(KY));
     KC_TRY(ensure(c, vs->buf, off));
     char *w = static_cast<char *>(vs->buf.p);
     KY *lbkey = reinterpret_cast<KY *>(w + o_lbkey), *amax = reinterpret_cast<KY *>(w + o_amax);
     KY *amin = reinterpret_cast<KY *>(w + o_amin), *cand = reinterpret_cast<KY *>(w + o_cand);
+    KY *dmax = reinterpret_cast<KY *>(w + o_dmax), *dmin = reinterpret_cast<KY *>(w + o_dmin);
     unsigned *flags = reinterpret_cast<unsigned *>(w + o_flags);
     T *blo = reinterpret_cast<T *>(w + o_blo), *bhi = reinterpret_cast<T *>(w + o_bhi);
     int64_t *reps = reinterpret_cast<int64_t *>(w + o_reps);
@@ -1180,7 +1224,7 @@ kc_status tighten_wide(kc_ctx *c, const View &v, const void *lo_, const void *hi
 
     const Margins mg = make_margins(c, alpha, 0.0);
     const double r_up = nextafter(std::sqrt(alpha), __builtin_huge_val());
-    KC_TRY(launch_wide_a(c, v, L, lo, hi, B, mg, lbkey, amax, amin, flags));
+    KC_TRY(launch_wide_a(c, v, L, lo, hi, B, mg, lbkey, amax, amin, flags, ndir, dmax, dmin));
     FinA fa;
     fa.seeds = seeds;
     fa.ids = L ? nullptr : v.ids;
@@ -1191,6 +1235,9 @@ kc_status tighten_wide(kc_ctx *c, const View &v, const void *lo_, const void *hi
     fa.seed_defl = 1.0 - gamma_n(f64_roundings(D), kU64);
     fa.cap = RM;
     fa.RM = RM;
+    fa.ndir = ndir;
+    fa.dmax = dmax;
+    fa.dmin = dmin;
     finalize_a_kernel<T><<<(B + 127) / 128, 128, 0, c->stream>>>(
         B, K_, D, lo, hi, lbkey, amax, amin, flags, static_cast<const T *>(c->X), c->ldx, fa, blo, bhi, reps, nreps,
         repx, have, lb, lb_raw, lbarg);
@@ -1217,7 +1264,12 @@ kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const vo
 {
     if (B <= 0) return KC_OK;
     const int cap = ball_cap > 0 ? ball_cap : 50;
+    // ball_cap above 2D + 1: representatives along pair directions too (wide kernels)
+    const bool dirs = ball_cap > 2 * c->D + 1 && c->D >= 2;
     if (c->dt == KC_F32) {
+        if (dirs)
+            return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, true, lo_out, hi_out, counts, cand, lb, lb_raw,
+                                lbarg, status, vs);
         if (c->K == 3 && c->D == 3)
             return tighten_impl<float, 3, 3, 7>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
                                                 lb, lb_raw, lbarg, status, vs);
@@ -1233,9 +1285,13 @@ kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const vo
         if (c->K <= 2 && c->D <= 8)
             return tighten_impl<float, 2, 8, 17>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
                                                  lb, lb_raw, lbarg, status, vs);
-        return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb, lb_raw, lbarg,
-                            status, vs);
+        return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, false, lo_out, hi_out, counts, cand, lb, lb_raw,
+                            lbarg, status, vs);
     }
+    if (dirs)
+        return set_err(c, KC_EINVAL,
+                       "kc_tighten: ball_cap above 2D + 1 (pair-direction representatives) needs float data "
+                       "(ball_cap=%d, D=%d)", ball_cap, c->D);
     if (c->K <= 4 && c->D <= 2)
         return tighten_impl<double, 4, 2, 5>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
                                              lb_raw, lbarg, status, vs);
@@ -1254,6 +1310,9 @@ kc_status launch_tighten_list(kc_ctx *c, const ListBatch &L, const void *lo, con
     if (c->dt != KC_F32) return set_err(c, KC_EINTERNAL, "list-mode tightening is for float data");
     const int cap = ball_cap > 0 ? ball_cap : 50;
     const View v = full_view(c);
+    if (ball_cap > 2 * c->D + 1 && c->D >= 2)
+        return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, true, lo_out, hi_out, counts, cand, lb, lb_raw,
+                            lbarg, status, vs, &L);
     if (c->K == 3 && c->D == 3)
         return tighten_impl<float, 3, 3, 7>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
                                             lb_raw, lbarg, status, vs, &L);
@@ -1269,8 +1328,8 @@ kc_status launch_tighten_list(kc_ctx *c, const ListBatch &L, const void *lo, con
     if (c->K <= 2 && c->D <= 8)
         return tighten_impl<float, 2, 8, 17>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
                                              lb_raw, lbarg, status, vs, &L);
-    return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb, lb_raw, lbarg,
-                        status, vs, &L);
+    return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, false, lo_out, hi_out, counts, cand, lb, lb_raw,
+                        lbarg, status, vs, &L);
 }
 
 kc_status launch_sample_reduction_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int M,

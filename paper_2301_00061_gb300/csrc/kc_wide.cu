@@ -105,20 +105,34 @@ __device__ __forceinline__ void wide_stage(const float *__restrict__ X, int64_t 
 // Shared memory: tile [D][tile] u64 | boxes [K][D] u64 | amax, amin [K][D] u64
 // | lbkey u64 | flag.
 
+// Directions after the attributes (the representatives' pair directions):
+// direction q of ndir is attribute pair q / 2 (pairs a < b in lexicographic
+// order, a in pa, b in pb), as x_a + x_b (q even) or x_a - x_b (q odd), in float.
+struct WideDirs {
+    int ndir;
+    const signed char *pa, *pb;   // shared memory [ndir / 2]
+    unsigned long long *sdmax, *sdmin;
+    unsigned long long *__restrict__ dmax, *__restrict__ dmin;   // global [B][K][ndir]
+};
+
 __device__ __forceinline__ void wide_a_node(const uint64_t *tp, int tile, int tn, const uint32_t *tids, int64_t base,
                             const float *__restrict__ lo, const float *__restrict__ hi, int b, int K, int D,
                             const Margins &mg, uint64_t *sbx, unsigned long long *samax,
                             unsigned long long *samin, unsigned long long *slb, unsigned *sflag,
                             unsigned long long *__restrict__ lbkey, unsigned long long *__restrict__ amax,
-                            unsigned long long *__restrict__ amin, unsigned *__restrict__ flags)
+                            unsigned long long *__restrict__ amin, unsigned *__restrict__ flags, const WideDirs &dv)
 {
-    const int KD = K * D;
+    const int KD = K * D, KQ = K * dv.ndir;
     __syncthreads();   // the previous node's readers are done
     for (int i = threadIdx.x; i < KD; i += kWT) {
         const size_t o = (size_t)b * KD + i;
         sbx[i] = pk(lo[o], -hi[o]);
         samax[i] = 0ull;
         samin[i] = 0ull;
+    }
+    for (int i = threadIdx.x; i < KQ; i += kWT) {
+        dv.sdmax[i] = 0ull;
+        dv.sdmin[i] = 0ull;
     }
     if (threadIdx.x == 0) {
         *slb = 0ull;
@@ -139,12 +153,20 @@ __device__ __forceinline__ void wide_a_node(const uint64_t *tp, int tile, int tn
         const unsigned long long key = wkey_max(bmin, pos);
         best = key > best ? key : best;
         if (left == 0) infeasible = true;
-        if (left == 1)
+        if (left == 1) {
             for (int a = 0; a < D; ++a) {
                 const float x = upk(tp[(size_t)a * tile + j]).x;
                 smax_u64(&samax[k1 * D + a], wkey_max(x, pos));
                 smax_u64(&samin[k1 * D + a], wkey_min(x, pos));
             }
+            for (int q = 0; q < dv.ndir; ++q) {
+                const float xa = upk(tp[(size_t)dv.pa[q >> 1] * tile + j]).x;
+                const float xb = upk(tp[(size_t)dv.pb[q >> 1] * tile + j]).x;
+                const float v = (q & 1) ? xa - xb : xa + xb;
+                smax_u64(&dv.sdmax[k1 * dv.ndir + q], wkey_max(v, pos));
+                smax_u64(&dv.sdmin[k1 * dv.ndir + q], wkey_min(v, pos));
+            }
+        }
     }
     best = warp_max_u64(best);
     if ((threadIdx.x & 31) == 0 && best) smax_u64(slb, best);
@@ -155,26 +177,43 @@ __device__ __forceinline__ void wide_a_node(const uint64_t *tp, int tile, int tn
         if (samax[i]) atomicMax(&amax[o], samax[i]);
         if (samin[i]) atomicMax(&amin[o], samin[i]);
     }
+    for (int i = threadIdx.x; i < KQ; i += kWT) {
+        const size_t o = (size_t)b * KQ + i;
+        if (dv.sdmax[i]) atomicMax(&dv.dmax[o], dv.sdmax[i]);
+        if (dv.sdmin[i]) atomicMax(&dv.dmin[o], dv.sdmin[i]);
+    }
     if (threadIdx.x == 0) {
         if (*slb) atomicMax(&lbkey[b], *slb);
         if (*sflag) atomicOr(&flags[b], 1u);
     }
 }
 
-__global__ void __launch_bounds__(kWT)
+__global__ void __launch_bounds__(kWT, 2)
 wide_a_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int tile, ListBatch L, int B, int K, int D,
               const float *__restrict__ lo, const float *__restrict__ hi, Margins mg,
               unsigned long long *__restrict__ lbkey, unsigned long long *__restrict__ amax,
-              unsigned long long *__restrict__ amin, unsigned *__restrict__ flags)
+              unsigned long long *__restrict__ amin, unsigned *__restrict__ flags, int ndir,
+              unsigned long long *__restrict__ dmax, unsigned long long *__restrict__ dmin)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int KD = K * D;
+    const int KD = K * D, KQ = K * ndir;
     uint64_t *tp = reinterpret_cast<uint64_t *>(smem);
     uint64_t *sbx = tp + (size_t)D * tile;
-    unsigned long long *samax = reinterpret_cast<unsigned long long *>(sbx + KD), *samin = samax + KD,
-                       *slb = samin + KD;
+    unsigned long long *samax = reinterpret_cast<unsigned long long *>(sbx + KD), *samin = samax + KD;
+    unsigned long long *sdmax = samin + KD, *sdmin = sdmax + KQ, *slb = sdmin + KQ;
     unsigned *sflag = reinterpret_cast<unsigned *>(slb + 1);
-    uint32_t *tids = reinterpret_cast<uint32_t *>(sflag + 2);
+    signed char *pa = reinterpret_cast<signed char *>(sflag + 2), *pb = pa + 16;
+    uint32_t *tids = reinterpret_cast<uint32_t *>(pa + 32);
+    if (threadIdx.x == 0) {
+        // the attribute pairs a < b in lexicographic order
+        int p = 0;
+        for (int a = 0; a < D && p < ndir / 2; ++a)
+            for (int c = a + 1; c < D && p < ndir / 2; ++c, ++p) {
+                pa[p] = (signed char)a;
+                pb[p] = (signed char)c;
+            }
+    }
+    const WideDirs dv{ndir, pa, pb, sdmax, sdmin, dmax, dmin};
     if (L.pool) {
         for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
             int g;
@@ -189,7 +228,7 @@ wide_a_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int tile, List
             const int n0 = L.node_start ? L.node_start[g] : g, n1 = L.node_start ? L.node_start[g + 1] : g + 1;
             for (int b = n0; b < n1; ++b)
                 wide_a_node(tp, tile, tn, tids, 0, lo, hi, b, K, D, mg, sbx, samax, samin, slb, sflag, lbkey, amax,
-                            amin, flags);
+                            amin, flags, dv);
         }
     } else {
         for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
@@ -198,7 +237,7 @@ wide_a_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int tile, List
             wide_stage(X, ld, D, tile, tn, base, nullptr, tp);
             for (int b = 0; b < B; ++b)
                 wide_a_node(tp, tile, tn, nullptr, base, lo, hi, b, K, D, mg, sbx, samax, samin, slb, sflag, lbkey,
-                            amax, amin, flags);
+                            amax, amin, flags, dv);
         }
     }
 }
@@ -374,11 +413,14 @@ size_t wide_b_node_bytes(int K, int D)
 // (tighten_common in kc_visit.cu) owns the workspace and the finalize kernels.
 kc_status launch_wide_a(kc_ctx *c, const View &v, const ListBatch *L, const float *lo, const float *hi, int B,
                         const Margins &mg, unsigned long long *lbkey, unsigned long long *amax,
-                        unsigned long long *amin, unsigned *flags)
+                        unsigned long long *amin, unsigned *flags, int ndir, unsigned long long *dmax,
+                        unsigned long long *dmin)
 {
     const int K = c->K, D = c->D, KD = K * D;
+    if (ndir > 32) return set_err(c, KC_EINTERNAL, "wide tightening: at most 16 attribute pairs");
     const int tile = (int)std::max<int64_t>(64, std::min<int64_t>(1024, (48 * 1024) / (8 * (int64_t)D)) / 32 * 32);
-    const size_t smem = (size_t)D * tile * 8 + (size_t)KD * 24 + 16 + (size_t)tile * 4 + 16;
+    const size_t smem = (size_t)D * tile * 8 + (size_t)KD * 24 + (size_t)K * ndir * 16 + 16 + 32 + (size_t)tile * 4 +
+                        16;
     if (smem > 48 * 1024)
         KC_CUDA(c, cudaFuncSetAttribute(wide_a_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -389,7 +431,7 @@ kc_status launch_wide_a(kc_ctx *c, const View &v, const ListBatch *L, const floa
     if (work <= 0) return KC_OK;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(work, (int64_t)per_sm * c->num_sms));
     wide_a_kernel<<<grid, kWT, smem, c->stream>>>(static_cast<const float *>(v.X), v.ld, v.n, tile, L ? *L : Lz, B,
-                                                  K, D, lo, hi, mg, lbkey, amax, amin, flags);
+                                                  K, D, lo, hi, mg, lbkey, amax, amin, flags, ndir, dmax, dmin);
     return after_launch(c, "tighten pass A (wide)");
 }
 

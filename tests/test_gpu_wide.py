@@ -9,8 +9,13 @@ is a multiple of 1/16 computed exactly in float (D <= 64, coordinates below
 64 in magnitude), and alpha is an odd multiple of 1/32: float and double
 take every decision alike and statuses, boxes and counts must equal the
 oracle's (candidates, nearest to an off-grid midpoint, within the float
-argmin's error).  The representatives are min(ball_cap, 2D + 1, 50) per
-cluster on both sides, so D = 29 exercises the cap of 50.
+argmin's error).  The representatives are the seed and the attribute
+extremes, then, for ball_cap above 2D + 1, the extremes of x_a + x_b and
+x_a - x_b over the first 16 attribute pairs, at most min(ball_cap, 50) per
+cluster on both sides: D = 29 exercises the cap of 50 within the attribute
+extremes, D = 2 .. 16 with ball_cap = 50 the pair directions.  Sums and
+differences of grid coordinates are exact in float, so they order samples
+alike on both sides.
 """
 import numpy as np
 import pytest
@@ -120,3 +125,57 @@ def test_wide_solve_matches_oracle(n, d, k, seed):
     assert g["status"] == 0 and r["status"] == 0
     assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
     assert oracle.objective(X, g["centers"])[0] == g["objective"]
+
+
+@pytest.mark.parametrize("n,d,k,cap,seeded", [
+    (8_000, 2, 3, 9, False), (8_000, 2, 4, 50, True), (6_000, 3, 3, 12, True), (6_000, 3, 3, 50, False),
+    (6_000, 4, 3, 25, False), (6_000, 4, 4, 50, True), (5_000, 5, 3, 50, False)])
+def test_pair_direction_representatives_on_grid(n, d, k, cap, seeded):
+    """ball_cap above 2D + 1 on shapes that otherwise run the register
+    kernels (K <= 4, D <= 4): the pair-direction representatives change the
+    tightened boxes and counts, and the kernels match the oracle exactly."""
+    X, c, fobj, lo, hi = _grid_case(n, d, k, seed=3 * d + k, B=10, scale=(0.05, 0.5))
+    kc = KCenter(_t(X), k)
+    seeds = np.array(c, np.int64) if seeded else None
+    feasible = changed = 0
+    for f in (0.8, 0.95, 1.02, 1.2):
+        alpha = (np.round(fobj * f * 16) + 0.5) / 16
+        g = kc.tighten(_t(lo), _t(hi), alpha, seeds=None if seeds is None else _t(seeds), ball_cap=cap)
+        torch.cuda.synchronize()
+        feasible += _compare(X, lo, hi, alpha, seeds, g, cap)
+        for b in range(lo.shape[0]):
+            r = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=True, ball_cap=cap)
+            r0 = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=True)
+            if r["status"] != 1 and (not np.array_equal(r["count"], r0["count"])
+                                     or not np.array_equal(r["lo"], r0["lo"])
+                                     or not np.array_equal(r["hi"], r0["hi"])):
+                changed += 1
+    assert feasible >= 5
+    assert changed >= 1, "the case does not tell the direction representatives from the attribute ones"
+
+
+@pytest.mark.parametrize("n,d,k,seed", [(2_000, 2, 3, 1), (2_000, 3, 3, 2), (1_500, 4, 4, 1)])
+def test_solve_with_pair_direction_representatives(n, d, k, seed):
+    """A solve with ball_cap = 50 (per-node lists, wide kernels) reaches the
+    oracle's certified optimum under the same budget."""
+    X = _blobs(n, d, k, seed)
+    kc = KCenter(_t(X), k)
+    g = kc.solve(tol=1e-12, time_limit_s=120.0, ball_cap=50)
+    r = oracle.solve(X, k, tol=1e-12, ball_cap=50)
+    assert g["status"] == 0 and r["status"] == 0
+    assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
+    assert oracle.objective(X, g["centers"])[0] == g["objective"]
+
+
+def test_pair_directions_refused_for_double_data():
+    X = _blobs(500, 2, 3, 1, dtype=np.float64)
+    kc = KCenter(_t(X), 3)
+    lo = np.broadcast_to(X.min(0), (1, 3, 2)).copy()
+    hi = np.broadcast_to(X.max(0), (1, 3, 2)).copy()
+    g = kc.tighten(_t(lo), _t(hi), 10.0, ball_cap=5)    # 2D + 1: the attribute extremes
+    torch.cuda.synchronize()
+    assert g["status"].cpu().numpy()[0] in (0, 1, 2)
+    with pytest.raises(RuntimeError, match="float data"):
+        kc.tighten(_t(lo), _t(hi), 10.0, ball_cap=6)
+    with pytest.raises(RuntimeError, match="float data"):
+        kc.solve(tol=1e-12, ball_cap=50)
