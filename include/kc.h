@@ -283,15 +283,13 @@ kc_status kc_fp32_probe(int32_t mode, void *stream, double *lane_ops_per_s, floa
  *   lb_out          [B] double certified lower bound of the input boxes, or NULL.
  *   status          [B] int8: 0 feasible, 1 proved to hold no solution of
  *                   value <= alpha, 2 leaf (every tightened box is a point).
- * ball_cap (the representatives' budget, "at most 50 balls" of Section
- * 4.1.2; ties go to the smaller sample index, duplicates are skipped):
- *   <= 0            the seed and the attribute extremes: min(2D + 1, 50);
- *   1 .. 2D + 1     the first ball_cap of those;
- *   above 2D + 1    (D >= 2, float data only) then the arg-min and arg-max
- *                   of x_a + x_b and of x_a - x_b (added in float) for the
- *                   first min(D(D-1)/2, 16) pairs a < b in lexicographic
- *                   order, up to min(ball_cap, 50) in all; these run on the
- *                   shared-memory kernels below.  Double data: KC_EINVAL.
+ * ball_cap: the representatives' budget ("at most 50 balls" of Section
+ * 4.1.2), at most min(ball_cap, 50) per cluster; <= 0 selects the default
+ * of 50.  In order: the seed, the arg-min and arg-max of each attribute,
+ * then, for float data, the arg-min and arg-max of x_a + x_b and of
+ * x_a - x_b (added in float) for the first min(D(D-1)/2, 16) pairs a < b in
+ * lexicographic order; ties go to the smaller sample index, duplicates are
+ * skipped.  Double data stop after the attribute extremes (2D + 1).
  * Shapes: float data any K <= 16 and D <= 64 (K <= 4 with D <= 4 and K <= 2
  * with D <= 8 run kernels with the node's state in registers, compiled per
  * shape; the others kernels whose node state lives in shared memory sized at
@@ -362,7 +360,7 @@ typedef struct {
     double time_limit_s;   /* 0: none */
     int64_t node_limit;    /* 0: none */
     int32_t batch;         /* 0: automatic; nodes bounded per launch */
-    int32_t ball_cap;      /* 0: representatives per cluster, as kc_tighten's ball_cap */
+    int32_t ball_cap;      /* 50: representatives per cluster, as kc_tighten's ball_cap */
     int32_t i_sr;          /* 1: sample reduction every i_sr batches, 0: off */
     int32_t use_bt;        /* 1: assignment + bounds tightening (BB+CF+BT); 0: BB+CF */
     int32_t order;         /* 0: best bound, max-range branching; 1: learned scorer (kc_set_scorer) */

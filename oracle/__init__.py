@@ -266,9 +266,9 @@ def bruteforce(X, k):
 
 def tighten(X, lo, hi, alpha, seeds=None, active=None, is_f32=False, ball_cap=0):
     """Cluster assignment + bounds tightening of one node; returns a dict.
-    ball_cap <= 0: representatives are the seed and the attribute extremes
-    (at most 2D + 1); ball_cap > 0: up to min(ball_cap, 50), the extremes
-    along attribute-pair directions after those."""
+    Representatives per cluster: at most min(ball_cap, 50) (ball_cap <= 0:
+    50), the seed, then the extremes along the attributes, then, for float
+    data, along attribute-pair directions."""
     X, lo, hi = _f64(X), _f64(lo), _f64(hi)
     n, d = X.shape
     k = lo.shape[0]

@@ -436,9 +436,10 @@ typedef struct {
  * the "at most 50 balls" of Section 4.1.2): the seed of cluster k (if seeds
  * exist), then the assigned samples attaining the minimum and the maximum of
  * x along a fixed list of directions -- first the D attributes (x_a), then,
- * when `diag`, the first P = min(D(D-1)/2, 16) attribute pairs a < b in
+ * for float data, the first P = min(D(D-1)/2, 16) attribute pairs a < b in
  * lexicographic order, each as x_a + x_b and then x_a - x_b -- smallest index
- * on ties, duplicates skipped, at most `cap` of them.  Arrays hold those
+ * on ties, duplicates skipped, at most `cap` of them (for double data the
+ * list stops after the attributes).  Arrays hold those
  * arg-extremes (-1 if none): amin_idx/amax_idx [D], dmin_idx/dmax_idx [2P]
  * (sum of pair p at 2p, difference at 2p + 1). */
 #define KCO_MAXPAIRS 16
@@ -514,11 +515,10 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
                 int ball_cap, kco_tighten_out *out)
 {
     if (K > KCO_MAXK || D > KCO_MAXD) return 1;
-    /* ball_cap <= 0: the seed and the attribute extremes (at most 2D + 1);
-     * otherwise up to ball_cap (at most 50) with the pair directions after them */
-    const int diag = ball_cap > 0;
-    if (ball_cap <= 0) ball_cap = 2 * D + 1;
-    if (ball_cap > KCO_MAXREPS) ball_cap = KCO_MAXREPS;
+    /* at most ball_cap representatives (<= 0: the default of 50, which is
+     * also the largest); pair directions for float data only */
+    const int diag = is_f32 != 0;
+    if (ball_cap <= 0 || ball_cap > KCO_MAXREPS) ball_cap = KCO_MAXREPS;
     const int npairs = D * (D - 1) / 2 < KCO_MAXPAIRS ? D * (D - 1) / 2 : KCO_MAXPAIRS;
     const int ndir = diag ? 2 * npairs : 0;
     const int KD = K * D;
@@ -759,7 +759,7 @@ typedef struct {
     int32_t use_bt;      /* 1: BB+CF+BT (assignment, tightening); 0: BB+CF */
     int32_t use_sr;      /* sample reduction (Algorithm 5) */
     int32_t i_sr;        /* run sample reduction every i_sr iterations */
-    int32_t ball_cap;    /* representatives per cluster: <= 0 the attribute extremes (2D + 1), else up to 50 */
+    int32_t ball_cap;    /* representatives per cluster, at most 50 (<= 0: 50) */
     int32_t is_f32;      /* data are float values promoted to double */
     int64_t seed;        /* FFT start = seed mod N */
     int64_t node_limit;  /* 0: none */

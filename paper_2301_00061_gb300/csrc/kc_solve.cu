@@ -1417,7 +1417,7 @@ void kc_solve_defaults(kc_solve_opts *o)
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
     o->tol = 1e-12;
-    o->ball_cap = 0;
+    o->ball_cap = 50;
     o->i_sr = 1;
     o->use_bt = 1;
     o->lists = 1;
@@ -1438,8 +1438,6 @@ kc_status kc_solve(kc_ctx *c, double tol, const kc_solve_opts *opt, kc_result *o
     if (o.order == 1 && !c->scorer) return set_err(c, KC_EINVAL, "kc_solve: order = 1 needs kc_set_scorer");
     if (o.lists != 0 && o.lists != 1) return set_err(c, KC_EINVAL, "kc_solve: lists must be 0 or 1");
     if (o.arena_mb < 0) return set_err(c, KC_EINVAL, "kc_solve: arena_mb must be >= 0");
-    if (o.use_bt && c->dt != KC_F32 && o.ball_cap > 2 * c->D + 1 && c->D >= 2)
-        return set_err(c, KC_EINVAL, "kc_solve: ball_cap above 2D + 1 needs float data");
     if (o.explore < 0 || o.explore > 100) return set_err(c, KC_EINVAL, "kc_solve: explore must be in [0, 100]");
     if (!(o.rule_margin >= 0.0)) return set_err(c, KC_EINVAL, "kc_solve: rule_margin must be >= 0");
     if (o.fft_starts < 0 || o.fft_starts > 4096) return set_err(c, KC_EINVAL, "kc_solve: fft_starts must be in [0, 4096]");

@@ -187,18 +187,35 @@ __device__ __forceinline__ bool proved_lt(float dhat, float infl, float slack, f
 // (j = j0, j0 + step, ... < tn).  Keys name a sample by tids[j] when the tile
 // was gathered from a list of sample ids, else by its position base + j.
 
+// Pair directions (float data): dv.ndir > 0 also keeps, per cluster, the
+// arg-extreme keys of x_a + x_b and x_a - x_b (added in float) over the
+// assigned samples for the first ndir / 2 attribute pairs a < b in
+// lexicographic order, in the warp's shared-memory slot sdk [K][ndir][2]
+// (max, min), merged into dmax / dmin [B][K][ndir] at the end of the node.
+struct DirKeys {
+    int ndir;
+    unsigned long long *sdk;
+    unsigned long long *__restrict__ dmax, *__restrict__ dmin;
+};
+
 template <typename T, int KM, int DM>
 __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td, int tile, int tn, int j0, int step,
                                             const uint32_t *tids, int64_t base, const T *__restrict__ lo,
                                             const T *__restrict__ hi, int b, int K, int D, double alpha,
                                             const Margins &mg, typename Key<T>::K *__restrict__ lbkey,
                                             typename Key<T>::K *__restrict__ amax, typename Key<T>::K *__restrict__ amin,
-                                            unsigned *__restrict__ flags)
+                                            unsigned *__restrict__ flags, const DirKeys &dk)
 {
     using KT = Key<T>;
     using KY = typename KT::K;
     constexpr bool F32 = sizeof(T) == 4;
     const int lane = threadIdx.x & 31;
+    if constexpr (F32) {
+        if (dk.ndir > 0) {
+            for (int i = lane; i < K * dk.ndir * 2; i += 32) dk.sdk[i] = 0ull;
+            __syncwarp();
+        }
+    }
     // node boxes into registers
     uint64_t bx[KM][DM];
     double blo[KM][DM], bhi[KM][DM];
@@ -266,6 +283,26 @@ __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td
                             acc_min[k][a] = kmax<T>(acc_min[k][a], KT::min_of(x[a], pos));
                         }
                 }
+            if constexpr (F32) {
+                if (dk.ndir > 0) {
+                    unsigned long long *s = dk.sdk + (size_t)k1 * dk.ndir * 2;
+                    int q = 0;
+#pragma unroll
+                    for (int a = 0; a < DM; ++a)
+#pragma unroll
+                        for (int c = a + 1; c < DM; ++c)
+                            if (c < D && q < dk.ndir) {
+                                const float vs = __fadd_rn(x[a], x[c]), vd = __fsub_rn(x[a], x[c]);
+                                const KY k0 = KT::max_of(vs, pos), k1_ = KT::min_of(vs, pos);
+                                const KY k2 = KT::max_of(vd, pos), k3 = KT::min_of(vd, pos);
+                                if (k0 > s[2 * q]) atomicMax(&s[2 * q], k0);
+                                if (k1_ > s[2 * q + 1]) atomicMax(&s[2 * q + 1], k1_);
+                                if (k2 > s[2 * q + 2]) atomicMax(&s[2 * q + 2], k2);
+                                if (k3 > s[2 * q + 3]) atomicMax(&s[2 * q + 3], k3);
+                                q += 2;
+                            }
+                }
+            }
         }
     }
     // warp reduction, then one atomic per accumulator and warp
@@ -283,6 +320,17 @@ __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td
                 if (lane == 0 && !KT::is_none(m2)) KT::atomic_max(&amin[o], m2, &flags[b]);
             }
     if (__any_sync(0xffffffffu, infeasible) && lane == 0) atomicOr(&flags[b], 1u);
+    if constexpr (F32) {
+        if (dk.ndir > 0) {
+            __syncwarp();
+            for (int i = lane; i < K * dk.ndir; i += 32) {
+                const size_t o = (size_t)b * K * dk.ndir + i;
+                if (dk.sdk[2 * i]) atomicMax(&dk.dmax[o], dk.sdk[2 * i]);
+                if (dk.sdk[2 * i + 1]) atomicMax(&dk.dmin[o], dk.sdk[2 * i + 1]);
+            }
+            __syncwarp();   // the slot is rewritten by the warp's next node
+        }
+    }
 }
 
 // Stages samples of a tile in shared memory: float data as (x, -x) pairs,
@@ -306,12 +354,16 @@ __global__ void __launch_bounds__(kThreads)
 visit_a_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, const T *__restrict__ lo,
                const T *__restrict__ hi, int B, int K, int D, double alpha, Margins mg,
                typename Key<T>::K *__restrict__ lbkey, typename Key<T>::K *__restrict__ amax,
-               typename Key<T>::K *__restrict__ amin, unsigned *__restrict__ flags)
+               typename Key<T>::K *__restrict__ amin, unsigned *__restrict__ flags, int ndir,
+               unsigned long long *__restrict__ dmax, unsigned long long *__restrict__ dmin)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *tp = reinterpret_cast<uint64_t *>(smem);
     double *td = reinterpret_cast<double *>(smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // per-warp direction keys after the tile
+    const DirKeys dk{ndir, reinterpret_cast<unsigned long long *>(smem + (size_t)D * tile * 8) + (size_t)warp * K * ndir * 2,
+                     dmax, dmin};
     for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
         const int tn = (int)((n - base) < (int64_t)tile ? (n - base) : (int64_t)tile);
         __syncthreads();
@@ -319,7 +371,7 @@ visit_a_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, const T
         __syncthreads();
         for (int b = warp; b < B; b += NWV)
             pass_a_node<T, KM, DM>(tp, td, tile, tn, lane, 32, nullptr, base, lo, hi, b, K, D, alpha, mg, lbkey, amax,
-                                   amin, flags);
+                                   amin, flags, dk);
     }
 }
 
@@ -330,13 +382,16 @@ __global__ void __launch_bounds__(kThreads, 2)
 visit_a_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile,
                     const T *__restrict__ lo, const T *__restrict__ hi, int K, int D, double alpha, Margins mg,
                     typename Key<T>::K *__restrict__ lbkey, typename Key<T>::K *__restrict__ amax,
-                    typename Key<T>::K *__restrict__ amin, unsigned *__restrict__ flags)
+                    typename Key<T>::K *__restrict__ amin, unsigned *__restrict__ flags, int ndir,
+                    unsigned long long *__restrict__ dmax, unsigned long long *__restrict__ dmin)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *tp = reinterpret_cast<uint64_t *>(smem);
     double *td = reinterpret_cast<double *>(smem);
     uint32_t *tids = reinterpret_cast<uint32_t *>(smem + (size_t)D * tile * 8);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // per-warp direction keys after the ids (tile is a multiple of 32)
+    const DirKeys dk{ndir, reinterpret_cast<unsigned long long *>(tids + tile) + (size_t)warp * K * ndir * 2, dmax, dmin};
     for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
         int b;
         int64_t st;
@@ -355,7 +410,7 @@ visit_a_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile,
         if (team < teams)
             for (int nd = n0 + team; nd < n1; nd += teams)
                 pass_a_node<T, KM, DM>(tp, td, tile, tn, (warp % wpt) * 32 + lane, wpt * 32, tids, 0, lo, hi, nd, K, D,
-                                       alpha, mg, lbkey, amax, amin, flags);
+                                       alpha, mg, lbkey, amax, amin, flags, dk);
     }
 }
 
@@ -544,10 +599,15 @@ struct PBSlot {
 __device__ __forceinline__ unsigned to_ord(float v) { return ord_f32(v); }
 __device__ __forceinline__ unsigned long long to_ord(double v) { return ord_f64(v); }
 
-template <typename T, int KM, int DM, int RMX>
+// Words of one staged representative: float data packs coordinate pairs
+// (DM + 1) / 2 u64, double data keeps DM values.
+template <typename T, int DM>
+constexpr int rep_words() { return sizeof(T) == 4 ? (DM + 1) / 2 : DM; }
+
+template <typename T, int KM, int DM>
 __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int jstart, int wstep, const uint32_t *tids,
                                             const uint32_t *__restrict__ ids, int64_t base, uint32_t *list,
-                                            PBSlot<T, KM, DM> *ws, int b, int K, int D, int RM,
+                                            PBSlot<T, KM, DM> *ws, uint64_t *wrep, int b, int K, int D, int RM,
                                             const T *__restrict__ lo_in, const T *__restrict__ hi_in,
                                             const T *__restrict__ blo, const T *__restrict__ bhi,
                                             const T *__restrict__ repx, const int *__restrict__ nreps,
@@ -585,7 +645,27 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
 #pragma unroll
     for (int k = 0; k < KM; ++k) nr[k] = k < K ? nreps[(size_t)b * K + k] : 0;
     const bool have = allhave[b] != 0;
-    const T *rxb = repx + (size_t)b * K * RM * D;
+    // the node's representatives into the warp's slot wrep [K][RM][words]
+    constexpr int RW = rep_words<T, DM>();
+    {
+        const T *rxb = repx + (size_t)b * K * RM * D;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            if (k >= K) continue;
+            const T *src = rxb + (size_t)k * RM * D;
+            for (int i = lane; i < nr[k] * RW; i += 32) {
+                const int r = i / RW, p = i - r * RW;
+                if constexpr (F32) {
+                    const float v0 = 2 * p < D ? (float)src[(size_t)r * D + 2 * p] : 0.f;
+                    const float v1 = 2 * p + 1 < D ? (float)src[(size_t)r * D + 2 * p + 1] : 0.f;
+                    wrep[((size_t)k * RM + r) * RW + p] = pk(v0, v1);
+                } else {
+                    const double v = p < D ? (double)src[(size_t)r * D + p] : 0.0;
+                    wrep[((size_t)k * RM + r) * RW + p] = (uint64_t)__double_as_longlong(v);
+                }
+            }
+        }
+    }
     unsigned long long c_cnt[KM];
     KY c_cand[KM];
 #pragma unroll
@@ -664,43 +744,42 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
 #pragma unroll
                 for (int p = 0; p < DH; ++p) px[p] = pk(x[2 * p], 2 * p + 1 < DM ? x[2 * p + 1] : 0.f);
             }
-            // distances to the representatives of the clusters that need them
-            unsigned long long far4 = 0ull, far1 = 0ull;
+            // distances to the representatives of the clusters that need them:
+            // far4[k] = some representative of k proved farther than 4 alpha
+            // (Lemma 2), far1[k] = some proved farther than alpha (ball test);
+            // far4 implies far1, so a cluster's scan stops at its first far4,
+            // or at its first far1 when only the ball test needs it
+            bool far4[KM], far1[KM];
 #pragma unroll
             for (int k = 0; k < KM; ++k) {
+                far4[k] = far1[k] = false;
                 const bool need = k < K && ((fl & 1u) || (fl & (2u << k)));
                 if (!need) continue;
-#pragma unroll
-                for (int r = 0; r < RMX; ++r)
-                    if (r < nr[k]) {
-                        const T *c = rxb + ((size_t)k * RM + r) * D;
-                        if constexpr (F32) {
-                            uint64_t pc[DH];
-#pragma unroll
-                            for (int p = 0; p < DH; ++p)
-                                pc[p] = pk(2 * p < D ? c[2 * p] : 0.f, 2 * p + 1 < D ? c[2 * p + 1] : 0.f);
-                            const float d = pt_dist_f32<2 * DH>(px, pc);
-                            if (d > mg.t_four) far4 |= 1ull << (k * RMX + r);
-                            if (d > mg.t_alpha) far1 |= 1ull << (k * RMX + r);
-                        } else {
-                            double cc[DM];
-#pragma unroll
-                            for (int a = 0; a < DM; ++a) cc[a] = a < D ? c[a] : 0.0;
-                            const double d = pt_dist_f64<DM>(reinterpret_cast<const double *>(x), cc, D);
-                            if (d > four_alpha) far4 |= 1ull << (k * RMX + r);
-                            if (d > alpha) far1 |= 1ull << (k * RMX + r);
-                        }
+                const bool want4 = (fl & 1u) != 0u;
+                const uint64_t *rk = wrep + (size_t)k * RM * RW;
+                for (int r = 0; r < nr[k]; ++r) {
+                    bool f4, f1;
+                    if constexpr (F32) {
+                        const float d = pt_dist_f32<2 * DH>(px, rk + (size_t)r * RW);
+                        f4 = d > mg.t_four;
+                        f1 = d > mg.t_alpha;
+                    } else {
+                        const double d = pt_dist_f64<DM>(reinterpret_cast<const double *>(x),
+                                                         reinterpret_cast<const double *>(rk + (size_t)r * RW), D);
+                        f4 = d > four_alpha;
+                        f1 = d > alpha;
                     }
+                    far1[k] = far1[k] || f1;
+                    if (f4) { far4[k] = true; break; }
+                    if (far1[k] && !want4) break;
+                }
             }
             // sample-based assignment of an unassigned sample (Algorithm 3, Lemma 2)
             if (fl & 1u) {
                 int left = 0, k1 = -1;
 #pragma unroll
                 for (int k = 0; k < KM; ++k)
-                    if (k < K) {
-                        const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
-                        if ((far4 & mk) == 0ull) { ++left; k1 = k; }
-                    }
+                    if (k < K && !far4[k]) { ++left; k1 = k; }
                 if (left == 0) infeasible = true;
                 if (left == 1)
                     for (int a = 0; a < D; ++a) {
@@ -713,8 +792,7 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
 #pragma unroll
             for (int k = 0; k < KM; ++k)
                 if (k < K && (fl & (2u << k))) {
-                    const unsigned long long mk = ((1ull << RMX) - 1ull) << (k * RMX);
-                    if (far1 & mk) continue;
+                    if (far1[k]) continue;
                     ++c_cnt[k];
                     for (int a = 0; a < D; ++a) {
                         const OT v = to_ord(x[a]);
@@ -762,8 +840,8 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
     if (__any_sync(0xffffffffu, infeasible) && lane == 0) atomicOr(&flags[b], 1u);
 }
 
-template <typename T, int KM, int DM, int RMX>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, int KM, int DM>
+__global__ void __launch_bounds__(kThreads, 3)
 visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, int K, int D, int RM,
                const T *__restrict__ lo_in, const T *__restrict__ hi_in, const T *__restrict__ blo,
                const T *__restrict__ bhi, const T *__restrict__ repx, const int *__restrict__ nreps,
@@ -781,6 +859,7 @@ visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, 
     auto *slots = reinterpret_cast<PBSlot<T, KM, DM> *>(lists + NWV * kSub);   // [warps]
     const int warp = threadIdx.x >> 5;
     uint32_t *list = lists + warp * kSub;
+    uint64_t *wrep = reinterpret_cast<uint64_t *>(slots + NWV) + (size_t)warp * KM * RM * rep_words<T, DM>();
     for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
         const int tn = (int)((n - base) < (int64_t)tile ? (n - base) : (int64_t)tile);
         __syncthreads();
@@ -790,14 +869,14 @@ visit_b_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, int B, 
         }
         __syncthreads();
         for (int b = warp; b < B; b += NWV)
-            pass_b_node<T, KM, DM, RMX>(tx, tile, tn, 0, 32, nullptr, ids, base, list, slots + warp, b, K, D, RM,
+            pass_b_node<T, KM, DM>(tx, tile, tn, 0, 32, nullptr, ids, base, list, slots + warp, wrep, b, K, D, RM,
                                         lo_in, hi_in, blo, bhi, repx, nreps, allhave, alpha, mg, seed_id, cnt, smax,
                                         smin, jmax, jmin, cand, flags);
     }
 }
 
 // List mode of pass B (see visit_a_list_kernel).
-template <typename T, int KM, int DM, int RMX>
+template <typename T, int KM, int DM>
 __global__ void __launch_bounds__(kThreads, 3)
 visit_b_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile, int K,
                     int D, int RM, const T *__restrict__ lo_in, const T *__restrict__ hi_in, const T *__restrict__ blo,
@@ -817,6 +896,8 @@ visit_b_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile, 
     uint32_t *tids = reinterpret_cast<uint32_t *>(slots + NWV);                 // [tile]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *list = lists + warp * kSub;
+    // [warps][KM][RM][words] after the ids (tile is a multiple of 32)
+    uint64_t *wrep = reinterpret_cast<uint64_t *>(tids + tile) + (size_t)warp * KM * RM * rep_words<T, DM>();
     for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
         int b;
         int64_t st;
@@ -835,9 +916,9 @@ visit_b_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile, 
         const int teams = (n1 - n0) < NWV ? (n1 - n0) : NWV, wpt = NWV / teams, team = warp / wpt;
         if (team < teams)
             for (int nd = n0 + team; nd < n1; nd += teams)
-                pass_b_node<T, KM, DM, RMX>(tx, tile, tn, (warp % wpt) * 32, wpt * 32, tids, nullptr, 0, list,
-                                            slots + warp, nd, K, D, RM, lo_in, hi_in, blo, bhi, repx, nreps, allhave,
-                                            alpha, mg, seed_id, cnt, smax, smin, jmax, jmin, cand, flags);
+                pass_b_node<T, KM, DM>(tx, tile, tn, (warp % wpt) * 32, wpt * 32, tids, nullptr, 0, list,
+                                       slots + warp, wrep, nd, K, D, RM, lo_in, hi_in, blo, bhi, repx, nreps, allhave,
+                                       alpha, mg, seed_id, cnt, smax, smin, jmax, jmin, cand, flags);
         (void)lane;
     }
 }
@@ -1043,15 +1124,24 @@ int reps_cap(int D, int cap) { return std::min(cap, std::min(kMaxReps, 2 * D + 1
 // Attribute-pair directions of the representatives: 2 min(D(D-1)/2, 16).
 int pair_dirs(int D) { return 2 * std::min(D * (D - 1) / 2, kMaxPairs); }
 
-template <typename T, int KM, int DM, int RMX>
+// Representatives per cluster: min(cap, 2D + 1, 50) along the attributes,
+// or, with `dirs` (float data), up to min(cap, 50) with the attribute-pair
+// directions after the attributes.
+int reps_slots(int D, int cap, int ndir)
+{
+    return std::max(1, ndir > 0 ? std::min(std::min(cap, kMaxReps), 1 + 2 * D + 2 * ndir) : reps_cap(D, cap));
+}
+
+template <typename T, int KM, int DM>
 kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi_, int B, double alpha,
-                       const int64_t *seeds, int cap, void *lo_out_, void *hi_out_, int64_t *counts, int64_t *cand_out,
-                       double *lb, double *lb_raw, int64_t *lbarg, int8_t *status, VisitScratch *vs,
+                       const int64_t *seeds, int cap, bool dirs, void *lo_out_, void *hi_out_, int64_t *counts,
+                       int64_t *cand_out, double *lb, double *lb_raw, int64_t *lbarg, int8_t *status, VisitScratch *vs,
                        const ListBatch *L = nullptr)
 {
     using KY = typename Key<T>::K;
     const int K_ = c->K, D = c->D;
-    const int RM = RMX;
+    const int ndir = (dirs && sizeof(T) == 4) ? pair_dirs(D) : 0;
+    const int RM = reps_slots(D, cap, ndir);
     const T *lo = static_cast<const T *>(lo_);
     const T *hi = static_cast<const T *>(hi_);
     const size_t KD = (size_t)B * K_ * D, BK = (size_t)B * K_;
@@ -1068,10 +1158,13 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     const size_t o_have = take(B * 4), o_cnt = take(BK * 8), o_smax = take(KD * sizeof(OrdT<T>));
     const size_t o_smin = take(KD * sizeof(OrdT<T>)), o_jmax = take(KD * sizeof(OrdT<T>));
     const size_t o_jmin = take(KD * sizeof(OrdT<T>)), o_cand = take(BK * sizeof(KY));
+    const size_t o_dmax = take(BK * ndir * 8), o_dmin = take(BK * ndir * 8);
     KC_TRY(ensure(c, vs->buf, off));
     char *w = static_cast<char *>(vs->buf.p);
     KY *lbkey = reinterpret_cast<KY *>(w + o_lbkey), *amax = reinterpret_cast<KY *>(w + o_amax);
     KY *amin = reinterpret_cast<KY *>(w + o_amin), *cand = reinterpret_cast<KY *>(w + o_cand);
+    unsigned long long *dmax = reinterpret_cast<unsigned long long *>(w + o_dmax);
+    unsigned long long *dmin = reinterpret_cast<unsigned long long *>(w + o_dmin);
     unsigned *flags = reinterpret_cast<unsigned *>(w + o_flags);
     T *blo = reinterpret_cast<T *>(w + o_blo), *bhi = reinterpret_cast<T *>(w + o_bhi);
     int64_t *reps = reinterpret_cast<int64_t *>(w + o_reps);
@@ -1091,20 +1184,21 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     const double r_up = nextafter(std::sqrt(alpha), __builtin_huge_val());
     // pass A
     const int tileA = (int)std::max<int64_t>(256, std::min<int64_t>(2048, (64 * 1024) / (D * 8)) / 32 * 32);
-    const size_t smemA = (size_t)D * tileA * 8;
+    const size_t dkA = (size_t)NWV * K_ * ndir * 2 * 8;   // per-warp direction keys
+    const size_t smemA = (size_t)D * tileA * 8 + dkA;
     int gA = 1;
     const int64_t tilesA = (v.n + tileA - 1) / tileA;
     auto kA = visit_a_kernel<T, KM, DM>;
     if (L) {
         // list mode: one node per work item, tile = list_tile() gathered ids
         const int lt = list_tile();
-        const size_t smem = (size_t)D * lt * 8 + (size_t)lt * 4;
+        const size_t smem = (size_t)D * lt * 8 + (size_t)lt * 4 + dkA;
         auto kAL = visit_a_list_kernel<T, KM, DM>;
         int g = 1;
         KC_TRY(grid_of(c, kAL, smem, std::max<int64_t>(1, L->W), &g));
         if (L->W > 0) {
             kAL<<<g, kThreads, smem, c->stream>>>(static_cast<const T *>(c->X), c->ldx, *L, lt, lo, hi, K_, D, alpha,
-                                                  mg, lbkey, amax, amin, flags);
+                                                  mg, lbkey, amax, amin, flags, ndir, dmax, dmin);
             KC_TRY(after_launch(c, "tighten pass A (lists)"));
         }
     } else {
@@ -1112,7 +1206,7 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
         if (sizeof(T) == 8) gA = 1;   // single-writer key merge (see Key<double>)
         if (v.n > 0) {
             kA<<<gA, kThreads, smemA, c->stream>>>(static_cast<const T *>(v.X), v.ld, v.n, tileA, lo, hi, B, K_, D,
-                                                  alpha, mg, lbkey, amax, amin, flags);
+                                                  alpha, mg, lbkey, amax, amin, flags, ndir, dmax, dmin);
             KC_TRY(after_launch(c, "tighten pass A"));
         }
     }
@@ -1124,10 +1218,11 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     fa.defl = deflate_factor(c->dt, D);
     fa.slack = underflow_slack(c->dt, D);
     fa.seed_defl = sizeof(T) == 4 ? 1.0 - gamma_n(f64_roundings(D), kU64) : 1.0;
-    fa.cap = std::min(reps_cap(D, cap), RM);
+    fa.cap = RM;
     fa.RM = RM;
-    fa.ndir = 0;
-    fa.dmax = fa.dmin = nullptr;
+    fa.ndir = ndir;
+    fa.dmax = dmax;
+    fa.dmin = dmin;
     finalize_a_kernel<T><<<(B + 127) / 128, 128, 0, c->stream>>>(
         B, K_, D, lo, hi, lbkey, amax, amin, flags, static_cast<const T *>(c->X), c->ldx, fa, blo, bhi, reps, nreps,
         repx, have, lb, lb_raw, lbarg);
@@ -1136,13 +1231,14 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     const int tileB = (int)std::max<int64_t>(256, std::min<int64_t>(2048, (32 * 1024) / (D * (int64_t)sizeof(T))) / 32 * 32);
     static_assert(kThreads / 32 * kSub * 4 <= 16 * 1024, "pass B lists");
     const size_t slotB = (size_t)NWV * sizeof(PBSlot<T, KM, DM>);
-    const size_t smemB = (size_t)D * tileB * sizeof(T) + (size_t)NWV * kSub * 4 + slotB;
+    const size_t repB = (size_t)NWV * KM * RM * rep_words<T, DM>() * 8;   // per-warp representatives
+    const size_t smemB = (size_t)D * tileB * sizeof(T) + (size_t)NWV * kSub * 4 + slotB + repB;
     int gB = 1;
-    auto kB = visit_b_kernel<T, KM, DM, RMX>;
+    auto kB = visit_b_kernel<T, KM, DM>;
     if (L) {
         const int lt = list_tile();
-        const size_t smem = (size_t)D * lt * sizeof(T) + (size_t)NWV * kSub * 4 + slotB + (size_t)lt * 4;
-        auto kBL = visit_b_list_kernel<T, KM, DM, RMX>;
+        const size_t smem = (size_t)D * lt * sizeof(T) + (size_t)NWV * kSub * 4 + slotB + (size_t)lt * 4 + repB;
+        auto kBL = visit_b_list_kernel<T, KM, DM>;
         int g = 1;
         KC_TRY(grid_of(c, kBL, smem, std::max<int64_t>(1, L->W), &g));
         if (L->W > 0) {
@@ -1186,7 +1282,7 @@ kc_status tighten_wide(kc_ctx *c, const View &v, const void *lo_, const void *hi
     using KY = unsigned long long;
     const int K_ = c->K, D = c->D;
     const int ndir = dirs ? pair_dirs(D) : 0;
-    const int RM = std::max(1, dirs ? std::min(std::min(cap, kMaxReps), 1 + 2 * D + 2 * ndir) : reps_cap(D, cap));
+    const int RM = reps_slots(D, cap, ndir);
     const T *lo = static_cast<const T *>(lo_);
     const T *hi = static_cast<const T *>(hi_);
     const size_t KD = (size_t)B * K_ * D, BK = (size_t)B * K_;
@@ -1255,6 +1351,39 @@ kc_status tighten_wide(kc_ctx *c, const View &v, const void *lo_, const void *hi
     return KC_OK;
 }
 
+// Shape dispatch of the tightening: the register kernels for the shapes
+// listed here, the shared-memory kernels (kc_wide.cu) for the other float
+// shapes.  Representatives: at most ball_cap (<= 0: 50); for float data a
+// cap above 2D + 1 reaches the pair directions, double data stop after the
+// attribute extremes.
+kc_status launch_tighten_any(kc_ctx *c, const View &v, const ListBatch *L, const void *lo, const void *hi, int B,
+                             double alpha, const int64_t *seeds_dev, int ball_cap, void *lo_out, void *hi_out,
+                             int64_t *counts, int64_t *cand, double *lb, double *lb_raw, int64_t *lbarg, int8_t *status,
+                             VisitScratch *vs)
+{
+    if (B <= 0) return KC_OK;
+    const int cap = ball_cap > 0 ? ball_cap : 50;
+    const int K = c->K, D = c->D;
+    const bool dirs = c->dt == KC_F32 && cap > 2 * D + 1 && D >= 2;
+#define KC_TIGHTEN(T_, KM_, DM_)                                                                                      \
+    return tighten_impl<T_, KM_, DM_>(c, v, lo, hi, B, alpha, seeds_dev, cap, dirs, lo_out, hi_out, counts, cand, lb, \
+                                      lb_raw, lbarg, status, vs, L)
+    if (c->dt == KC_F32) {
+        if (K == 3 && D == 3) KC_TIGHTEN(float, 3, 3);
+        if (K == 3 && D == 4) KC_TIGHTEN(float, 3, 4);
+        if (K <= 4 && D <= 2) KC_TIGHTEN(float, 4, 2);
+        if (K <= 4 && D <= 4) KC_TIGHTEN(float, 4, 4);
+        if (K <= 2 && D <= 8) KC_TIGHTEN(float, 2, 8);
+        return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, dirs, lo_out, hi_out, counts, cand, lb, lb_raw,
+                            lbarg, status, vs, L);
+    }
+    if (L) return set_err(c, KC_EINTERNAL, "list-mode tightening is for float data");
+    if (K <= 4 && D <= 2) KC_TIGHTEN(double, 4, 2);
+    if (K <= 4 && D <= 4) KC_TIGHTEN(double, 4, 4);
+#undef KC_TIGHTEN
+    return set_err(c, KC_EINVAL, "kc_tighten: double data supported for K <= 4, D <= 4 (K=%d, D=%d)", K, D);
+}
+
 }  // namespace
 
 kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int B, double alpha,
@@ -1262,43 +1391,8 @@ kc_status launch_tighten_view(kc_ctx *c, const View &v, const void *lo, const vo
                               int64_t *cand, double *lb, double *lb_raw, int64_t *lbarg, int8_t *status,
                               VisitScratch *vs)
 {
-    if (B <= 0) return KC_OK;
-    const int cap = ball_cap > 0 ? ball_cap : 50;
-    // ball_cap above 2D + 1: representatives along pair directions too (wide kernels)
-    const bool dirs = ball_cap > 2 * c->D + 1 && c->D >= 2;
-    if (c->dt == KC_F32) {
-        if (dirs)
-            return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, true, lo_out, hi_out, counts, cand, lb, lb_raw,
-                                lbarg, status, vs);
-        if (c->K == 3 && c->D == 3)
-            return tighten_impl<float, 3, 3, 7>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
-                                                lb, lb_raw, lbarg, status, vs);
-        if (c->K == 3 && c->D == 4)
-            return tighten_impl<float, 3, 4, 9>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
-                                                lb, lb_raw, lbarg, status, vs);
-        if (c->K <= 4 && c->D <= 2)
-            return tighten_impl<float, 4, 2, 5>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
-                                                lb, lb_raw, lbarg, status, vs);
-        if (c->K <= 4 && c->D <= 4)
-            return tighten_impl<float, 4, 4, 9>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
-                                                lb, lb_raw, lbarg, status, vs);
-        if (c->K <= 2 && c->D <= 8)
-            return tighten_impl<float, 2, 8, 17>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand,
-                                                 lb, lb_raw, lbarg, status, vs);
-        return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, false, lo_out, hi_out, counts, cand, lb, lb_raw,
-                            lbarg, status, vs);
-    }
-    if (dirs)
-        return set_err(c, KC_EINVAL,
-                       "kc_tighten: ball_cap above 2D + 1 (pair-direction representatives) needs float data "
-                       "(ball_cap=%d, D=%d)", ball_cap, c->D);
-    if (c->K <= 4 && c->D <= 2)
-        return tighten_impl<double, 4, 2, 5>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
-                                             lb_raw, lbarg, status, vs);
-    if (c->K <= 4 && c->D <= 4)
-        return tighten_impl<double, 4, 4, 9>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
-                                             lb_raw, lbarg, status, vs);
-    return set_err(c, KC_EINVAL, "kc_tighten: double data supported for K <= 4, D <= 4 (K=%d, D=%d)", c->K, c->D);
+    return launch_tighten_any(c, v, nullptr, lo, hi, B, alpha, seeds_dev, ball_cap, lo_out, hi_out, counts, cand, lb,
+                              lb_raw, lbarg, status, vs);
 }
 
 kc_status launch_tighten_list(kc_ctx *c, const ListBatch &L, const void *lo, const void *hi, int B, double alpha,
@@ -1306,30 +1400,9 @@ kc_status launch_tighten_list(kc_ctx *c, const ListBatch &L, const void *lo, con
                               int64_t *cand, double *lb, double *lb_raw, int64_t *lbarg, int8_t *status,
                               VisitScratch *vs)
 {
-    if (B <= 0) return KC_OK;
     if (c->dt != KC_F32) return set_err(c, KC_EINTERNAL, "list-mode tightening is for float data");
-    const int cap = ball_cap > 0 ? ball_cap : 50;
-    const View v = full_view(c);
-    if (ball_cap > 2 * c->D + 1 && c->D >= 2)
-        return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, true, lo_out, hi_out, counts, cand, lb, lb_raw,
-                            lbarg, status, vs, &L);
-    if (c->K == 3 && c->D == 3)
-        return tighten_impl<float, 3, 3, 7>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
-                                            lb_raw, lbarg, status, vs, &L);
-    if (c->K == 3 && c->D == 4)
-        return tighten_impl<float, 3, 4, 9>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
-                                            lb_raw, lbarg, status, vs, &L);
-    if (c->K <= 4 && c->D <= 2)
-        return tighten_impl<float, 4, 2, 5>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
-                                            lb_raw, lbarg, status, vs, &L);
-    if (c->K <= 4 && c->D <= 4)
-        return tighten_impl<float, 4, 4, 9>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
-                                            lb_raw, lbarg, status, vs, &L);
-    if (c->K <= 2 && c->D <= 8)
-        return tighten_impl<float, 2, 8, 17>(c, v, lo, hi, B, alpha, seeds_dev, cap, lo_out, hi_out, counts, cand, lb,
-                                             lb_raw, lbarg, status, vs, &L);
-    return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, false, lo_out, hi_out, counts, cand, lb, lb_raw,
-                        lbarg, status, vs, &L);
+    return launch_tighten_any(c, full_view(c), &L, lo, hi, B, alpha, seeds_dev, ball_cap, lo_out, hi_out, counts,
+                              cand, lb, lb_raw, lbarg, status, vs);
 }
 
 kc_status launch_sample_reduction_view(kc_ctx *c, const View &v, const void *lo, const void *hi, int M,

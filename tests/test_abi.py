@@ -49,7 +49,7 @@ def test_argument_validation_without_gpu(kcpkg):
 
 def test_solve_defaults(kcpkg):
     o = kcpkg.kc_solve_defaults()
-    assert o.tol == 1e-12 and o.ball_cap == 0 and o.i_sr == 1 and o.use_bt == 1
+    assert o.tol == 1e-12 and o.ball_cap == 50 and o.i_sr == 1 and o.use_bt == 1
 
 
 def test_null_context_is_rejected(kcpkg):

@@ -50,7 +50,7 @@ def _nodes_around(X, centers, B, seed, scale=(0.05, 0.6)):
     return np.ascontiguousarray(lo.astype(X.dtype)), np.ascontiguousarray(hi.astype(X.dtype))
 
 
-def _compare_tighten(X, lo, hi, alpha, seeds, g, exact_cand=True):
+def _compare_tighten(X, lo, hi, alpha, seeds, g, exact_cand=True, ball_cap=0):
     B, k, d = lo.shape
     st = g["status"].cpu().numpy() if hasattr(g["status"], "cpu") else g["status"]
     glo = g["lo"].cpu().numpy() if hasattr(g["lo"], "cpu") else g["lo"]
@@ -61,7 +61,7 @@ def _compare_tighten(X, lo, hi, alpha, seeds, g, exact_cand=True):
     is_f32 = X.dtype == np.float32
     n_feasible = 0
     for b in range(B):
-        r = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=is_f32)
+        r = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=is_f32, ball_cap=ball_cap)
         assert glb[b] <= r["beta"] and glb[b] >= r["beta"] * (1 - 1e-6), (b, glb[b], r["beta"])
         assert st[b] == r["status"], (b, st[b], r["status"])
         if r["status"] == 1:
@@ -86,7 +86,7 @@ def _compare_tighten(X, lo, hi, alpha, seeds, g, exact_cand=True):
     return n_feasible
 
 
-def _ambiguous(X, lo, hi, alpha, seeds, band=3e-6):
+def _ambiguous(X, lo, hi, alpha, seeds, band=3e-6, ball_cap=0):
     """True when some decision quantity of the tightening lies within `band`
     (relative) of its threshold, where float and double decisions can differ."""
     Xd = X.astype(np.float64)
@@ -94,7 +94,7 @@ def _ambiguous(X, lo, hi, alpha, seeds, band=3e-6):
         bm = oracle.beta_matrix(Xd, lo[b], hi[b])
         if np.any(np.abs(bm - alpha) <= band * alpha):
             return True
-        r = oracle.tighten(Xd, lo[b], hi[b], alpha, seeds=seeds, is_f32=True)
+        r = oracle.tighten(Xd, lo[b], hi[b], alpha, seeds=seeds, is_f32=True, ball_cap=ball_cap)
         for reps in r["reps"]:
             for j in reps:
                 dd = ((Xd - Xd[j]) ** 2).sum(1)
@@ -118,22 +118,26 @@ def test_tighten_f64_exact(d, k):
             assert nf >= 1
 
 
+@pytest.mark.parametrize("axes", [False, True])
 @pytest.mark.parametrize("d,k", [(2, 3), (4, 3), (2, 4), (3, 3)])
-def test_tighten_f32_exact_on_unambiguous_inputs(d, k):
+def test_tighten_f32_exact_on_unambiguous_inputs(d, k, axes):
+    """axes: ball_cap = 2D + 1 (the seed and the attribute extremes), else the
+    default of 50 with the pair directions."""
+    cap = 2 * d + 1 if axes else 0
     X = _blobs(4_003, d, k, seed=100 + d * 7 + k, dtype=np.float32)
     c, fobj = oracle.fft(X, k, 3)
     kc = KCenter(_t(X), k)
     lo, hi = _nodes_around(X, c, 12, seed=d)
     alpha = fobj * 0.71
     for _ in range(20):
-        if not _ambiguous(X, lo, hi, alpha, None):
+        if not _ambiguous(X, lo, hi, alpha, None, ball_cap=cap):
             break
         alpha *= 1.0000373
     else:
         pytest.skip("could not find an unambiguous alpha")
-    g = kc.tighten(_t(lo), _t(hi), alpha)
+    g = kc.tighten(_t(lo), _t(hi), alpha, ball_cap=cap)
     torch.cuda.synchronize()
-    _compare_tighten(X, lo, hi, alpha, None, g, exact_cand=False)
+    _compare_tighten(X, lo, hi, alpha, None, g, exact_cand=False, ball_cap=cap)
 
 
 def _step_a_clear(X64, lo, hi, alpha, band=3e-6):
@@ -247,12 +251,13 @@ def test_tighten_f32_exact_at_one_million_samples():
     hi = (np.ceil(hi.astype(np.float64) * 4) / 4).astype(np.float32)
     kc = KCenter(_t(X), w.k)
     n_feasible = 0
-    for f in (0.83, 0.95):
-        alpha = (np.round(fobj * f * 16) + 0.5) / 16
-        g = kc.tighten(_t(lo), _t(hi), alpha)
-        torch.cuda.synchronize()
-        n_feasible += _compare_tighten(X, lo, hi, alpha, None, g, exact_cand=False)
-    assert n_feasible >= 8
+    for cap in (0, 2 * X.shape[1] + 1):   # default (pair directions), attribute extremes
+        for f in (0.83, 0.95):
+            alpha = (np.round(fobj * f * 16) + 0.5) / 16
+            g = kc.tighten(_t(lo), _t(hi), alpha, ball_cap=cap)
+            torch.cuda.synchronize()
+            n_feasible += _compare_tighten(X, lo, hi, alpha, None, g, exact_cand=False, ball_cap=cap)
+    assert n_feasible >= 16
 
 
 def test_tighten_root_and_ragged_sizes():

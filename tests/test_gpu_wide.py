@@ -131,9 +131,10 @@ def test_wide_solve_matches_oracle(n, d, k, seed):
     (8_000, 2, 3, 9, False), (8_000, 2, 4, 50, True), (6_000, 3, 3, 12, True), (6_000, 3, 3, 50, False),
     (6_000, 4, 3, 25, False), (6_000, 4, 4, 50, True), (5_000, 5, 3, 50, False)])
 def test_pair_direction_representatives_on_grid(n, d, k, cap, seeded):
-    """ball_cap above 2D + 1 on shapes that otherwise run the register
-    kernels (K <= 4, D <= 4): the pair-direction representatives change the
-    tightened boxes and counts, and the kernels match the oracle exactly."""
+    """ball_cap above 2D + 1 on the shapes of the register kernels (K <= 4,
+    D <= 4, and D = 5 on the shared-memory kernels): the pair-direction
+    representatives change the tightened boxes and counts, and the kernels
+    match the oracle exactly."""
     X, c, fobj, lo, hi = _grid_case(n, d, k, seed=3 * d + k, B=10, scale=(0.05, 0.5))
     kc = KCenter(_t(X), k)
     seeds = np.array(c, np.int64) if seeded else None
@@ -167,15 +168,28 @@ def test_solve_with_pair_direction_representatives(n, d, k, seed):
     assert oracle.objective(X, g["centers"])[0] == g["objective"]
 
 
-def test_pair_directions_refused_for_double_data():
-    X = _blobs(500, 2, 3, 1, dtype=np.float64)
-    kc = KCenter(_t(X), 3)
+def test_double_data_keep_the_attribute_extremes():
+    """Double data: any ball_cap above 2D + 1 gives the attribute extremes,
+    as in the oracle."""
+    X = np.round(_blobs(600, 2, 3, 1, dtype=np.float64) * 4) / 4
+    c, fobj = oracle.fft(X, 3, 0)
     lo = np.broadcast_to(X.min(0), (1, 3, 2)).copy()
     hi = np.broadcast_to(X.max(0), (1, 3, 2)).copy()
-    g = kc.tighten(_t(lo), _t(hi), 10.0, ball_cap=5)    # 2D + 1: the attribute extremes
-    torch.cuda.synchronize()
-    assert g["status"].cpu().numpy()[0] in (0, 1, 2)
-    with pytest.raises(RuntimeError, match="float data"):
-        kc.tighten(_t(lo), _t(hi), 10.0, ball_cap=6)
-    with pytest.raises(RuntimeError, match="float data"):
-        kc.solve(tol=1e-12, ball_cap=50)
+    for i, ctr in enumerate(c):
+        lo[0, i] = np.maximum(lo[0, i], X[ctr] - 3)
+        hi[0, i] = np.minimum(hi[0, i], X[ctr] + 3)
+    kc = KCenter(_t(X), 3)
+    alpha = (np.round(fobj * 16) + 0.5) / 16
+    outs = []
+    for cap in (5, 50, 0):
+        g = kc.tighten(_t(lo), _t(hi), alpha, ball_cap=cap)
+        torch.cuda.synchronize()
+        outs.append({k: v.cpu().numpy() for k, v in g.items()})
+        r = oracle.tighten(X, lo[0], hi[0], alpha, ball_cap=cap)
+        assert outs[-1]["status"][0] == r["status"]
+        if r["status"] != 1:
+            assert np.array_equal(outs[-1]["lo"][0], r["lo"]) and np.array_equal(outs[-1]["hi"][0], r["hi"])
+            assert np.array_equal(outs[-1]["count"][0], r["count"])
+    for o in outs[1:]:
+        for k in ("status", "lo", "hi", "count"):
+            assert np.array_equal(o[k], outs[0][k])

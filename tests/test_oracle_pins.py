@@ -512,22 +512,27 @@ def test_representatives_along_pair_directions():
     """Reading of the 50-ball budget (Section 4.1.2): the seed, the assigned
     samples at the min and max of each attribute, then the min and max of
     x_a + x_b and of x_a - x_b over the first attribute pairs; duplicates
-    skipped, at most ball_cap.  Hand-derived, one cluster, every sample
-    assigned: s0 (0,0), s1 (4,0), s2 (0,4), s3 (3,3), s4 (1,-1), s5 (3.5,-0.875).
+    skipped, at most ball_cap (default 50); the pair directions for float
+    data only.  Hand-derived, one cluster, every sample assigned: s0 (0,0),
+    s1 (4,0), s2 (0,4), s3 (3,3), s4 (1,-1), s5 (3.5,-0.875).
       attributes: min x0 s0 (tie with s2: smaller index), max x0 s1,
                   min x1 s4, max x1 s2            -> [0, 1, 4, 2]
       x0 + x1: 0, 4, 4, 6, 0, 2.625: min s0 (dup), max s3 (new)
       x0 - x1: 0, 4, -4, 0, 2, 4.375: min s2 (dup), max s5 (new)  -> [0, 1, 4, 2, 3, 5]
-    The same in float (every value exact)."""
+    Every value is exact in float."""
     X = np.array([[0.0, 0.0], [4.0, 0.0], [0.0, 4.0], [3.0, 3.0], [1.0, -1.0], [3.5, -0.875]])
     lo = np.array([[-10.0, -10.0]])
     hi = np.array([[10.0, 10.0]])
-    for f32 in (False, True):
-        assert oracle.tighten(X, lo, hi, 1e6, ball_cap=50, is_f32=f32)["reps"] == [[0, 1, 4, 2, 3, 5]]
-        assert oracle.tighten(X, lo, hi, 1e6, is_f32=f32)["reps"] == [[0, 1, 4, 2]]   # default: attributes only
-        assert oracle.tighten(X, lo, hi, 1e6, ball_cap=5, is_f32=f32)["reps"] == [[0, 1, 4, 2, 3]]
+    assert oracle.tighten(X, lo, hi, 1e6, ball_cap=50, is_f32=True)["reps"] == [[0, 1, 4, 2, 3, 5]]
+    assert oracle.tighten(X, lo, hi, 1e6, is_f32=True)["reps"] == [[0, 1, 4, 2, 3, 5]]   # default 50
+    assert oracle.tighten(X, lo, hi, 1e6, ball_cap=5, is_f32=True)["reps"] == [[0, 1, 4, 2, 3]]
+    assert oracle.tighten(X, lo, hi, 1e6, ball_cap=4, is_f32=True)["reps"] == [[0, 1, 4, 2]]
+    # double data: the attribute extremes only, whatever the cap
+    assert oracle.tighten(X, lo, hi, 1e6, ball_cap=50)["reps"] == [[0, 1, 4, 2]]
+    assert oracle.tighten(X, lo, hi, 1e6)["reps"] == [[0, 1, 4, 2]]
     # with a seed it comes first and is not repeated
-    assert oracle.tighten(X, lo, hi, 1e6, seeds=np.array([3]), ball_cap=50)["reps"] == [[3, 0, 1, 4, 2, 5]]
+    assert oracle.tighten(X, lo, hi, 1e6, seeds=np.array([3]), is_f32=True)["reps"] == [[3, 0, 1, 4, 2, 5]]
+    assert oracle.tighten(X, lo, hi, 1e6, seeds=np.array([3]))["reps"] == [[3, 0, 1, 4, 2]]
 
 
 def test_pair_direction_values_in_the_data_precision():
@@ -535,11 +540,14 @@ def test_pair_direction_values_in_the_data_precision():
     Samples s0 (2^24, 0), s1 (2^24, 1), s2 (2^24 + 2, -5), s3 (0, 3):
       attributes: min x0 s3, max x0 s2, min x1 s2 (dup), max x1 s3 (dup) -> [3, 2]
       x0 + x1: 2^24, 2^24 + 1, 2^24 - 3, 3 -- in float 2^24 + 1 rounds to 2^24
-        (ties to even): the max is s1 in double, s0 in float (tie, smaller index);
-        the min is s3 (dup)
+        (ties to even): the max is s0 (tie with s1, smaller index), where
+        the exact sums would pick s1; the min is s3 (dup)
       x0 - x1: 2^24, 2^24 - 1, 2^24 + 7, -3: max s2 (dup), min s3 (dup)."""
     X = np.array([[16777216.0, 0.0], [16777216.0, 1.0], [16777218.0, -5.0], [0.0, 3.0]])
     lo = np.array([[-1e8, -1e8]])
     hi = np.array([[1e8, 1e8]])
-    assert oracle.tighten(X, lo, hi, 1e30, ball_cap=50)["reps"] == [[3, 2, 1]]
     assert oracle.tighten(X, lo, hi, 1e30, ball_cap=50, is_f32=True)["reps"] == [[3, 2, 0]]
+    # the same samples shifted off the rounding tie pick s1: the sum decides
+    X2 = X.copy()
+    X2[1, 1] = 2.0
+    assert oracle.tighten(X2, lo, hi, 1e30, ball_cap=50, is_f32=True)["reps"] == [[3, 2, 1]]
