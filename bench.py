@@ -53,6 +53,9 @@ def parse():
                    help="N of the batched-solve workload timed to a certified optimum (0: skip)")
     p.add_argument("--no-hbm-points", action="store_true")
     p.add_argument("--solve-time-limit", type=float, default=60.0)
+    p.add_argument("--solve-arena-mb", type=int, default=0,
+                   help="device memory (MiB) for the solve's per-node lists (0: automatic; profiling runs "
+                        "keep it small)")
     p.add_argument("--learned-n", type=int, default=100_000_000,
                    help="N of the learned-order workload solved with the scorer and with best bound (0: skip)")
     return p.parse_args()
@@ -463,7 +466,7 @@ def main():
         fft100 = fft_best_of(kcm, kc, Xs.shape[0], 100, 11 + rank)
         torch.cuda.synchronize()
         barrier()
-        r = kc.solve(tol=1e-12, time_limit_s=args.solve_time_limit)
+        r = kc.solve(tol=1e-12, time_limit_s=args.solve_time_limit, arena_mb=args.solve_arena_mb)
         torch.cuda.synchronize()
         secs = r["seconds"]
         secs = max_over_ranks(secs, ws)

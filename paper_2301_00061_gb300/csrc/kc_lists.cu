@@ -293,7 +293,10 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
     __shared__ uint64_t sbox[kMaxK * DMAX];
     __shared__ float sl[kMaxK * DMAX], sh[kMaxK * DMAX];
     __shared__ unsigned long long red[8];
-    const int Dp = (D + 1) & ~1;
+    __shared__ int snr[kMaxK];
+    // the node's representatives as packed coordinate pairs [K][RM][Dp / 2]
+    extern __shared__ uint64_t srep[];
+    const int Dp = (D + 1) & ~1, H = Dp / 2;
     const int lane = threadIdx.x & 31;
     for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
         int b;
@@ -309,9 +312,16 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
             sbox[i] = a < D ? pk(lo[o], -hi[o]) : pk(0.f, -0.f);
             if (a < D) { sl[k * D + a] = lo[o]; sh[k * D + a] = hi[o]; }
         }
+        const size_t rb = rmap ? (size_t)rmap[b] : (size_t)b;   // row of the node's representatives
+        for (int k = threadIdx.x; k < K; k += blockDim.x) snr[k] = nreps ? nreps[rb * K + k] : 0;
+        if (nreps)
+            for (int i = threadIdx.x; i < K * RM * H; i += blockDim.x) {
+                const int k = i / (RM * H), r = (i / H) % RM, p = i % H;
+                const float *c = repx + ((rb * K + k) * RM + r) * D;
+                if (r < nreps[rb * K + k]) srep[i] = pk(c[2 * p], 2 * p + 1 < D ? c[2 * p + 1] : 0.f);
+            }
         __syncthreads();
         const float bth = beta_dn[b];
-        const size_t rb = rmap ? (size_t)rmap[b] : (size_t)b;   // row of the node's representatives
         // the children's split: box ks, attribute as_, at (cm | cs)
         const int cv = ckeys ? cvar[b] : 0, ks = cv / D, as_ = cv % D;
         const float cm = ckeys ? csplit[2 * b] : 0.f, cs = ckeys ? csplit[2 * b + 1] : 0.f;
@@ -345,23 +355,31 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
                     as = fminf(as, s2.x + s2.y);
                 }
                 const bool lbred = __fadd_ru(__fmul_ru(as, infl), slack) < bth;
-                bool ubred = true;
+                // the upper-bound test only matters for lower-bound redundant samples
+                bool ubred = lbred;
+                uint64_t pxx[DMAX / 2];
+#pragma unroll
+                for (int p = 0; p < DMAX / 2; ++p) pxx[p] = pk(x[2 * p], x[2 * p + 1]);
                 for (int k = 0; k < K && ubred; ++k) {
                     bool inb = true;
                     for (int a = 0; a < D; ++a)
                         if (x[a] < sl[k * D + a] || x[a] > sh[k * D + a]) inb = false;
                     if (!inb) continue;
                     bool excl = false;
-                    const int nr = nreps ? nreps[rb * K + k] : 0;
-                    for (int r = 0; r < nr && !excl; ++r) {
-                        const float *c = repx + ((rb * K + k) * RM + r) * D;
-                        float acc0 = 0.f, acc1 = 0.f;
-                        for (int a = 0; a < D; a += 2) {
-                            const float t0 = x[a] - c[a];
-                            acc0 = fmaf(t0, t0, acc0);
-                            if (a + 1 < D) { const float t1 = x[a + 1] - c[a + 1]; acc1 = fmaf(t1, t1, acc1); }
-                        }
-                        if (acc0 + acc1 > t_alpha) excl = true;
+                    const int nr = snr[k];
+                    const uint64_t *ck = srep + (size_t)k * RM * H;
+                    for (int r = 0; r < nr && !excl; ++r, ck += H) {
+                        // squared distance: even attributes in .x, odd in .y, each
+                        // a fused chain in attribute order (zero padding adds 0)
+                        uint64_t acc = 0;
+#pragma unroll
+                        for (int p = 0; p < DMAX / 2; ++p)
+                            if (p < H) {
+                                const uint64_t t = sub2(pxx[p], ck[p]);
+                                acc = fma2(t, t, acc);
+                            }
+                        const float2 s2 = upk(acc);
+                        if (s2.x + s2.y > t_alpha) excl = true;
                     }
                     if (!excl) ubred = false;
                 }
@@ -573,7 +591,10 @@ kc_status launch_seg_filter(kc_ctx *c, const ListBatch &L, const void *lo, const
     float t_alpha = (float)(((double)aup + (double)slack) / (double)defl * (1.0 + 1e-6));
     if ((double)t_alpha < ((double)aup + (double)slack) / (double)defl * (1.0 + 1e-6)) t_alpha = nextafterf(t_alpha, 3.4e38f);
     const int gr = grid_items(c, L.W);
-    seg_filter_f32<8><<<gr, 256, 0, c->stream>>>(static_cast<const float *>(c->X), c->ldx, L,
+    const size_t srep = nreps ? (size_t)c->K * RM * (((c->D + 1) & ~1) / 2) * 8 : 0;
+    if (srep > 48 * 1024)
+        KC_CUDA(c, cudaFuncSetAttribute(seg_filter_f32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)srep));
+    seg_filter_f32<8><<<gr, 256, srep, c->stream>>>(static_cast<const float *>(c->X), c->ldx, L,
                                                  static_cast<const float *>(lo), static_cast<const float *>(hi), c->K,
                                                  c->D, beta_dn_dev, infl, slack, t_alpha,
                                                  static_cast<const float *>(repx), nreps, RM, rmap, out_pool, out_off,

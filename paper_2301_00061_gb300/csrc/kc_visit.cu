@@ -187,16 +187,22 @@ __device__ __forceinline__ bool proved_lt(float dhat, float infl, float slack, f
 // (j = j0, j0 + step, ... < tn).  Keys name a sample by tids[j] when the tile
 // was gathered from a list of sample ids, else by its position base + j.
 
-// Pair directions (float data): dv.ndir > 0 also keeps, per cluster, the
-// arg-extreme keys of x_a + x_b and x_a - x_b (added in float) over the
-// assigned samples for the first ndir / 2 attribute pairs a < b in
-// lexicographic order, in the warp's shared-memory slot sdk [K][ndir][2]
-// (max, min), merged into dmax / dmin [B][K][ndir] at the end of the node.
-struct DirKeys {
+// Float data keep the node's arg-extreme keys in the warp's shared-memory
+// slot sk, updated with atomics that a plain read skips when they cannot
+// change the value, and merged into global memory at the end of the node:
+// per cluster and attribute (max, min) at sk [K][D][2], then, with ndir > 0,
+// per cluster and pair direction at sk [2KD + (k ndir + q) 2] -- the keys of
+// x_a + x_b and x_a - x_b (added in float) for the first ndir / 2 attribute
+// pairs a < b in lexicographic order, merged into dmax / dmin [B][K][ndir].
+// Double data keep the attribute keys in registers (no directions).
+struct WarpKeys {
     int ndir;
-    unsigned long long *sdk;
+    unsigned long long *sk;
     unsigned long long *__restrict__ dmax, *__restrict__ dmin;
 };
+
+// u64 words of a warp's key slot
+__host__ __device__ constexpr int warp_key_words(int K, int D, int ndir) { return 2 * K * D + 2 * K * ndir; }
 
 template <typename T, int KM, int DM>
 __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td, int tile, int tn, int j0, int step,
@@ -204,17 +210,15 @@ __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td
                                             const T *__restrict__ hi, int b, int K, int D, double alpha,
                                             const Margins &mg, typename Key<T>::K *__restrict__ lbkey,
                                             typename Key<T>::K *__restrict__ amax, typename Key<T>::K *__restrict__ amin,
-                                            unsigned *__restrict__ flags, const DirKeys &dk)
+                                            unsigned *__restrict__ flags, const WarpKeys &dk)
 {
     using KT = Key<T>;
     using KY = typename KT::K;
     constexpr bool F32 = sizeof(T) == 4;
     const int lane = threadIdx.x & 31;
     if constexpr (F32) {
-        if (dk.ndir > 0) {
-            for (int i = lane; i < K * dk.ndir * 2; i += 32) dk.sdk[i] = 0ull;
-            __syncwarp();
-        }
+        for (int i = lane; i < warp_key_words(K, D, dk.ndir); i += 32) dk.sk[i] = 0ull;
+        __syncwarp();
     }
     // node boxes into registers
     uint64_t bx[KM][DM];
@@ -233,11 +237,13 @@ __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td
             }
         }
     KY acc_lb = KT::none();
-    KY acc_max[KM][DM], acc_min[KM][DM];
+    KY acc_max[F32 ? 1 : KM][DM], acc_min[F32 ? 1 : KM][DM];   // double data only
+    if constexpr (!F32) {
 #pragma unroll
-    for (int k = 0; k < KM; ++k)
+        for (int k = 0; k < KM; ++k)
 #pragma unroll
-        for (int a = 0; a < DM; ++a) { acc_max[k][a] = KT::none(); acc_min[k][a] = KT::none(); }
+            for (int a = 0; a < DM; ++a) { acc_max[k][a] = KT::none(); acc_min[k][a] = KT::none(); }
+    }
     bool infeasible = false;
     for (int j = j0; j < tn; j += step) {
         const uint32_t pos = tids ? tids[j] : (uint32_t)(base + j);
@@ -273,19 +279,28 @@ __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td
         acc_lb = kmax<T>(acc_lb, KT::max_of(bmin, pos));
         if (left == 0) infeasible = true;
         if (left == 1) {
+            if constexpr (!F32) {
 #pragma unroll
-            for (int k = 0; k < KM; ++k)
-                if (k == k1) {
+                for (int k = 0; k < KM; ++k)
+                    if (k == k1) {
 #pragma unroll
-                    for (int a = 0; a < DM; ++a)
-                        if (a < D) {
-                            acc_max[k][a] = kmax<T>(acc_max[k][a], KT::max_of(x[a], pos));
-                            acc_min[k][a] = kmax<T>(acc_min[k][a], KT::min_of(x[a], pos));
-                        }
-                }
-            if constexpr (F32) {
+                        for (int a = 0; a < DM; ++a)
+                            if (a < D) {
+                                acc_max[k][a] = kmax<T>(acc_max[k][a], KT::max_of(x[a], pos));
+                                acc_min[k][a] = kmax<T>(acc_min[k][a], KT::min_of(x[a], pos));
+                            }
+                    }
+            } else {
+                unsigned long long *sa = dk.sk + (size_t)k1 * D * 2;
+#pragma unroll
+                for (int a = 0; a < DM; ++a)
+                    if (a < D) {
+                        const KY k0 = KT::max_of(x[a], pos), k1_ = KT::min_of(x[a], pos);
+                        if (k0 > sa[2 * a]) atomicMax(&sa[2 * a], k0);
+                        if (k1_ > sa[2 * a + 1]) atomicMax(&sa[2 * a + 1], k1_);
+                    }
                 if (dk.ndir > 0) {
-                    unsigned long long *s = dk.sdk + (size_t)k1 * dk.ndir * 2;
+                    unsigned long long *s = dk.sk + (size_t)2 * K * D + (size_t)k1 * dk.ndir * 2;
                     int q = 0;
 #pragma unroll
                     for (int a = 0; a < DM; ++a)
@@ -308,28 +323,34 @@ __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td
     // warp reduction, then one atomic per accumulator and warp
     acc_lb = warp_kmax<T>(acc_lb);
     if (lane == 0 && !KT::is_none(acc_lb)) KT::atomic_max(&lbkey[b], acc_lb, &flags[b]);
+    if constexpr (!F32) {
 #pragma unroll
-    for (int k = 0; k < KM; ++k)
+        for (int k = 0; k < KM; ++k)
 #pragma unroll
-        for (int a = 0; a < DM; ++a)
-            if (k < K && a < D) {
-                const KY m1 = warp_kmax<T>(acc_max[k][a]);
-                const KY m2 = warp_kmax<T>(acc_min[k][a]);
-                const size_t o = ((size_t)b * K + k) * D + a;
-                if (lane == 0 && !KT::is_none(m1)) KT::atomic_max(&amax[o], m1, &flags[b]);
-                if (lane == 0 && !KT::is_none(m2)) KT::atomic_max(&amin[o], m2, &flags[b]);
-            }
+            for (int a = 0; a < DM; ++a)
+                if (k < K && a < D) {
+                    const KY m1 = warp_kmax<T>(acc_max[k][a]);
+                    const KY m2 = warp_kmax<T>(acc_min[k][a]);
+                    const size_t o = ((size_t)b * K + k) * D + a;
+                    if (lane == 0 && !KT::is_none(m1)) KT::atomic_max(&amax[o], m1, &flags[b]);
+                    if (lane == 0 && !KT::is_none(m2)) KT::atomic_max(&amin[o], m2, &flags[b]);
+                }
+    }
     if (__any_sync(0xffffffffu, infeasible) && lane == 0) atomicOr(&flags[b], 1u);
     if constexpr (F32) {
-        if (dk.ndir > 0) {
-            __syncwarp();
-            for (int i = lane; i < K * dk.ndir; i += 32) {
-                const size_t o = (size_t)b * K * dk.ndir + i;
-                if (dk.sdk[2 * i]) atomicMax(&dk.dmax[o], dk.sdk[2 * i]);
-                if (dk.sdk[2 * i + 1]) atomicMax(&dk.dmin[o], dk.sdk[2 * i + 1]);
-            }
-            __syncwarp();   // the slot is rewritten by the warp's next node
+        __syncwarp();
+        for (int i = lane; i < K * D; i += 32) {
+            const size_t o = (size_t)b * K * D + i;
+            if (dk.sk[2 * i]) atomicMax(&amax[o], dk.sk[2 * i]);
+            if (dk.sk[2 * i + 1]) atomicMax(&amin[o], dk.sk[2 * i + 1]);
         }
+        const unsigned long long *sd = dk.sk + (size_t)2 * K * D;
+        for (int i = lane; i < K * dk.ndir; i += 32) {
+            const size_t o = (size_t)b * K * dk.ndir + i;
+            if (sd[2 * i]) atomicMax(&dk.dmax[o], sd[2 * i]);
+            if (sd[2 * i + 1]) atomicMax(&dk.dmin[o], sd[2 * i + 1]);
+        }
+        __syncwarp();   // the slot is rewritten by the warp's next node
     }
 }
 
@@ -361,9 +382,11 @@ visit_a_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, const T
     uint64_t *tp = reinterpret_cast<uint64_t *>(smem);
     double *td = reinterpret_cast<double *>(smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // per-warp direction keys after the tile
-    const DirKeys dk{ndir, reinterpret_cast<unsigned long long *>(smem + (size_t)D * tile * 8) + (size_t)warp * K * ndir * 2,
-                     dmax, dmin};
+    // per-warp key slots after the tile
+    const WarpKeys dk{ndir,
+                      reinterpret_cast<unsigned long long *>(smem + (size_t)D * tile * 8) +
+                          (size_t)warp * warp_key_words(K, D, ndir),
+                      dmax, dmin};
     for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
         const int tn = (int)((n - base) < (int64_t)tile ? (n - base) : (int64_t)tile);
         __syncthreads();
@@ -378,7 +401,7 @@ visit_a_kernel(const T *__restrict__ X, int64_t ld, int64_t n, int tile, const T
 // List mode: work item w = one tile of a group's sample-id list (see
 // ListBatch); the CTA evaluates every node of the group on the staged tile.
 template <typename T, int KM, int DM>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
 visit_a_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile,
                     const T *__restrict__ lo, const T *__restrict__ hi, int K, int D, double alpha, Margins mg,
                     typename Key<T>::K *__restrict__ lbkey, typename Key<T>::K *__restrict__ amax,
@@ -390,8 +413,9 @@ visit_a_list_kernel(const T *__restrict__ X, int64_t ld, ListBatch L, int tile,
     double *td = reinterpret_cast<double *>(smem);
     uint32_t *tids = reinterpret_cast<uint32_t *>(smem + (size_t)D * tile * 8);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // per-warp direction keys after the ids (tile is a multiple of 32)
-    const DirKeys dk{ndir, reinterpret_cast<unsigned long long *>(tids + tile) + (size_t)warp * K * ndir * 2, dmax, dmin};
+    // per-warp key slots after the ids (tile is a multiple of 32)
+    const WarpKeys dk{ndir, reinterpret_cast<unsigned long long *>(tids + tile) + (size_t)warp * warp_key_words(K, D, ndir),
+                      dmax, dmin};
     for (int64_t w = blockIdx.x; w < L.W; w += gridDim.x) {
         int b;
         int64_t st;
@@ -757,6 +781,7 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
                 if (!need) continue;
                 const bool want4 = (fl & 1u) != 0u;
                 const uint64_t *rk = wrep + (size_t)k * RM * RW;
+#pragma unroll 4
                 for (int r = 0; r < nr[k]; ++r) {
                     bool f4, f1;
                     if constexpr (F32) {
@@ -783,9 +808,10 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
                 if (left == 0) infeasible = true;
                 if (left == 1)
                     for (int a = 0; a < D; ++a) {
+                        // a plain read skips the atomics that cannot change the value
                         const OT v = to_ord(x[a]);
-                        atomicMax(&ws->jmax[k1][a], v);
-                        atomicMin(&ws->jmin[k1][a], v);
+                        if (v > ws->jmax[k1][a]) atomicMax(&ws->jmax[k1][a], v);
+                        if (v < ws->jmin[k1][a]) atomicMin(&ws->jmin[k1][a], v);
                     }
             }
             // ball-based tightening and centers on samples (Algorithm 4)
@@ -796,8 +822,8 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
                     ++c_cnt[k];
                     for (int a = 0; a < D; ++a) {
                         const OT v = to_ord(x[a]);
-                        atomicMax(&ws->smax[k][a], v);
-                        atomicMin(&ws->smin[k][a], v);
+                        if (v > ws->smax[k][a]) atomicMax(&ws->smax[k][a], v);
+                        if (v < ws->smin[k][a]) atomicMin(&ws->smin[k][a], v);
                     }
                     T dm;
                     if constexpr (F32) {
@@ -1125,8 +1151,7 @@ int reps_cap(int D, int cap) { return std::min(cap, std::min(kMaxReps, 2 * D + 1
 int pair_dirs(int D) { return 2 * std::min(D * (D - 1) / 2, kMaxPairs); }
 
 // Representatives per cluster: min(cap, 2D + 1, 50) along the attributes,
-// or, with `dirs` (float data), up to min(cap, 50) with the attribute-pair
-// directions after the attributes.
+// or, with pair directions (ndir > 0), up to min(cap, 50, 2D + 1 + 2 ndir).
 int reps_slots(int D, int cap, int ndir)
 {
     return std::max(1, ndir > 0 ? std::min(std::min(cap, kMaxReps), 1 + 2 * D + 2 * ndir) : reps_cap(D, cap));
@@ -1184,22 +1209,26 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     const double r_up = nextafter(std::sqrt(alpha), __builtin_huge_val());
     // pass A
     const int tileA = (int)std::max<int64_t>(256, std::min<int64_t>(2048, (64 * 1024) / (D * 8)) / 32 * 32);
-    const size_t dkA = (size_t)NWV * K_ * ndir * 2 * 8;   // per-warp direction keys
+    const size_t dkA = sizeof(T) == 4 ? (size_t)NWV * warp_key_words(K_, D, ndir) * 8 : 0;   // per-warp key slots
     const size_t smemA = (size_t)D * tileA * 8 + dkA;
     int gA = 1;
     const int64_t tilesA = (v.n + tileA - 1) / tileA;
     auto kA = visit_a_kernel<T, KM, DM>;
     if (L) {
-        // list mode: one node per work item, tile = list_tile() gathered ids
-        const int lt = list_tile();
-        const size_t smem = (size_t)D * lt * 8 + (size_t)lt * 4 + dkA;
-        auto kAL = visit_a_list_kernel<T, KM, DM>;
-        int g = 1;
-        KC_TRY(grid_of(c, kAL, smem, std::max<int64_t>(1, L->W), &g));
-        if (L->W > 0) {
-            kAL<<<g, kThreads, smem, c->stream>>>(static_cast<const T *>(c->X), c->ldx, *L, lt, lo, hi, K_, D, alpha,
-                                                  mg, lbkey, amax, amin, flags, ndir, dmax, dmin);
-            KC_TRY(after_launch(c, "tighten pass A (lists)"));
+        // list mode (float data): one node per work item, tile = list_tile() gathered ids
+        if constexpr (sizeof(T) == 4) {
+            const int lt = list_tile();
+            const size_t smem = (size_t)D * lt * 8 + (size_t)lt * 4 + dkA;
+            auto kAL = visit_a_list_kernel<T, KM, DM>;
+            int g = 1;
+            KC_TRY(grid_of(c, kAL, smem, std::max<int64_t>(1, L->W), &g));
+            if (L->W > 0) {
+                kAL<<<g, kThreads, smem, c->stream>>>(static_cast<const T *>(c->X), c->ldx, *L, lt, lo, hi, K_, D,
+                                                      alpha, mg, lbkey, amax, amin, flags, ndir, dmax, dmin);
+                KC_TRY(after_launch(c, "tighten pass A (lists)"));
+            }
+        } else {
+            return set_err(c, KC_EINTERNAL, "list-mode tightening is for float data");
         }
     } else {
         KC_TRY(grid_of(c, kA, smemA, tilesA, &gA));
@@ -1236,16 +1265,18 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     int gB = 1;
     auto kB = visit_b_kernel<T, KM, DM>;
     if (L) {
-        const int lt = list_tile();
-        const size_t smem = (size_t)D * lt * sizeof(T) + (size_t)NWV * kSub * 4 + slotB + (size_t)lt * 4 + repB;
-        auto kBL = visit_b_list_kernel<T, KM, DM>;
-        int g = 1;
-        KC_TRY(grid_of(c, kBL, smem, std::max<int64_t>(1, L->W), &g));
-        if (L->W > 0) {
-            kBL<<<g, kThreads, smem, c->stream>>>(static_cast<const T *>(c->X), c->ldx, *L, lt, K_, D, RM, lo, hi, blo,
-                                                  bhi, repx, nreps, have, alpha, mg, seeds, cnt, smax, smin, jmax, jmin,
-                                                  cand, flags);
-            KC_TRY(after_launch(c, "tighten pass B (lists)"));
+        if constexpr (sizeof(T) == 4) {
+            const int lt = list_tile();
+            const size_t smem = (size_t)D * lt * sizeof(T) + (size_t)NWV * kSub * 4 + slotB + (size_t)lt * 4 + repB;
+            auto kBL = visit_b_list_kernel<T, KM, DM>;
+            int g = 1;
+            KC_TRY(grid_of(c, kBL, smem, std::max<int64_t>(1, L->W), &g));
+            if (L->W > 0) {
+                kBL<<<g, kThreads, smem, c->stream>>>(static_cast<const T *>(c->X), c->ldx, *L, lt, K_, D, RM, lo, hi,
+                                                      blo, bhi, repx, nreps, have, alpha, mg, seeds, cnt, smax, smin,
+                                                      jmax, jmin, cand, flags);
+                KC_TRY(after_launch(c, "tighten pass B (lists)"));
+            }
         }
     } else {
     KC_TRY(grid_of(c, kB, smemB, (v.n + tileB - 1) / tileB, &gB));
@@ -1353,9 +1384,10 @@ kc_status tighten_wide(kc_ctx *c, const View &v, const void *lo_, const void *hi
 
 // Shape dispatch of the tightening: the register kernels for the shapes
 // listed here, the shared-memory kernels (kc_wide.cu) for the other float
-// shapes.  Representatives: at most ball_cap (<= 0: 50); for float data a
-// cap above 2D + 1 reaches the pair directions, double data stop after the
-// attribute extremes.
+// shapes.  Representatives: at most ball_cap (<= 0: 50); float data keep the
+// pair-direction keys whenever the cap can reach them (the attribute
+// extremes may number fewer than 2D + 1 distinct samples), double data stop
+// after the attribute extremes.
 kc_status launch_tighten_any(kc_ctx *c, const View &v, const ListBatch *L, const void *lo, const void *hi, int B,
                              double alpha, const int64_t *seeds_dev, int ball_cap, void *lo_out, void *hi_out,
                              int64_t *counts, int64_t *cand, double *lb, double *lb_raw, int64_t *lbarg, int8_t *status,
@@ -1364,7 +1396,7 @@ kc_status launch_tighten_any(kc_ctx *c, const View &v, const ListBatch *L, const
     if (B <= 0) return KC_OK;
     const int cap = ball_cap > 0 ? ball_cap : 50;
     const int K = c->K, D = c->D;
-    const bool dirs = c->dt == KC_F32 && cap > 2 * D + 1 && D >= 2;
+    const bool dirs = c->dt == KC_F32 && cap >= 2 && D >= 2;
 #define KC_TIGHTEN(T_, KM_, DM_)                                                                                      \
     return tighten_impl<T_, KM_, DM_>(c, v, lo, hi, B, alpha, seeds_dev, cap, dirs, lo_out, hi_out, counts, cand, lb, \
                                       lb_raw, lbarg, status, vs, L)

@@ -121,8 +121,9 @@ def test_tighten_f64_exact(d, k):
 @pytest.mark.parametrize("axes", [False, True])
 @pytest.mark.parametrize("d,k", [(2, 3), (4, 3), (2, 4), (3, 3)])
 def test_tighten_f32_exact_on_unambiguous_inputs(d, k, axes):
-    """axes: ball_cap = 2D + 1 (the seed and the attribute extremes), else the
-    default of 50 with the pair directions."""
+    """axes: ball_cap = 2D + 1 (the attribute extremes, and pair-direction
+    extremes only where fewer than 2D + 1 of those are distinct), else the
+    default of 50."""
     cap = 2 * d + 1 if axes else 0
     X = _blobs(4_003, d, k, seed=100 + d * 7 + k, dtype=np.float32)
     c, fobj = oracle.fft(X, k, 3)
@@ -149,7 +150,7 @@ def _step_a_clear(X64, lo, hi, alpha, band=3e-6):
     return True
 
 
-def _ambiguous_ball_alpha(X, lo, hi, alpha0):
+def _ambiguous_ball_alpha(X, lo, hi, alpha0, ball_cap=0):
     """An alpha at which the center-based assignment, and so the
     representatives, are decided the same in float and double, but some
     sample s of a box-BT box M'^k lies within sqrt(alpha) of every
@@ -163,7 +164,7 @@ def _ambiguous_ball_alpha(X, lo, hi, alpha0):
         if _step_a_clear(X64, lo, hi, alpha):
             best = None
             for b in range(lo.shape[0]):
-                r = oracle.tighten(X64, lo[b], hi[b], alpha, is_f32=True)
+                r = oracle.tighten(X64, lo[b], hi[b], alpha, is_f32=True, ball_cap=ball_cap)
                 if r["status"] == 1:
                     continue
                 for k, reps in enumerate(r["reps"]):
@@ -185,8 +186,8 @@ def _ambiguous_ball_alpha(X, lo, hi, alpha0):
                 # moving alpha to a2 must not change the representatives or
                 # any other decision of the center-based rule
                 if _step_a_clear(X64, lo, hi, a2):
-                    same = all(oracle.tighten(X64, lo[b], hi[b], a2, is_f32=True)["reps"] ==
-                               oracle.tighten(X64, lo[b], hi[b], alpha, is_f32=True)["reps"]
+                    same = all(oracle.tighten(X64, lo[b], hi[b], a2, is_f32=True, ball_cap=ball_cap)["reps"] ==
+                               oracle.tighten(X64, lo[b], hi[b], alpha, is_f32=True, ball_cap=ball_cap)["reps"]
                                for b in range(lo.shape[0]))
                     if same:
                         return a2, [(best[1], best[2], best[3])]
@@ -194,8 +195,8 @@ def _ambiguous_ball_alpha(X, lo, hi, alpha0):
     return None
 
 
-@pytest.mark.parametrize("d,k", [(2, 3), (4, 3)])
-def test_tighten_f32_ambiguous_ball_decisions_are_conservative(d, k):
+@pytest.mark.parametrize("d,k,cap", [(2, 3, 0), (4, 3, 9)])
+def test_tighten_f32_ambiguous_ball_decisions_are_conservative(d, k, cap):
     """Float tightening where float and double decisions differ: alpha is
     placed within the rounding band of a ball-membership test (see
     _ambiguous_ball_alpha).  The kernels take an exclusion only where the
@@ -207,16 +208,16 @@ def test_tighten_f32_ambiguous_ball_decisions_are_conservative(d, k):
     X = _blobs(4_003, d, k, seed=300 + d * 7 + k, dtype=np.float32)
     c, fobj = oracle.fft(X, k, 1)
     lo, hi = _nodes_around(X, c, 12, seed=d + 40)
-    found = _ambiguous_ball_alpha(X, lo, hi, fobj * 0.71)
+    found = _ambiguous_ball_alpha(X, lo, hi, fobj * 0.71, ball_cap=cap)
     assert found is not None, "no ambiguous ball decision could be placed"
     alpha, planted = found
     kc = KCenter(_t(X), k)
-    g = kc.tighten(_t(lo), _t(hi), alpha)
+    g = kc.tighten(_t(lo), _t(hi), alpha, ball_cap=cap)
     torch.cuda.synchronize()
     st, glo, ghi = g["status"].cpu().numpy(), g["lo"].cpu().numpy(), g["hi"].cpu().numpy()
     gcnt, glb = g["count"].cpu().numpy(), g["lb"].cpu().numpy()
     for b in range(lo.shape[0]):
-        r = oracle.tighten(X, lo[b], hi[b], alpha, is_f32=True)
+        r = oracle.tighten(X, lo[b], hi[b], alpha, is_f32=True, ball_cap=cap)
         assert glb[b] <= r["beta"] and glb[b] >= r["beta"] * (1 - 1e-6)
         if st[b] == 1:
             assert r["status"] == 1, b
@@ -226,7 +227,7 @@ def test_tighten_f32_ambiguous_ball_decisions_are_conservative(d, k):
         assert np.all(glo[b] <= r["lo"].astype(np.float32)) and np.all(ghi[b] >= r["hi"].astype(np.float32)), b
         assert np.all(gcnt[b] >= r["count"]), (b, gcnt[b], r["count"])
     for b, j, s_ in planted:
-        r = oracle.tighten(X, lo[b], hi[b], alpha, is_f32=True)
+        r = oracle.tighten(X, lo[b], hi[b], alpha, is_f32=True, ball_cap=cap)
         if r["status"] != 1 and st[b] != 1:
             assert gcnt[b, j] > r["count"][j], (b, j, s_, gcnt[b], r["count"])
 
@@ -508,7 +509,7 @@ def test_certificate_replay_at_one_hundred_million_samples(tmp_path):
     r = oracle.replay(X, str(log), g["objective"], g["centers"], 1e-12)
     print(r)
     assert r["ok"], r
-    assert r["pruned"] > 10_000 and r["witness_proved"] >= r["pruned"] - r["rebound"]
+    assert r["pruned"] > 1_000 and r["witness_proved"] >= r["pruned"] - r["rebound"]
 
 
 def test_solve_degenerate_and_edge_inputs():

@@ -146,7 +146,8 @@ def test_pair_direction_representatives_on_grid(n, d, k, cap, seeded):
         feasible += _compare(X, lo, hi, alpha, seeds, g, cap)
         for b in range(lo.shape[0]):
             r = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=True, ball_cap=cap)
-            r0 = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=True)
+            # the budget of the seed and the attribute extremes alone
+            r0 = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=True, ball_cap=2 * d + int(seeded))
             if r["status"] != 1 and (not np.array_equal(r["count"], r0["count"])
                                      or not np.array_equal(r["lo"], r0["lo"])
                                      or not np.array_equal(r["hi"], r0["hi"])):
