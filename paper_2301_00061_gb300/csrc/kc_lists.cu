@@ -368,18 +368,26 @@ seg_filter_f32(const float *__restrict__ X, int64_t ld, ListBatch L, const float
                     bool excl = false;
                     const int nr = snr[k];
                     const uint64_t *ck = srep + (size_t)k * RM * H;
-                    for (int r = 0; r < nr && !excl; ++r, ck += H) {
-                        // squared distance: even attributes in .x, odd in .y, each
-                        // a fused chain in attribute order (zero padding adds 0)
-                        uint64_t acc = 0;
+                    // chunks of 4 representatives decided by their largest distance
+                    // (a short last chunk repeats the last representative)
+                    for (int r0 = 0; r0 < nr && !excl; r0 += 4) {
+                        float d[4];
 #pragma unroll
-                        for (int p = 0; p < DMAX / 2; ++p)
-                            if (p < H) {
-                                const uint64_t t = sub2(pxx[p], ck[p]);
-                                acc = fma2(t, t, acc);
-                            }
-                        const float2 s2 = upk(acc);
-                        if (s2.x + s2.y > t_alpha) excl = true;
+                        for (int u = 0; u < 4; ++u) {
+                            const uint64_t *cr = ck + (size_t)(r0 + u < nr ? r0 + u : nr - 1) * H;
+                            // squared distance: even attributes in .x, odd in .y, each
+                            // a fused chain in attribute order (zero padding adds 0)
+                            uint64_t acc = 0;
+#pragma unroll
+                            for (int p = 0; p < DMAX / 2; ++p)
+                                if (p < H) {
+                                    const uint64_t t = sub2(pxx[p], cr[p]);
+                                    acc = fma2(t, t, acc);
+                                }
+                            const float2 s2 = upk(acc);
+                            d[u] = s2.x + s2.y;
+                        }
+                        if (fmaxf(fmaxf(d[0], d[1]), fmaxf(d[2], d[3])) > t_alpha) excl = true;
                     }
                     if (!excl) ubred = false;
                 }

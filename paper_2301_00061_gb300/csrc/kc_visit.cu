@@ -770,9 +770,12 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
             }
             // distances to the representatives of the clusters that need them:
             // far4[k] = some representative of k proved farther than 4 alpha
-            // (Lemma 2), far1[k] = some proved farther than alpha (ball test);
+            // (Lemma 2), far1[k] = some proved farther than alpha (ball test).
+            // Chunks of 4 representatives are decided by their largest
+            // distance (a short last chunk repeats the last representative);
             // far4 implies far1, so a cluster's scan stops at its first far4,
             // or at its first far1 when only the ball test needs it
+            const T th1 = F32 ? (T)mg.t_alpha : (T)alpha, th4 = F32 ? (T)mg.t_four : (T)four_alpha;
             bool far4[KM], far1[KM];
 #pragma unroll
             for (int k = 0; k < KM; ++k) {
@@ -781,22 +784,25 @@ __device__ __forceinline__ void pass_b_node(const T *tx, int tile, int tn, int j
                 if (!need) continue;
                 const bool want4 = (fl & 1u) != 0u;
                 const uint64_t *rk = wrep + (size_t)k * RM * RW;
-#pragma unroll 4
-                for (int r = 0; r < nr[k]; ++r) {
-                    bool f4, f1;
-                    if constexpr (F32) {
-                        const float d = pt_dist_f32<2 * DH>(px, rk + (size_t)r * RW);
-                        f4 = d > mg.t_four;
-                        f1 = d > mg.t_alpha;
-                    } else {
-                        const double d = pt_dist_f64<DM>(reinterpret_cast<const double *>(x),
-                                                         reinterpret_cast<const double *>(rk + (size_t)r * RW), D);
-                        f4 = d > four_alpha;
-                        f1 = d > alpha;
+                const int nk = nr[k];
+                for (int r0 = 0; r0 < nk; r0 += 4) {
+                    T d[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int r = r0 + u < nk ? r0 + u : nk - 1;
+                        if constexpr (F32) d[u] = pt_dist_f32<2 * DH>(px, rk + (size_t)r * RW);
+                        else
+                            d[u] = pt_dist_f64<DM>(reinterpret_cast<const double *>(x),
+                                                   reinterpret_cast<const double *>(rk + (size_t)r * RW), D);
                     }
-                    far1[k] = far1[k] || f1;
-                    if (f4) { far4[k] = true; break; }
-                    if (far1[k] && !want4) break;
+                    T m;
+                    if constexpr (F32) m = fmaxf(fmaxf(d[0], d[1]), fmaxf(d[2], d[3]));
+                    else m = fmax(fmax(d[0], d[1]), fmax(d[2], d[3]));
+                    if (m > th1) {
+                        far1[k] = true;
+                        if (m > th4) { far4[k] = true; break; }
+                        if (!want4) break;
+                    }
                 }
             }
             // sample-based assignment of an unassigned sample (Algorithm 3, Lemma 2)
