@@ -204,6 +204,24 @@ struct WarpKeys {
 // u64 words of a warp's key slot
 __host__ __device__ constexpr int warp_key_words(int K, int D, int ndir) { return 2 * K * D + 2 * K * ndir; }
 
+// Raise the float key at `slot` (max) and `slot + 1` (min) by value v of the
+// sample at position pos.  A key's high word is the ordered value, so a 32-bit
+// read of it decides all but the ties; the stored keys only grow, so a stale
+// read can only cost an atomic that changes nothing.
+__device__ __forceinline__ void raise_keys(unsigned long long *slot, float v, uint32_t pos)
+{
+    const uint32_t o = ord_f32(v);
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(slot);   // little-endian: high words at 1, 3
+    if (o >= w[1]) {
+        const unsigned long long k = ((unsigned long long)o << 32) | (unsigned long long)(0xFFFFFFFFu - pos);
+        if (k > slot[0]) atomicMax(&slot[0], k);
+    }
+    if (~o >= w[3]) {
+        const unsigned long long k = ((unsigned long long)(~o) << 32) | (unsigned long long)(0xFFFFFFFFu - pos);
+        if (k > slot[1]) atomicMax(&slot[1], k);
+    }
+}
+
 template <typename T, int KM, int DM>
 __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td, int tile, int tn, int j0, int step,
                                             const uint32_t *tids, int64_t base, const T *__restrict__ lo,
@@ -294,11 +312,7 @@ __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td
                 unsigned long long *sa = dk.sk + (size_t)k1 * D * 2;
 #pragma unroll
                 for (int a = 0; a < DM; ++a)
-                    if (a < D) {
-                        const KY k0 = KT::max_of(x[a], pos), k1_ = KT::min_of(x[a], pos);
-                        if (k0 > sa[2 * a]) atomicMax(&sa[2 * a], k0);
-                        if (k1_ > sa[2 * a + 1]) atomicMax(&sa[2 * a + 1], k1_);
-                    }
+                    if (a < D) raise_keys(sa + 2 * a, x[a], pos);
                 if (dk.ndir > 0) {
                     unsigned long long *s = dk.sk + (size_t)2 * K * D + (size_t)k1 * dk.ndir * 2;
                     int q = 0;
@@ -307,13 +321,8 @@ __device__ __forceinline__ void pass_a_node(const uint64_t *tp, const double *td
 #pragma unroll
                         for (int c = a + 1; c < DM; ++c)
                             if (c < D && q < dk.ndir) {
-                                const float vs = __fadd_rn(x[a], x[c]), vd = __fsub_rn(x[a], x[c]);
-                                const KY k0 = KT::max_of(vs, pos), k1_ = KT::min_of(vs, pos);
-                                const KY k2 = KT::max_of(vd, pos), k3 = KT::min_of(vd, pos);
-                                if (k0 > s[2 * q]) atomicMax(&s[2 * q], k0);
-                                if (k1_ > s[2 * q + 1]) atomicMax(&s[2 * q + 1], k1_);
-                                if (k2 > s[2 * q + 2]) atomicMax(&s[2 * q + 2], k2);
-                                if (k3 > s[2 * q + 3]) atomicMax(&s[2 * q + 3], k3);
+                                raise_keys(s + 2 * q, __fadd_rn(x[a], x[c]), pos);
+                                raise_keys(s + 2 * q + 2, __fsub_rn(x[a], x[c]), pos);
                                 q += 2;
                             }
                 }
