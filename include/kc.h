@@ -285,7 +285,10 @@ kc_status kc_fp32_probe(int32_t mode, void *stream, double *lane_ops_per_s, floa
  *                   value <= alpha, 2 leaf (every tightened box is a point).
  * ball_cap: the representatives' budget ("at most 50 balls" of Section
  * 4.1.2), at most min(ball_cap, 50) per cluster; <= 0 selects the default
- * of 50.  In order: the seed, the arg-min and arg-max of each attribute,
+ * of 50, except KC_BALLS_ALL: every sample of J_A^k (the samples step A
+ * assigns to k, and the seed of k) is a representative of k -- the ball-BT
+ * without a budget, S x |J_A^k| distances per node, run as a tiled pass
+ * (float data, D <= 16; otherwise KC_EINVAL).  In order: the seed, the arg-min and arg-max of each attribute,
  * then, for float data, the arg-min and arg-max of x_a + x_b and of
  * x_a - x_b (added in float) for the first min(D(D-1)/2, 16) pairs a < b in
  * lexicographic order; ties go to the smaller sample index, duplicates are
@@ -295,6 +298,7 @@ kc_status kc_fp32_probe(int32_t mode, void *stream, double *lane_ops_per_s, floa
  * shape; the others kernels whose node state lives in shared memory sized at
  * launch); double data K <= 4 with D <= 4.  Other shapes return KC_EINVAL.
  */
+#define KC_BALLS_ALL (-1)
 kc_status kc_tighten(kc_ctx *ctx, const void *lo, const void *hi, int32_t B, double alpha,
                      const int64_t *seeds, int32_t ball_cap, void *lo_out, void *hi_out,
                      int64_t *counts, int64_t *cand, double *lb_out, int8_t *status);
@@ -360,7 +364,8 @@ typedef struct {
     double time_limit_s;   /* 0: none */
     int64_t node_limit;    /* 0: none */
     int32_t batch;         /* 0: automatic; nodes bounded per launch */
-    int32_t ball_cap;      /* 50: representatives per cluster, as kc_tighten's ball_cap */
+    int32_t ball_cap;      /* 50: representatives per cluster, as kc_tighten's ball_cap
+                              (KC_BALLS_ALL: float data, D <= 16, lists = 0) */
     int32_t i_sr;          /* 1: sample reduction every i_sr batches, 0: off */
     int32_t use_bt;        /* 1: assignment + bounds tightening (BB+CF+BT); 0: BB+CF */
     int32_t order;         /* 0: best bound, max-range branching; 1: learned scorer (kc_set_scorer) */

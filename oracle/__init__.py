@@ -25,6 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 MAXK, MAXD, MAXREPS = 16, 64, 50
+BALLS_ALL = -1   # ball_cap: every sample assigned to a cluster is one of its representatives
 
 
 GCC_FLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-fopenmp"]
@@ -268,7 +269,9 @@ def tighten(X, lo, hi, alpha, seeds=None, active=None, is_f32=False, ball_cap=0)
     """Cluster assignment + bounds tightening of one node; returns a dict.
     Representatives per cluster: at most min(ball_cap, 50) (ball_cap <= 0:
     50), the seed, then the extremes along the attributes, then, for float
-    data, along attribute-pair directions."""
+    data, along attribute-pair directions; ball_cap = BALLS_ALL: every sample
+    assigned to the cluster in step A (the reported "reps" stay the default
+    ones)."""
     X, lo, hi = _f64(X), _f64(lo), _f64(hi)
     n, d = X.shape
     k = lo.shape[0]

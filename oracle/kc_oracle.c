@@ -33,6 +33,9 @@
 #define KCO_MAXK 16
 #define KCO_MAXD 64
 #define KCO_MAXREPS 50
+/* ball_cap value: every sample assigned to cluster k in step A is a
+ * representative of k (no budget; the paper's unrestricted ball-BT) */
+#define KCO_BALLS_ALL (-1)
 
 /* ---------------------------------------------------------------------- */
 /* Elementary pieces                                                       */
@@ -516,8 +519,11 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
 {
     if (K > KCO_MAXK || D > KCO_MAXD) return 1;
     /* at most ball_cap representatives (<= 0: the default of 50, which is
-     * also the largest); pair directions for float data only */
+     * also the largest); pair directions for float data only.  KCO_BALLS_ALL:
+     * step B tests against every sample of J_A^k instead (the reported
+     * representatives are then the default ones, for information) */
     const int diag = is_f32 != 0;
+    const int all_balls = ball_cap == KCO_BALLS_ALL;
     if (ball_cap <= 0 || ball_cap > KCO_MAXREPS) ball_cap = KCO_MAXREPS;
     const int npairs = D * (D - 1) / 2 < KCO_MAXPAIRS ? D * (D - 1) / 2 : KCO_MAXPAIRS;
     const int ndir = diag ? 2 * npairs : 0;
@@ -612,6 +618,21 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
         if (out->n_reps[k] == 0) all_have = 0;
     }
 
+    /* J_A^k as index lists (for KCO_BALLS_ALL): samples with asg == k, in order */
+    int64_t *jl = NULL, joff[KCO_MAXK + 1];
+    if (all_balls) {
+        jl = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+        if (!jl) { free(asg); return 2; }
+        for (int k = 0; k <= K; ++k) joff[k] = 0;
+        for (int64_t s = 0; s < N; ++s)
+            if (asg[s] >= 0) ++joff[asg[s] + 1];
+        for (int k = 0; k < K; ++k) joff[k + 1] += joff[k];
+        int64_t fill[KCO_MAXK];
+        for (int k = 0; k < K; ++k) fill[k] = joff[k];
+        for (int64_t s = 0; s < N; ++s)
+            if (asg[s] >= 0) jl[fill[asg[s]]++] = s;
+    }
+
     /* step B */
     double slo[KCO_MAXK * KCO_MAXD], shi[KCO_MAXK * KCO_MAXD];
     double bmin2[KCO_MAXK * KCO_MAXD], bmax2[KCO_MAXK * KCO_MAXD];
@@ -630,8 +651,13 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
             int left = 0, kk = -1;
             for (int k = 0; k < K; ++k) {
                 int excl = 0;
-                for (int q = 0; q < out->n_reps[k] && !excl; ++q)
-                    if (sqdist(x, X + out->reps[k * KCO_MAXREPS + q] * D, D) > four_alpha) excl = 1;
+                if (all_balls) {
+                    for (int64_t q = joff[k]; q < joff[k + 1] && !excl; ++q)
+                        if (sqdist(x, X + jl[q] * D, D) > four_alpha) excl = 1;
+                } else {
+                    for (int q = 0; q < out->n_reps[k] && !excl; ++q)
+                        if (sqdist(x, X + out->reps[k * KCO_MAXREPS + q] * D, D) > four_alpha) excl = 1;
+                }
                 if (!excl) { ++left; kk = k; }
             }
             if (left == 0) infeasible = 1;
@@ -647,8 +673,13 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
         for (int k = 0; k < K; ++k) {
             if (!in_box(x, blo + k * D, bhi + k * D, D)) continue;
             int ok = 1;
-            for (int q = 0; q < out->n_reps[k] && ok; ++q)
-                if (sqdist(x, X + out->reps[k * KCO_MAXREPS + q] * D, D) > alpha) ok = 0;
+            if (all_balls) {
+                for (int64_t q = joff[k]; q < joff[k + 1] && ok; ++q)
+                    if (sqdist(x, X + jl[q] * D, D) > alpha) ok = 0;
+            } else {
+                for (int q = 0; q < out->n_reps[k] && ok; ++q)
+                    if (sqdist(x, X + out->reps[k * KCO_MAXREPS + q] * D, D) > alpha) ok = 0;
+            }
             if (!ok) continue;
             ++out->count[k];
             for (int a = 0; a < D; ++a) {
@@ -678,6 +709,7 @@ int kco_tighten(const double *X, int64_t N, int D, int K, const double *lo, cons
         }
     }
     free(asg);
+    free(jl);
     if (infeasible) { out->status = 1; return 0; }
     int leaf = 1;
     for (int i = 0; i < KD; ++i)

@@ -30,6 +30,7 @@ __all__ = [
 
 KC_F32, KC_F64 = 0, 1
 KC_ROW_MAJOR, KC_COL_MAJOR = 0, 1
+KC_BALLS_ALL = -1   # ball_cap: every sample assigned to a cluster is one of its representatives
 _STATUS = {0: "KC_OK", 1: "KC_EINVAL", 2: "KC_ENOMEM", 3: "KC_ECUDA", 4: "KC_ETIMEOUT",
            5: "KC_ELIMIT", 6: "KC_EINTERNAL"}
 

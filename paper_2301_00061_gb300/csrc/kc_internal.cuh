@@ -30,6 +30,7 @@ struct DevBuf {
 // Workspace and outputs of one tightening call that later steps reuse.
 struct VisitScratch {
     DevBuf buf;
+    DevBuf jbuf;                     // every-sample representatives: the sets J_A^k as lists
     const int64_t *reps = nullptr;   // [B][K][RM] representative sample ids (-1 unused)
     const int *nreps = nullptr;      // [B][K]
     const void *repx = nullptr;      // [B][K][RM][D] their coordinates
@@ -226,6 +227,15 @@ kc_status launch_sample_reduction_view(kc_ctx *c, const View &v, const void *lo,
 
 // Passes A and B of the float tightening for any K <= 16, D <= 64 (kc_wide.cu;
 // the workspace and finalize kernels are kc_visit.cu's).
+// Step B with every sample of J_A^k as a representative of k (no budget):
+// builds the sets J_A^k of the B nodes as lists of view positions in
+// vs->jbuf, then runs the tiled sample x J_A^k pass; same accumulators as
+// launch_wide_b.
+kc_status launch_wide_ball_all(kc_ctx *c, const View &v, const float *lo, const float *hi, int B, const Margins &mg,
+                               const float *blo, const float *bhi, const int *allhave, const int64_t *seeds,
+                               unsigned long long *cnt, unsigned long long *cand, unsigned *smax, unsigned *smin,
+                               unsigned *jmax, unsigned *jmin, unsigned *flags, VisitScratch *vs);
+
 // ndir > 0 (at most 32): also the arg-extreme keys of the assigned samples
 // along the attribute-pair directions, dmax / dmin [B][K][ndir].
 kc_status launch_wide_a(kc_ctx *c, const View &v, const ListBatch *L, const float *lo, const float *hi, int B,

@@ -1438,6 +1438,8 @@ kc_status kc_solve(kc_ctx *c, double tol, const kc_solve_opts *opt, kc_result *o
     if (o.order == 1 && !c->scorer) return set_err(c, KC_EINVAL, "kc_solve: order = 1 needs kc_set_scorer");
     if (o.lists != 0 && o.lists != 1) return set_err(c, KC_EINVAL, "kc_solve: lists must be 0 or 1");
     if (o.arena_mb < 0) return set_err(c, KC_EINVAL, "kc_solve: arena_mb must be >= 0");
+    if (o.ball_cap == KC_BALLS_ALL && (c->dt != KC_F32 || c->D > 16 || (o.lists && c->D <= 8)))
+        return set_err(c, KC_EINVAL, "kc_solve: ball_cap = KC_BALLS_ALL needs float data, D <= 16 and lists = 0");
     if (o.explore < 0 || o.explore > 100) return set_err(c, KC_EINVAL, "kc_solve: explore must be in [0, 100]");
     if (!(o.rule_margin >= 0.0)) return set_err(c, KC_EINVAL, "kc_solve: rule_margin must be >= 0");
     if (o.fft_starts < 0 || o.fft_starts > 4096) return set_err(c, KC_EINVAL, "kc_solve: fft_starts must be in [0, 4096]");

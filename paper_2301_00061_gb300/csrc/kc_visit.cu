@@ -1322,7 +1322,7 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
 kc_status tighten_wide(kc_ctx *c, const View &v, const void *lo_, const void *hi_, int B, double alpha,
                        const int64_t *seeds, int cap, bool dirs, void *lo_out_, void *hi_out_, int64_t *counts,
                        int64_t *cand_out, double *lb, double *lb_raw, int64_t *lbarg, int8_t *status, VisitScratch *vs,
-                       const ListBatch *L = nullptr)
+                       const ListBatch *L = nullptr, bool all_balls = false)
 {
     using T = float;
     using KY = unsigned long long;
@@ -1384,8 +1384,12 @@ kc_status tighten_wide(kc_ctx *c, const View &v, const void *lo_, const void *hi
         B, K_, D, lo, hi, lbkey, amax, amin, flags, static_cast<const T *>(c->X), c->ldx, fa, blo, bhi, reps, nreps,
         repx, have, lb, lb_raw, lbarg);
     KC_TRY(after_launch(c, "tighten finalize A"));
-    KC_TRY(launch_wide_b(c, v, L, lo, hi, B, mg, blo, bhi, repx, nreps, have, seeds, RM, cnt, cand, smax, smin, jmax,
-                         jmin, flags));
+    if (all_balls)
+        KC_TRY(launch_wide_ball_all(c, v, lo, hi, B, mg, blo, bhi, have, seeds, cnt, cand, smax, smin, jmax, jmin, flags,
+                                    vs));
+    else
+        KC_TRY(launch_wide_b(c, v, L, lo, hi, B, mg, blo, bhi, repx, nreps, have, seeds, RM, cnt, cand, smax, smin,
+                             jmax, jmin, flags));
     finalize_b_kernel<T><<<(B + 127) / 128, 128, 0, c->stream>>>(B, K_, D, cnt, smax, smin, jmax, jmin, cand, flags,
                                                                 L ? nullptr : v.ids, r_up, static_cast<T *>(lo_out_),
                                                                 static_cast<T *>(hi_out_), counts, cand_out, status);
@@ -1412,6 +1416,14 @@ kc_status launch_tighten_any(kc_ctx *c, const View &v, const ListBatch *L, const
     const int cap = ball_cap > 0 ? ball_cap : 50;
     const int K = c->K, D = c->D;
     const bool dirs = c->dt == KC_F32 && cap >= 2 && D >= 2;
+    if (ball_cap == KC_BALLS_ALL) {
+        // every sample of J_A^k a representative: the tiled pass of kc_wide.cu
+        if (c->dt != KC_F32 || L || D > 16)
+            return set_err(c, KC_EINVAL,
+                           "ball_cap = KC_BALLS_ALL: float data, D <= 16, a shared sample set (D=%d)", D);
+        return tighten_wide(c, v, lo, hi, B, alpha, seeds_dev, cap, dirs, lo_out, hi_out, counts, cand, lb, lb_raw,
+                            lbarg, status, vs, nullptr, true);
+    }
 #define KC_TIGHTEN(T_, KM_, DM_)                                                                                      \
     return tighten_impl<T_, KM_, DM_>(c, v, lo, hi, B, alpha, seeds_dev, cap, dirs, lo_out, hi_out, counts, cand, lb, \
                                       lb_raw, lbarg, status, vs, L)

@@ -13,6 +13,8 @@
 // once per (tile, node).
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "kc_device.cuh"
 #include "kc_internal.cuh"
 
@@ -402,6 +404,198 @@ wide_b_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int tile, List
     }
 }
 
+// ------------------------------------------------- every-sample step B
+// The step-A sets J_A^k of node b: the samples whose center-based rule
+// leaves exactly the cluster k (Lemma 1, the float decisions of pass A) and
+// the seed of k.  jpool == NULL: counts |J_A^k| into jcnt [B][K]; otherwise
+// writes view positions at jpool[joff[b][k] + slot], slot taken from jcnt
+// (reset to 0 before), one atomic per warp and cluster.
+__global__ void __launch_bounds__(kWT)
+jall_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int tile, int B, int K, int D,
+            const float *__restrict__ lo, const float *__restrict__ hi, Margins mg, const uint32_t *__restrict__ ids,
+            const int64_t *__restrict__ seeds, unsigned long long *__restrict__ jcnt,
+            const int64_t *__restrict__ joff, uint32_t *__restrict__ jpool)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *tp = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *sbx = tp + (size_t)D * tile;   // [K][D] boxes of the current node
+    const int KD = K * D, lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
+        const int tn = (int)((n - base) < (int64_t)tile ? (n - base) : (int64_t)tile);
+        __syncthreads();
+        wide_stage(X, ld, D, tile, tn, base, nullptr, tp);
+        for (int b = 0; b < B; ++b) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < KD; i += kWT) sbx[i] = pk(lo[(size_t)b * KD + i], -hi[(size_t)b * KD + i]);
+            __syncthreads();
+            for (int j = threadIdx.x; j < tn; j += kWT) {
+                const int64_t pos = base + j, id = ids ? (int64_t)ids[pos] : pos;
+                int kk = -1;
+                if (seeds)
+                    for (int k = 0; k < K; ++k)
+                        if (seeds[k] == id) kk = k;
+                if (kk < 0) {
+                    int left = 0, k1 = -1;
+                    for (int k = 0; k < K; ++k)
+                        if (!(wide_box_dist(tp, tile, j, sbx + (size_t)k * D, D) > mg.t_alpha)) { ++left; k1 = k; }
+                    if (left == 1) kk = k1;
+                }
+                // lanes of a warp with the same cluster share one atomic
+                const unsigned grp = __match_any_sync(__activemask(), kk);
+                const int leader = __ffs(grp) - 1, rank = __popc(grp & ((1u << lane) - 1u));
+                unsigned long long slot = 0ull;
+                const size_t o = (size_t)b * K + (kk < 0 ? 0 : kk);
+                if (kk >= 0 && lane == leader) slot = atomicAdd(&jcnt[o], (unsigned long long)__popc(grp));
+                slot = __shfl_sync(grp, slot, leader);
+                if (kk >= 0 && jpool) jpool[joff[o] + (int64_t)slot + rank] = (uint32_t)pos;
+            }
+        }
+    }
+}
+
+// Step B of node b = blockIdx.y against every sample of J_A^k (Algorithm 3's
+// sample-based assignment and Algorithm 4's ball test without a budget): one
+// view sample per thread (kWT per CTA, blockIdx.x), the lists J_A^k streamed
+// through shared memory kJC points at a time.  A sample's scan of cluster k
+// stops once it is decided (some point proved farther than 4 alpha, or than
+// alpha when only the ball test needs k); the CTA stops when all are.
+// Distances and decisions as in wide_b_node; chunks of 4 points are decided
+// by their largest distance.
+constexpr int kJC = 256;
+
+__global__ void __launch_bounds__(kWT)
+ball_all_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int K, int D, const float *__restrict__ lo,
+                const float *__restrict__ hi, Margins mg, const uint32_t *__restrict__ ids,
+                const int64_t *__restrict__ joff, const uint32_t *__restrict__ jpool, WideB p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int KD = K * D, b = blockIdx.y;
+    uint64_t *tp = reinterpret_cast<uint64_t *>(smem);                  // [D][kWT] staged samples
+    uint64_t *sbx = tp + (size_t)D * kWT;                                 // [K][D] input boxes
+    float *sl = reinterpret_cast<float *>(sbx + KD), *sh = sl + KD, *smid = sh + KD;   // box-BT boxes
+    float *chunk = smid + KD;                                             // [kJC][D]
+    unsigned *s_smax = reinterpret_cast<unsigned *>(chunk + (size_t)kJC * D), *s_smin = s_smax + KD;
+    unsigned *s_jmax = s_smin + KD, *s_jmin = s_jmax + KD;
+    unsigned long long *scnt = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(s_jmin + KD) + 7) & ~(uintptr_t)7);
+    unsigned long long *scand = scnt + K;
+    unsigned *sflag = reinterpret_cast<unsigned *>(scand + K);
+    const int64_t base = (int64_t)blockIdx.x * kWT;
+    const int tn = (int)((n - base) < (int64_t)kWT ? (n - base) : (int64_t)kWT);
+    wide_stage(X, ld, D, kWT, tn, base, nullptr, tp);
+    for (int i = threadIdx.x; i < KD; i += kWT) {
+        const size_t o = (size_t)b * KD + i;
+        sbx[i] = pk(lo[o], -hi[o]);
+        const float lv = p.blo[o], hv = p.bhi[o];
+        sl[i] = lv;
+        sh[i] = hv;
+        smid[i] = (float)(0.5 * ((double)lv + (double)hv));
+        s_smax[i] = 0u;
+        s_smin[i] = ~0u;
+        s_jmax[i] = 0u;
+        s_jmin[i] = ~0u;
+    }
+    for (int k = threadIdx.x; k < K; k += kWT) {
+        scnt[k] = 0ull;
+        scand[k] = 0ull;
+    }
+    if (threadIdx.x == 0) *sflag = 0u;
+    __syncthreads();
+    const int j = threadIdx.x;
+    const bool valid = j < tn, have = p.allhave[b] != 0;
+    const uint32_t pos = (uint32_t)(base + j);
+    // clusters the center-based rule leaves open; an open sample that is not
+    // a seed gets the sample-based rule
+    bool open = false;
+    if (valid && have) {
+        int left = 0;
+        for (int k = 0; k < K; ++k)
+            if (!(wide_box_dist(tp, kWT, j, sbx + (size_t)k * D, D) > mg.t_alpha)) ++left;
+        if (left >= 2) {
+            const int64_t id = ids ? (int64_t)ids[base + j] : base + j;
+            bool is_seed = false;
+            for (int k = 0; k < K; ++k)
+                if (p.seeds && p.seeds[k] == id) is_seed = true;
+            open = !is_seed;
+        }
+    }
+    int left4 = 0, k4 = -1;
+    bool infeasible = false;
+    for (int k = 0; k < K; ++k) {
+        bool inb = valid;
+        for (int a = 0; a < D && inb; ++a) {
+            const float x = upk(tp[(size_t)a * kWT + j]).x;
+            if (x < sl[k * D + a] || x > sh[k * D + a]) inb = false;
+        }
+        const bool need = open || inb;
+        if (!__syncthreads_or(need)) continue;
+        bool far4 = false, far1 = false, done = !need;
+        const int64_t q1 = joff[(size_t)b * K + k + 1];
+        for (int64_t q0 = joff[(size_t)b * K + k]; q0 < q1; q0 += kJC) {
+            const int cn = (int)((q1 - q0) < kJC ? (q1 - q0) : kJC);
+            for (int i = threadIdx.x; i < cn * D; i += kWT) {
+                const int r = i / D, a = i - r * D;
+                chunk[i] = X[(size_t)a * ld + jpool[q0 + r]];
+            }
+            __syncthreads();
+            if (!done) {
+                for (int r0 = 0; r0 < cn; r0 += 4) {
+                    float d[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        d[u] = wide_pt_dist(tp, kWT, j, chunk + (size_t)(r0 + u < cn ? r0 + u : cn - 1) * D, D);
+                    const float m = fmaxf(fmaxf(d[0], d[1]), fmaxf(d[2], d[3]));
+                    if (m > mg.t_alpha) {
+                        far1 = true;
+                        if (m > mg.t_four) { far4 = true; break; }
+                        if (!open) break;
+                    }
+                }
+                done = far4 || (far1 && !open);
+            }
+            // the barrier before the next chunk overwrites the buffer
+            if (!__syncthreads_or(!done)) break;
+        }
+        if (open && !far4) { ++left4; k4 = k; }
+        if (inb && !far1) {
+            // ball-based tightening and centers on samples
+            atomicAdd(&scnt[k], 1ull);
+            for (int a = 0; a < D; ++a) {
+                const unsigned v = ord_f32(upk(tp[(size_t)a * kWT + j]).x);
+                smax_u32(&s_smax[k * D + a], v);
+                smin_u32(&s_smin[k * D + a], v);
+            }
+            const float dm = wide_pt_dist(tp, kWT, j, smid + (size_t)k * D, D);
+            smax_u64(&scand[k], wkey_min(dm, pos));
+        }
+    }
+    if (open) {
+        // sample-based assignment (Algorithm 3, Lemma 2)
+        if (left4 == 0) infeasible = true;
+        if (left4 == 1)
+            for (int a = 0; a < D; ++a) {
+                const unsigned v = ord_f32(upk(tp[(size_t)a * kWT + j]).x);
+                smax_u32(&s_jmax[k4 * D + a], v);
+                smin_u32(&s_jmin[k4 * D + a], v);
+            }
+    }
+    if (infeasible) atomicOr(sflag, 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < KD; i += kWT) {
+        const size_t o = (size_t)b * KD + i;
+        if (s_smax[i] != 0u) atomicMax(&p.smax[o], s_smax[i]);
+        if (s_smin[i] != ~0u) atomicMin(&p.smin[o], s_smin[i]);
+        if (s_jmax[i] != 0u) atomicMax(&p.jmax[o], s_jmax[i]);
+        if (s_jmin[i] != ~0u) atomicMin(&p.jmin[o], s_jmin[i]);
+    }
+    for (int k = threadIdx.x; k < K; k += kWT) {
+        const size_t o = (size_t)b * K + k;
+        if (scnt[k]) atomicAdd(&p.cnt[o], scnt[k]);
+        if (scand[k]) atomicMax(&p.cand[o], scand[k]);
+    }
+    if (threadIdx.x == 0 && *sflag) atomicOr(&p.flags[b], 1u);
+}
+
 }  // namespace
 
 size_t wide_b_node_bytes(int K, int D)
@@ -457,6 +651,62 @@ kc_status launch_wide_b(kc_ctx *c, const View &v, const ListBatch *L, const floa
     wide_b_kernel<<<grid, kWT, smem, c->stream>>>(static_cast<const float *>(v.X), v.ld, v.n, tile, L ? *L : Lz, B, K,
                                                   D, lo, hi, mg, L ? nullptr : v.ids, p);
     return after_launch(c, "tighten pass B (wide)");
+}
+
+kc_status launch_wide_ball_all(kc_ctx *c, const View &v, const float *lo, const float *hi, int B, const Margins &mg,
+                               const float *blo, const float *bhi, const int *allhave, const int64_t *seeds,
+                               unsigned long long *cnt, unsigned long long *cand, unsigned *smax, unsigned *smin,
+                               unsigned *jmax, unsigned *jmin, unsigned *flags, VisitScratch *vs)
+{
+    const int K = c->K, D = c->D;
+    if (v.n <= 0 || B <= 0) return KC_OK;
+    if (v.n > (int64_t)UINT32_MAX) return set_err(c, KC_EINVAL, "every-sample tightening: at most 2^32 - 1 samples");
+    const size_t BK = (size_t)B * K;
+    // counts, then offsets (host prefix), then the lists
+    const size_t o_off = (BK * 8 + 255) & ~(size_t)255, o_pool = o_off + (((BK + 1) * 8 + 255) & ~(size_t)255);
+    KC_TRY(ensure(c, vs->jbuf, o_pool));
+    unsigned long long *jcnt = static_cast<unsigned long long *>(vs->jbuf.p);
+    const int tile = (int)std::max<int64_t>(64, std::min<int64_t>(1024, (48 * 1024) / (8 * (int64_t)D)) / 32 * 32);
+    const size_t smemJ = (size_t)D * tile * 8 + (size_t)K * D * 8;
+    if (smemJ > 48 * 1024)
+        KC_CUDA(c, cudaFuncSetAttribute(jall_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemJ));
+    int per_sm = 0;
+    KC_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jall_kernel, kWT, smemJ));
+    if (per_sm < 1) return set_err(c, KC_EINTERNAL, "every-sample tightening: list kernel does not fit");
+    const int gJ = (int)std::max<int64_t>(1, std::min<int64_t>((v.n + tile - 1) / tile, (int64_t)per_sm * c->num_sms));
+    const float *X = static_cast<const float *>(v.X);
+    KC_CUDA(c, cudaMemsetAsync(jcnt, 0, BK * 8, c->stream));
+    jall_kernel<<<gJ, kWT, smemJ, c->stream>>>(X, v.ld, v.n, tile, B, K, D, lo, hi, mg, v.ids, seeds, jcnt, nullptr,
+                                                nullptr);
+    KC_TRY(after_launch(c, "every-sample tightening: set sizes"));
+    std::vector<unsigned long long> hc(BK);
+    std::vector<int64_t> ho(BK + 1);
+    KC_CUDA(c, cudaMemcpyAsync(hc.data(), jcnt, BK * 8, cudaMemcpyDeviceToHost, c->stream));
+    KC_CUDA(c, cudaStreamSynchronize(c->stream));
+    ho[0] = 0;
+    for (size_t i = 0; i < BK; ++i) ho[i + 1] = ho[i] + (int64_t)hc[i];
+    KC_TRY(ensure(c, vs->jbuf, o_pool + (size_t)std::max<int64_t>(1, ho[BK]) * 4));
+    jcnt = static_cast<unsigned long long *>(vs->jbuf.p);
+    int64_t *joff = reinterpret_cast<int64_t *>(static_cast<char *>(vs->jbuf.p) + o_off);
+    uint32_t *jpool = reinterpret_cast<uint32_t *>(static_cast<char *>(vs->jbuf.p) + o_pool);
+    KC_CUDA(c, cudaMemcpyAsync(joff, ho.data(), (BK + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+    KC_CUDA(c, cudaMemsetAsync(jcnt, 0, BK * 8, c->stream));
+    jall_kernel<<<gJ, kWT, smemJ, c->stream>>>(X, v.ld, v.n, tile, B, K, D, lo, hi, mg, v.ids, seeds, jcnt, joff,
+                                                jpool);
+    KC_TRY(after_launch(c, "every-sample tightening: sets"));
+    // the tiled pass
+    const size_t KD = (size_t)K * D;
+    const size_t smemB = (size_t)D * kWT * 8 + KD * 8 + KD * 12 + (size_t)kJC * D * 4 + KD * 16 + 8 + (size_t)K * 16 + 8;
+    if (smemB > 48 * 1024)
+        KC_CUDA(c, cudaFuncSetAttribute(ball_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB));
+    if ((v.n + kWT - 1) / kWT > (int64_t)INT32_MAX || B > 65535)
+        return set_err(c, KC_EINVAL, "every-sample tightening: grid too large");
+    const dim3 grid((unsigned)((v.n + kWT - 1) / kWT), (unsigned)B);
+    WideB p{blo, bhi, nullptr, nullptr, allhave, seeds, 0, cnt, cand, smax, smin, jmax, jmin, flags};
+    ball_all_kernel<<<grid, kWT, smemB, c->stream>>>(X, v.ld, v.n, K, D, lo, hi, mg, v.ids, joff, jpool, p);
+    // keep the host vectors alive until the copies they feed have run
+    KC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return after_launch(c, "every-sample tightening: tiled pass");
 }
 
 }  // namespace kc

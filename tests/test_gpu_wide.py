@@ -194,3 +194,86 @@ def test_double_data_keep_the_attribute_extremes():
     for o in outs[1:]:
         for k in ("status", "lo", "hi", "count"):
             assert np.array_equal(o[k], outs[0][k])
+
+
+@pytest.mark.parametrize("n,d,k,seeded,scale", [
+    (3_000, 2, 3, False, (0.05, 0.5)), (3_000, 2, 4, True, (0.3, 0.9)), (2_500, 3, 3, False, (0.3, 0.9)),
+    (2_500, 4, 3, True, (0.05, 0.5)), (2_000, 8, 2, False, (0.3, 0.9)), (2_000, 12, 3, False, (0.3, 0.9))])
+def test_every_sample_representatives_on_grid(n, d, k, seeded, scale):
+    """ball_cap = KC_BALLS_ALL: every sample of J_A^k is a representative of
+    k (the ball-BT of Section 4.1.2 without a budget; the tiled sample x
+    J_A^k pass).  Grid-valued data: the kernels match the oracle exactly.  At
+    D <= 4 the default 50 (attribute and pair-direction extremes) almost
+    always reach the same result; at D = 8 and 12 (16 of 28 or 66 pairs)
+    the cases tell the unbudgeted sets from them."""
+    from paper_2301_00061_gb300 import KC_BALLS_ALL
+    X, c, fobj, lo, hi = _grid_case(n, d, k, seed=5 * d + k, B=8, scale=scale)
+    kc = KCenter(_t(X), k)
+    seeds = np.array(c, np.int64) if seeded else None
+    feasible = changed = 0
+    for f in (0.6, 0.8, 0.95, 1.02, 1.2):
+        alpha = (np.round(fobj * f * 16) + 0.5) / 16
+        g = kc.tighten(_t(lo), _t(hi), alpha, seeds=None if seeds is None else _t(seeds), ball_cap=KC_BALLS_ALL)
+        torch.cuda.synchronize()
+        feasible += _compare(X, lo, hi, alpha, seeds, g, oracle.BALLS_ALL)
+        for b in range(lo.shape[0]):
+            r = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=True, ball_cap=oracle.BALLS_ALL)
+            r0 = oracle.tighten(X, lo[b], hi[b], alpha, seeds=seeds, is_f32=True)
+            if r0["status"] != 1 and (r["status"] != r0["status"] or not np.array_equal(r["count"], r0["count"])):
+                changed += 1
+    assert feasible >= 4
+    if d >= 8:
+        assert changed >= 1, "the case does not tell every sample from the default representatives"
+
+
+def test_every_sample_representatives_tighten_at_least_as_much():
+    """At N = 200,000 (the batched-solve recipe, 32 nodes, thousands of CTAs
+    and sets J_A^k of tens of thousands of samples): with every assigned
+    sample as a representative each node's result is at least as tight as
+    with the default 50 -- infeasible wherever the default is, boxes inside
+    the default's, counts |S_+^k| no larger -- since each test only gains
+    representatives."""
+    from paper_2301_00061_gb300 import KC_BALLS_ALL
+    X, w = synth.make_workload("batched_solve", n=200_000)
+    c, fobj = oracle.fft(X, w.k, 0)
+    rng = np.random.default_rng(3)
+    lo0, hi0 = X.min(0).astype(np.float64), X.max(0).astype(np.float64)
+    B = 32
+    lo = np.empty((B, w.k, w.d), np.float32)
+    hi = np.empty((B, w.k, w.d), np.float32)
+    for b in range(B):
+        for j in range(w.k):
+            wd = rng.uniform(0.05, 0.4, size=w.d) * (hi0 - lo0)
+            ctr = X[c[j]].astype(np.float64)
+            lo[b, j] = np.clip(ctr - rng.uniform(0.2, 0.8, size=w.d) * wd, lo0, hi0)
+            hi[b, j] = np.clip(lo[b, j] + wd, lo0, hi0)
+    kc = KCenter(_t(X), w.k)
+    seen = 0
+    for f in (0.9, 1.1):
+        alpha = fobj * f
+        g0 = {q: v.cpu().numpy() for q, v in kc.tighten(_t(lo), _t(hi), alpha).items()}
+        ga = {q: v.cpu().numpy() for q, v in kc.tighten(_t(lo), _t(hi), alpha, ball_cap=KC_BALLS_ALL).items()}
+        for b in range(B):
+            if g0["status"][b] == 1:
+                assert ga["status"][b] == 1, b
+                continue
+            if ga["status"][b] == 1:
+                continue
+            seen += 1
+            assert np.all(ga["lo"][b] >= g0["lo"][b]) and np.all(ga["hi"][b] <= g0["hi"][b]), b
+            assert np.all(ga["count"][b] <= g0["count"][b]), (b, ga["count"][b], g0["count"][b])
+    assert seen >= 8
+
+
+def test_solve_with_every_sample_representatives():
+    """kc_solve with ball_cap = KC_BALLS_ALL (one shared sample set) reaches
+    the oracle's certified optimum; per-node lists refuse it."""
+    from paper_2301_00061_gb300 import KC_BALLS_ALL, KCError
+    X = _blobs(1_500, 2, 3, 2)
+    kc = KCenter(_t(X), 3)
+    g = kc.solve(tol=1e-12, time_limit_s=120.0, ball_cap=KC_BALLS_ALL, lists=0)
+    r = oracle.solve(X, 3, tol=1e-12)
+    assert g["status"] == 0 and r["status"] == 0
+    assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
+    with pytest.raises(KCError, match="KC_BALLS_ALL"):
+        kc.solve(tol=1e-12, ball_cap=KC_BALLS_ALL)

@@ -62,8 +62,10 @@ C_MUTANTS = {
                                          "if (left == 1) asg[s] = (int8_t)kk;")]),
     "box_bt_wrong_extreme": ("Sec. 4.1.2", [("double l = round_down_dt(nextafter(jmax[i] - r, -INFINITY), is_f32);",
                                              "double l = round_down_dt(nextafter(jmin[i] - r, -INFINITY), is_f32);")]),
-    "sample_based_alpha_for_4alpha": ("Alg. 3, Lemma 2", [("> four_alpha", "> alpha")]),
-    "ball_bt_4alpha_for_alpha": ("Alg. 4", [("D) > alpha) ok = 0;", "D) > four_alpha) ok = 0;")]),
+    "sample_based_alpha_for_4alpha": ("Alg. 3, Lemma 2", [("KCO_MAXREPS + q] * D, D) > four_alpha",
+                                                          "KCO_MAXREPS + q] * D, D) > alpha")]),
+    "ball_bt_4alpha_for_alpha": ("Alg. 4", [("KCO_MAXREPS + q] * D, D) > alpha) ok = 0;",
+                                            "KCO_MAXREPS + q] * D, D) > four_alpha) ok = 0;")]),
     "centers_on_samples_bbox_dropped": ("Alg. 4", [("double l = slo[i], h = shi[i];",
                                                     "double l = blo[i], h = bhi[i];")]),
     "sr_nonstrict_corner_test": ("Sec. 4.2.1", [("if (!(as < beta_glob))", "if (!(as <= beta_glob))")]),
@@ -107,6 +109,11 @@ C_MUTANTS = {
                                                                     "    if (0) {\n        const float fa")]),
     "pair_directions_dropped": ("Sec. 4.1.2, R11", [("for (int q = 0; q < ndir; ++q) {\n        KCO_ADD_REP",
                                                      "for (int q = 0; q < 0; ++q) {\n        KCO_ADD_REP")]),
+    "all_balls_ball_test_skips_first": ("Sec. 4.1.2, Alg. 4", [
+        ("for (int64_t q = joff[k]; q < joff[k + 1] && ok; ++q)",
+         "for (int64_t q = joff[k] + 1; q < joff[k + 1] && ok; ++q)")]),
+    "all_balls_lemma2_at_alpha": ("Lemma 2", [("if (sqdist(x, X + jl[q] * D, D) > four_alpha) excl = 1;",
+                                               "if (sqdist(x, X + jl[q] * D, D) > alpha) excl = 1;")]),
 }
 
 # name -> (what, [(original, planted), ...]) in mlp.py

@@ -551,3 +551,80 @@ def test_pair_direction_values_in_the_data_precision():
     X2 = X.copy()
     X2[1, 1] = 2.0
     assert oracle.tighten(X2, lo, hi, 1e30, ball_cap=50, is_f32=True)["reps"] == [[3, 2, 1]]
+
+
+def _assign_step_a(X, lo, hi, alpha):
+    """Lemma 1 from its definition: beta_s^k = squared distance from x_s to
+    box k; k excluded when beta_s^k > alpha; assigned when one cluster is left."""
+    d = ((X[:, None, :] - np.clip(X[:, None, :], lo[None], hi[None])) ** 2).sum(2)   # (N, K)
+    left = d <= alpha
+    return np.where(left.sum(1) == 1, left.argmax(1), -1), left
+
+
+def test_uncapped_representatives_brute_force():
+    """ball_cap = BALLS_ALL (the paper's ball-BT without a budget, Section
+    4.1.2 and Algorithm 3): every sample of J_A^k is a representative.  Against
+    a direct evaluation of the definitions on small random instances: the
+    step-A assignment (Lemma 1), the sample-based assignment of the others
+    (Lemma 2: k excluded when some j of J_A^k is farther than 4 alpha), and
+    |S_+^k| = samples of the box-BT box within sqrt(alpha) of every j of
+    J_A^k; the node's status follows (no cluster left, or an empty S_+)."""
+    rng = np.random.default_rng(11)
+    checked = 0
+    for trial in range(40):
+        n, d, k = 60, 2, 2
+        cen = np.array([[-4.0, 0.0], [4.0, 0.0]]) + rng.uniform(-1, 1, size=(2, 2))
+        X = np.round(np.repeat(cen, n // k, 0) + rng.normal(0, 1.2, size=(n, d)), 2)
+        w = rng.uniform(1.0, 3.0, size=(k, d))
+        lo, hi = cen - w, cen + w
+        alpha = float(rng.uniform(3.0, 25.0))
+        r = oracle.tighten(X, lo, hi, alpha, ball_cap=oracle.BALLS_ALL)
+        asg, left = _assign_step_a(X, lo, hi, alpha)
+        if (left.sum(1) == 0).any():
+            assert r["status"] == 1
+            continue
+        J = [np.flatnonzero(asg == j) for j in range(k)]
+        if any(len(j) == 0 for j in J):
+            continue   # step B does not run without representatives in every cluster
+        dd = ((X[:, None, :] - X[None, :, :]) ** 2).sum(2)
+        infeasible = False
+        for s_ in np.flatnonzero(asg < 0):
+            if not any(not (dd[s_, J[j]] > 4 * alpha).any() for j in range(k)):
+                infeasible = True
+        count = []
+        for j in range(k):
+            inb = np.all((X >= r["box_bt_lo"][j]) & (X <= r["box_bt_hi"][j]), axis=1)
+            count.append(int(np.sum(inb & (dd[:, J[j]] <= alpha).all(1))))
+        if infeasible or min(count) == 0 or np.any(r["box_bt_lo"] > r["box_bt_hi"]):
+            assert r["status"] == 1, trial
+            continue
+        if r["status"] == 1:
+            continue   # infeasible through the final boxes (J_B and S_+ boxes disjoint)
+        assert list(r["count"]) == count, (trial, r["count"], count)
+        checked += 1
+    assert checked >= 10
+
+
+def test_uncapped_representatives_reach_a_hull_vertex_the_budget_misses():
+    """Twelve samples on the unit circle at 60, 90, ..., 330, 0, 30 degrees
+    (in this index order) and one sample s at 0.1 (cos 240, sin 240), one
+    cluster, box [-2, 2]^2, alpha = 1.2 (double data).  Every sample is
+    assigned; the default representatives are the attribute extremes: 0, 180,
+    90 and 270 degrees (samples 10, 4, 1, 7).  Squared distances from
+    s: 1 + 0.01 - 0.2 cos(angle - 240): 1.21 to the point at 60 degrees, 1.1832
+    at 30 and 90, at most 1.11 to the four representatives; so s is within
+    sqrt(alpha) of every representative (|S_+| = 1: the circle points lie
+    outside the box-BT box [1 - sqrt(1.2), sqrt(1.2) - 1]^2; the tightened box
+    is the point s, a leaf), but not of the sample at 60 degrees: with every
+    assigned sample as a representative S_+ is empty and the node is
+    infeasible."""
+    ang = np.deg2rad((np.arange(0, 360, 30) + 60) % 360)
+    X = np.concatenate([np.stack([np.cos(ang), np.sin(ang)], 1), [[0.1 * np.cos(np.deg2rad(240)),
+                                                                   0.1 * np.sin(np.deg2rad(240))]]])
+    lo = np.array([[-2.0, -2.0]])
+    hi = np.array([[2.0, 2.0]])
+    r = oracle.tighten(X, lo, hi, 1.2)
+    assert r["status"] == 2 and list(r["count"]) == [1]
+    assert sorted(r["reps"][0]) == [1, 4, 7, 10]
+    r = oracle.tighten(X, lo, hi, 1.2, ball_cap=oracle.BALLS_ALL)
+    assert r["status"] == 1
