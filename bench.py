@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--solve-n", type=int, default=10_000_000,
                    help="N of the batched-solve workload timed to a certified optimum (0: skip)")
     p.add_argument("--no-hbm-points", action="store_true")
+    p.add_argument("--every-sample-n", type=int, default=200_000,
+                   help="N of the tightening comparison: every sample of J_A^k against the default 50 (0: skip)")
     p.add_argument("--solve-time-limit", type=float, default=60.0)
     p.add_argument("--solve-arena-mb", type=int, default=0,
                    help="device memory (MiB) for the solve's per-node lists (0: automatic; profiling runs "
@@ -191,6 +193,43 @@ def time_events(fn, iters, stream, torch):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / iters
+
+
+def every_sample_point(kcm, torch, dev, stream, n, B=32, iters=3):
+    """kc_tighten on B nodes of the batched-solve recipe at N = n (boxes around
+    the farthest-first centers, alpha 1.1 x their objective) with the default
+    representatives (at most 50 per cluster) and with every sample of J_A^k
+    (KC_BALLS_ALL, the tiled sample x J_A^k pass): device time per call (CUDA
+    events, after one warm-up call each) and the nodes whose status or counts
+    the two settings decide differently."""
+    X, w = synth.make_workload("batched_solve", n=n)
+    kc = kcm.KCenter(torch.from_numpy(X).to(dev), w.k)
+    c, obj = kc.fft(0)
+    c = np.asarray(c).astype(np.int64)
+    alpha = 1.1 * float(np.asarray(obj).reshape(-1)[0])
+    rng = np.random.default_rng(3)
+    lo0, hi0 = X.min(0).astype(np.float64), X.max(0).astype(np.float64)
+    lo = np.empty((B, w.k, w.d), np.float32)
+    hi = np.empty((B, w.k, w.d), np.float32)
+    for b in range(B):
+        for j in range(w.k):
+            wd = rng.uniform(0.05, 0.4, size=w.d) * (hi0 - lo0)
+            ctr = X[c[j]].astype(np.float64)
+            lo[b, j] = np.clip(ctr - rng.uniform(0.2, 0.8, size=w.d) * wd, lo0, hi0)
+            hi[b, j] = np.clip(lo[b, j] + wd, lo0, hi0)
+    lo_t, hi_t = torch.from_numpy(lo).to(dev), torch.from_numpy(hi).to(dev)
+    out = {}
+    for name, cap in (("default", 0), ("every_sample", kcm.KC_BALLS_ALL)):
+        g = kc.tighten(lo_t, hi_t, alpha, ball_cap=cap)
+        out[name] = {q: v.cpu().numpy() for q, v in g.items()}
+        out[name + "_ms"] = time_events(lambda: kc.tighten(lo_t, hi_t, alpha, ball_cap=cap), iters, stream, torch)
+    kc.close()
+    differ = int(sum(1 for b in range(B) if out["default"]["status"][b] != out["every_sample"]["status"][b]
+                     or not np.array_equal(out["default"]["count"][b], out["every_sample"]["count"][b])))
+    return {"workload": f"batched_solve N={n:,} D={w.d} K={w.k}, {B} nodes, alpha = 1.1 x FFT objective",
+            "ms_default": out["default_ms"], "ms_every_sample": out["every_sample_ms"],
+            "nodes_decided_differently": differ,
+            "timed": "kc_tighten call, CUDA events, %d calls each" % iters}
 
 
 def one_node_point(kcm, torch, dev, stream, h, lo4, hi4, n, d, k, name, hbm_peak, iters):
@@ -504,6 +543,11 @@ def main():
         kc.close()
         sc.close()
 
+    # ---- tightening without a representatives' budget against the default
+    every = None
+    if args.every_sample_n > 0:
+        every = every_sample_point(kcm, torch, dev, stream, args.every_sample_n)
+
     cfg = config_dict(n, w)
     cfg["autotuned"] = {"samples_per_thread": tuned_st, "nodes_per_launch": tuned_chunk}
     line = {
@@ -518,6 +562,8 @@ def main():
         line["solve"] = solve
     if learned is not None:
         line["learned_order"] = learned
+    if every is not None:
+        line["every_sample_tighten"] = every
     if rank == 0 and not args.no_cpu_baseline:
         model = cpu_model()
         rate_p, dt_p, nt = cpu_oracle_rate_all_cores(X, lo, hi, 2_000_000)
