@@ -462,7 +462,36 @@ jall_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int tile, int B,
 // Distances and decisions as in wide_b_node; chunks of 4 points are decided
 // by their largest distance.
 constexpr int kJC = 256;
+constexpr int kAllMaxD = 16;
 
+// wide_pt_dist with the sample in registers as coordinate pairs (xp[p] =
+// (x_2p, x_2p+1), zero beyond D; xlast = x_{D-1}): the same pairs, chains
+// and order.
+template <int DM>
+struct RegSample {
+    uint64_t xp[DM / 2];
+    float xlast;
+};
+
+template <int DM>
+__device__ __forceinline__ float reg_pt_dist(const RegSample<DM> &x, const float *c, int D)
+{
+    uint64_t acc = 0;
+#pragma unroll
+    for (int p = 0; p < DM / 2; ++p)
+        if (2 * p + 1 < D) {
+            const uint64_t t = sub2(x.xp[p], pk(c[2 * p], c[2 * p + 1]));
+            acc = fma2(t, t, acc);
+        }
+    float2 s = upk(acc);
+    if (D & 1) {
+        const float t = x.xlast - c[D - 1];
+        s.x = fmaf(t, t, s.x);
+    }
+    return s.x + s.y;
+}
+
+template <int DM>   // D <= DM (2, 4, 8 or 16): the unrolled width of the distance scans
 __global__ void __launch_bounds__(kWT)
 ball_all_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int K, int D, const float *__restrict__ lo,
                 const float *__restrict__ hi, Margins mg, const uint32_t *__restrict__ ids,
@@ -519,6 +548,13 @@ ball_all_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int K, int D
             open = !is_seed;
         }
     }
+    // the thread's sample in registers for the distance scans
+    RegSample<DM> xr;
+    xr.xlast = upk(tp[(size_t)(D - 1) * kWT + j]).x;
+#pragma unroll
+    for (int p = 0; p < DM / 2; ++p)
+        xr.xp[p] = pk(2 * p < D ? upk(tp[(size_t)(2 * p) * kWT + j]).x : 0.f,
+                      2 * p + 1 < D ? upk(tp[(size_t)(2 * p + 1) * kWT + j]).x : 0.f);
     int left4 = 0, k4 = -1;
     bool infeasible = false;
     for (int k = 0; k < K; ++k) {
@@ -543,7 +579,7 @@ ball_all_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int K, int D
                     float d[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
-                        d[u] = wide_pt_dist(tp, kWT, j, chunk + (size_t)(r0 + u < cn ? r0 + u : cn - 1) * D, D);
+                        d[u] = reg_pt_dist(xr, chunk + (size_t)(r0 + u < cn ? r0 + u : cn - 1) * D, D);
                     const float m = fmaxf(fmaxf(d[0], d[1]), fmaxf(d[2], d[3]));
                     if (m > mg.t_alpha) {
                         far1 = true;
@@ -697,13 +733,16 @@ kc_status launch_wide_ball_all(kc_ctx *c, const View &v, const float *lo, const 
     // the tiled pass
     const size_t KD = (size_t)K * D;
     const size_t smemB = (size_t)D * kWT * 8 + KD * 8 + KD * 12 + (size_t)kJC * D * 4 + KD * 16 + 8 + (size_t)K * 16 + 8;
-    if (smemB > 48 * 1024)
-        KC_CUDA(c, cudaFuncSetAttribute(ball_all_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB));
     if ((v.n + kWT - 1) / kWT > (int64_t)INT32_MAX || B > 65535)
         return set_err(c, KC_EINVAL, "every-sample tightening: grid too large");
+    if (D > kAllMaxD) return set_err(c, KC_EINVAL, "every-sample tightening: D <= %d", kAllMaxD);
     const dim3 grid((unsigned)((v.n + kWT - 1) / kWT), (unsigned)B);
     WideB p{blo, bhi, nullptr, nullptr, allhave, seeds, 0, cnt, cand, smax, smin, jmax, jmin, flags};
-    ball_all_kernel<<<grid, kWT, smemB, c->stream>>>(X, v.ld, v.n, K, D, lo, hi, mg, v.ids, joff, jpool, p);
+    auto kern = D <= 2 ? ball_all_kernel<2> : D <= 4 ? ball_all_kernel<4> : D <= 8 ? ball_all_kernel<8>
+                                                                              : ball_all_kernel<16>;
+    if (smemB > 48 * 1024)
+        KC_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemB));
+    kern<<<grid, kWT, smemB, c->stream>>>(X, v.ld, v.n, K, D, lo, hi, mg, v.ids, joff, jpool, p);
     // keep the host vectors alive until the copies they feed have run
     KC_CUDA(c, cudaStreamSynchronize(c->stream));
     return after_launch(c, "every-sample tightening: tiled pass");
