@@ -516,7 +516,18 @@ def main():
                  "certified": r["status"] == 0, "objective": r["objective"], "lower_bound": r["lower_bound"],
                  "gap": r["gap"], "nodes": int(r["nodes"]), "batches": int(r["batches"]),
                  "lists_filtered": int(r["lists_filtered"]), "fft_100_starts": fft100}
+        # the same instance in the committed scorer's order
+        from paper_2301_00061_gb300 import scorer as kc_scorer
+        sc = kcm.Scorer(kc_scorer.load())
+        kc.set_scorer(sc)
+        torch.cuda.synchronize()
+        barrier()
+        r1 = kc.solve(tol=1e-12, order=1, time_limit_s=args.solve_time_limit, arena_mb=args.solve_arena_mb)
+        solve["learned_order"] = {"seconds": max_over_ranks(r1["seconds"], ws), "nodes": int(r1["nodes"]),
+                                  "certified": r1["status"] == 0, "objective": r1["objective"],
+                                  "same_objective": r1["objective"] == r["objective"]}
         kc.close()
+        sc.close()
         del Xsd
 
     # ---- learned node order against best bound on the learned-order recipe
