@@ -26,7 +26,7 @@
  * Errors.  Every call returns a kc_status; nothing is thrown across the ABI.
  * On failure the outputs are unspecified and kc_last_error() describes the
  * cause.  After KC_ECUDA the context should be destroyed; after any other
- * error it stays usable.  Limits: 1 <= K <= 16, 1 <= D <= 64,
+ * error it stays usable.  Limits: 1 <= K <= 16, 1 <= D <= 128,
  * K <= N <= 4,294,967,294.
  */
 #ifndef KC_H_
@@ -293,7 +293,7 @@ kc_status kc_fp32_probe(int32_t mode, void *stream, double *lane_ops_per_s, floa
  * x_a - x_b (added in float) for the first min(D(D-1)/2, 16) pairs a < b in
  * lexicographic order; ties go to the smaller sample index, duplicates are
  * skipped.  Double data stop after the attribute extremes (2D + 1).
- * Shapes: float data any K <= 16 and D <= 64 (K <= 4 with D <= 4 and K <= 2
+ * Shapes: float data any K <= 16 and D <= 128 (K <= 4 with D <= 4 and K <= 2
  * with D <= 8 run kernels with the node's state in registers, compiled per
  * shape; the others kernels whose node state lives in shared memory sized at
  * launch); double data K <= 4 with D <= 4.  Other shapes return KC_EINVAL.
@@ -422,7 +422,7 @@ void kc_solve_defaults(kc_solve_opts *opt);
  * overrides opt->tol when >= 0.  Returns KC_OK at optimality within tol,
  * KC_ETIMEOUT / KC_ELIMIT (with *out filled) at a limit, KC_EINVAL for
  * options out of range, KC_ENOMEM when the list arena or buffers do not fit.
- * Shapes: those of kc_tighten (float K <= 16, D <= 64; double K <= 4 with
+ * Shapes: those of kc_tighten (float K <= 16, D <= 128; double K <= 4 with
  * D <= 4); other shapes return KC_EINVAL.  Float data with D > 8 scan one
  * shared sample set (no per-node lists) without sample reduction.
  */

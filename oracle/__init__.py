@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MAXK, MAXD, MAXREPS = 16, 64, 50
+MAXK, MAXD, MAXREPS = 16, 128, 50
 BALLS_ALL = -1   # ball_cap: every sample assigned to a cluster is one of its representatives
 
 

@@ -31,7 +31,7 @@
 #endif
 
 #define KCO_MAXK 16
-#define KCO_MAXD 64
+#define KCO_MAXD 128
 #define KCO_MAXREPS 50
 /* ball_cap value: every sample assigned to cluster k in step A is a
  * representative of k (no budget; the paper's unrestricted ball-BT) */

@@ -16,7 +16,7 @@
 namespace kc {
 
 constexpr int kMaxK = 16;
-constexpr int kMaxD = 64;
+constexpr int kMaxD = 128;
 constexpr int kMaxReps = 50;
 constexpr int kMaxPairs = 16;   // attribute pairs a < b along which representatives are taken
 constexpr int kThreads = 256;
@@ -225,7 +225,7 @@ kc_status launch_sample_reduction_view(kc_ctx *c, const View &v, const void *lo,
                                        const void *repx, const int *nreps, int R, double beta_glob, double alpha,
                                        uint8_t *mask, unsigned long long *n_active);
 
-// Passes A and B of the float tightening for any K <= 16, D <= 64 (kc_wide.cu;
+// Passes A and B of the float tightening for any K <= 16, D <= 128 (kc_wide.cu;
 // the workspace and finalize kernels are kc_visit.cu's).
 // Step B with every sample of J_A^k as a representative of k (no budget):
 // builds the sets J_A^k of the B nodes as lists of view positions in

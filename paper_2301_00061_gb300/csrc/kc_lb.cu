@@ -530,21 +530,12 @@ kc_status launch_lower_bounds_cfg(kc_ctx *c, const View &v, const void *lo, cons
                         static_cast<unsigned long long *>(c->part.p));
             } else {
                 const int64_t tiles = (v.n + kThreads - 1) / kThreads;
-                if (D <= 16) {
-                    KC_TRY(prep_kernel(c, lb_f32_generic<16>, smem, &grid, tiles));
-                    KC_TRY(ensure(c, c->part, (size_t)grid * nb * 8));
-                    if (v.n > 0)
-                        lb_f32_generic<16><<<grid, kThreads, smem, c->stream>>>(
-                            static_cast<const float *>(v.X), v.ld, v.n, l, h, nb, K, D,
-                            static_cast<unsigned long long *>(c->part.p));
-                } else {
-                    KC_TRY(prep_kernel(c, lb_f32_generic<64>, smem, &grid, tiles));
-                    KC_TRY(ensure(c, c->part, (size_t)grid * nb * 8));
-                    if (v.n > 0)
-                        lb_f32_generic<64><<<grid, kThreads, smem, c->stream>>>(
-                            static_cast<const float *>(v.X), v.ld, v.n, l, h, nb, K, D,
-                            static_cast<unsigned long long *>(c->part.p));
-                }
+                auto g = D <= 16 ? lb_f32_generic<16> : (D <= 64 ? lb_f32_generic<64> : lb_f32_generic<128>);
+                KC_TRY(prep_kernel(c, g, smem, &grid, tiles));
+                KC_TRY(ensure(c, c->part, (size_t)grid * nb * 8));
+                if (v.n > 0)
+                    g<<<grid, kThreads, smem, c->stream>>>(static_cast<const float *>(v.X), v.ld, v.n, l, h, nb, K, D,
+                                                           static_cast<unsigned long long *>(c->part.p));
             }
             if (v.n > 0) KC_TRY(after_launch(c, "lower bound"));
             const int nparts = v.n > 0 ? grid : 0;
@@ -564,21 +555,14 @@ kc_status launch_lower_bounds_cfg(kc_ctx *c, const View &v, const void *lo, cons
             const double *h = static_cast<const double *>(hi) + (size_t)b0 * K * D;
             const int64_t tiles = (v.n + kThreads - 1) / kThreads;
             int grid = 1;
-            if (D <= 16) {
-                KC_TRY(prep_kernel(c, lb_f64<16>, smem, &grid, tiles));
-            } else {
-                KC_TRY(prep_kernel(c, lb_f64<64>, smem, &grid, tiles));
-            }
+            auto g = D <= 16 ? lb_f64<16> : (D <= 64 ? lb_f64<64> : lb_f64<128>);
+            KC_TRY(prep_kernel(c, g, smem, &grid, tiles));
             KC_TRY(ensure(c, c->part, (size_t)grid * nb * 12));
             double *pval = static_cast<double *>(c->part.p);
             uint32_t *ppos = reinterpret_cast<uint32_t *>(pval + (size_t)grid * nb);
             if (v.n > 0) {
-                if (D <= 16)
-                    lb_f64<16><<<grid, kThreads, smem, c->stream>>>(static_cast<const double *>(v.X), v.ld,
-                                                                    v.n, l, h, nb, K, D, pval, ppos);
-                else
-                    lb_f64<64><<<grid, kThreads, smem, c->stream>>>(static_cast<const double *>(v.X), v.ld,
-                                                                    v.n, l, h, nb, K, D, pval, ppos);
+                g<<<grid, kThreads, smem, c->stream>>>(static_cast<const double *>(v.X), v.ld, v.n, l, h, nb, K, D, pval,
+                                                       ppos);
                 KC_TRY(after_launch(c, "lower bound f64"));
             }
             lb_finalize_f64<<<(nb + 3) / 4, 128, 0, c->stream>>>(
@@ -622,7 +606,7 @@ kc_status launch_lower_bounds_refine(kc_ctx *c, const View &v, const void *lo, c
         const size_t smem = (size_t)K * Dp * 8 * nb + (size_t)((nb + 1) & ~1) * 4 + (size_t)NW * 12 * nb;
         const int64_t tiles = (v.n + kThreads - 1) / kThreads;
         int grid = 1;
-        auto kern = D <= 16 ? lb_refine_f32<16> : lb_refine_f32<64>;
+        auto kern = D <= 16 ? lb_refine_f32<16> : (D <= 64 ? lb_refine_f32<64> : lb_refine_f32<128>);
         KC_TRY(prep_kernel(c, kern, smem, &grid, tiles));
         const size_t thr_off = 0, part_off = 256 + (size_t)nb * 4;
         KC_TRY(ensure(c, c->part, part_off + (size_t)grid * nb * 12 + 256));
@@ -781,7 +765,7 @@ extern "C" kc_status kc_lower_bounds_noalloc(const float *X, int64_t N, int64_t 
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fast, kThreads, smem) != cudaSuccess)
                 return KC_ECUDA;
         } else {
-            auto g = D <= 16 ? lb_f32_generic<16> : lb_f32_generic<64>;
+            auto g = D <= 16 ? lb_f32_generic<16> : (D <= 64 ? lb_f32_generic<64> : lb_f32_generic<128>);
             if (smem > 48 * 1024 &&
                 cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
                 return KC_ECUDA;
@@ -795,10 +779,9 @@ extern "C" kc_status kc_lower_bounds_noalloc(const float *X, int64_t N, int64_t 
         if (N > 0) {
             if (fast)
                 fast<<<grid, kThreads, smem, st>>>(X, ld, N, l, h, nb, part);
-            else if (D <= 16)
-                lb_f32_generic<16><<<grid, kThreads, smem, st>>>(X, ld, N, l, h, nb, K, D, part);
             else
-                lb_f32_generic<64><<<grid, kThreads, smem, st>>>(X, ld, N, l, h, nb, K, D, part);
+                (D <= 16 ? lb_f32_generic<16> : (D <= 64 ? lb_f32_generic<64> : lb_f32_generic<128>))
+                    <<<grid, kThreads, smem, st>>>(X, ld, N, l, h, nb, K, D, part);
             if (cudaGetLastError() != cudaSuccess) return KC_ECUDA;
         }
         lb_finalize_f32<<<(nb + 3) / 4, 128, 0, st>>>(part, N > 0 ? grid : 0, nb, nullptr, defl, slack, lb_out + b0,

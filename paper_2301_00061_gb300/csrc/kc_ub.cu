@@ -376,8 +376,10 @@ kc_status objective_chunk(kc_ctx *c, const View &v, const int64_t *centers, int 
         const size_t smem1 = sets_bytes + (size_t)NW * S * 8;
         const size_t smem2 = sets_bytes + (size_t)((S + 1) & ~1) * 4 + (size_t)NW * S * 12;
         int g1 = 1, g2 = 1;
-        auto k1 = Dh <= 4 ? obj_screen_f32<4> : (Dh <= 8 ? obj_screen_f32<8> : obj_screen_f32<32>);
-        auto k2 = Dh <= 4 ? obj_exact_f32<4> : (Dh <= 8 ? obj_exact_f32<8> : obj_exact_f32<32>);
+        auto k1 = Dh <= 4 ? obj_screen_f32<4>
+                          : (Dh <= 8 ? obj_screen_f32<8> : (Dh <= 32 ? obj_screen_f32<32> : obj_screen_f32<64>));
+        auto k2 = Dh <= 4 ? obj_exact_f32<4>
+                          : (Dh <= 8 ? obj_exact_f32<8> : (Dh <= 32 ? obj_exact_f32<32> : obj_exact_f32<64>));
         KC_TRY(grid_for(c, k1, smem1, v.n, &g1));
         KC_TRY(grid_for(c, k2, smem2, v.n, &g2));
         const int gmax = g1 > g2 ? g1 : g2;
@@ -413,7 +415,8 @@ kc_status objective_chunk(kc_ctx *c, const View &v, const int64_t *centers, int 
     } else {
         const size_t smem = (size_t)S * Kc * D * 8 + (size_t)NW * S * 12;
         int g = 1;
-        auto k = D <= 8 ? obj_exact_f64<8> : (D <= 16 ? obj_exact_f64<16> : obj_exact_f64<64>);
+        auto k = D <= 8 ? obj_exact_f64<8>
+                        : (D <= 16 ? obj_exact_f64<16> : (D <= 64 ? obj_exact_f64<64> : obj_exact_f64<128>));
         KC_TRY(grid_for(c, k, smem, v.n, &g));
         KC_TRY(ensure(c, c->work, (size_t)g * S * 12 + 64));
         double *pval = static_cast<double *>(c->work.p);

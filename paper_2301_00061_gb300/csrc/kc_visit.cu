@@ -1314,7 +1314,7 @@ kc_status tighten_impl(kc_ctx *c, const View &v, const void *lo_, const void *hi
     return KC_OK;
 }
 
-// The wide path (float data, K <= 16, D <= 64): the workspace, finalize
+// The wide path (float data, K <= 16, D <= 128): the workspace, finalize
 // kernels and outputs of tighten_impl, passes A and B from kc_wide.cu.
 // Representatives per cluster: min(cap, 2D + 1, 50) along the attributes, or,
 // with `dirs`, up to min(cap, 50) with the attribute-pair directions after

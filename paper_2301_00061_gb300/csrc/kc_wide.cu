@@ -1,6 +1,6 @@
 // kc_wide.cu -- cluster assignment and bounds tightening (Section 4.1,
 // Algorithms 3-4) for float data of any shape up to K = 16 clusters and
-// D = 64 attributes (the compile-time kernels of kc_visit.cu cover the small
+// D = 128 attributes (the compile-time kernels of kc_visit.cu cover the small
 // shapes).  Same decisions, same proofs of float exclusions, same outputs.
 //
 // Layout of the work: a CTA stages a tile of samples in shared memory (packed

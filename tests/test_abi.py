@@ -96,7 +96,7 @@ def test_noalloc_rejects_bad_sizes_before_touching_cuda(kcpkg):
         a = {**ok, **kw}
         return f(a["X"], a["N"], a["ld"], a["D"], a["K"], a["lo"], a["hi"], a["B"], a["lb"], None, None, None)
 
-    for bad in (dict(B=4097), dict(B=-1), dict(K=0), dict(K=17), dict(D=0), dict(D=65), dict(N=-1),
+    for bad in (dict(B=4097), dict(B=-1), dict(K=0), dict(K=17), dict(D=0), dict(D=129), dict(N=-1),
                 dict(ld=9), dict(N=2 ** 32, ld=2 ** 32), dict(X=None), dict(lo=None), dict(hi=None), dict(lb=None)):
         assert call(**bad) == 1, bad
     assert call(B=0) == 0

@@ -297,3 +297,40 @@ def test_sharded_calls_with_one_rank_equal_the_library():
         assert np.array_equal(cf, rc) and of == ro
     finally:
         dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("d,k", [(68, 3), (128, 2)])
+def test_bounds_at_high_dimension(d, k):
+    """D = 68 (the largest data set of the paper's Table 4 has 68 attributes)
+    and D = 128, the library's limit: float lower bounds within the proved
+    gap 2 gamma_n below the oracle's FP64 value (n = ceil(D/2) + 3 roundings,
+    gamma_n = n u / (1 - n u), u = 2^-24) and never above it; double lower
+    bounds and the objective of center sets bit-identical; the farthest first
+    traversal equal to the oracle's."""
+    n_r = (d + 1) // 2 + 3
+    u = 2.0 ** -24
+    rel = 2 * n_r * u / (1 - n_r * u)
+    for dtype in (np.float32, np.float64):
+        X = _mix(20_003, d, k, seed=d + k, dtype=dtype)
+        lo, hi = synth.random_boxes(X, k, 9, seed=d, frac_lo=0.0, frac_hi=0.5)
+        kc = KCenter(_t(X), k)
+        lb, raw, arg = kc.lower_bounds(_t(lo), _t(hi))
+        torch.cuda.synchronize()
+        ref, refarg = oracle.lower_bounds(X, lo, hi)
+        lbn = lb.cpu().numpy()
+        if dtype == np.float64:
+            assert np.array_equal(raw.cpu().numpy(), ref)
+            assert np.array_equal(arg.cpu().numpy(), refarg)
+        else:
+            assert np.all(lbn <= ref), np.max(lbn - ref)
+            assert np.all(lbn >= ref * (1 - rel)), np.min(lbn / np.maximum(ref, 1e-300))
+        C = np.random.default_rng(d).integers(0, X.shape[0], size=(3, k))
+        ub, worst = kc.upper_bound(_t(C))
+        torch.cuda.synchronize()
+        for s in range(C.shape[0]):
+            v, a = oracle.objective(X, C[s])
+            assert float(ub[s]) == v and int(worst[s]) == a
+        c, obj = kc.fft(5)
+        rc, robj = oracle.fft(X, k, 5)
+        assert list(np.asarray(c.cpu() if hasattr(c, "cpu") else c)) == list(rc)
+        assert float(np.asarray(obj.cpu() if hasattr(obj, "cpu") else obj).reshape(-1)[0]) == robj

@@ -1,21 +1,21 @@
 """The float tightening kernels for shapes without a compile-time
-instantiation (any K <= 16, D <= 64; node state in shared memory) against
+instantiation (any K <= 16, D <= 128; node state in shared memory) against
 the FP64 oracle, and the solver on such shapes (Section 4.1, Algorithms 3-4;
 Algorithm 1).
 
 Tightening inputs sit on a grid: coordinates are multiples of 1/4 and node
 boxes are rounded outward to that grid, so every clamp and sample distance
-is a multiple of 1/16 computed exactly in float (D <= 64, coordinates below
-64 in magnitude), and alpha is an odd multiple of 1/32: float and double
-take every decision alike and statuses, boxes and counts must equal the
-oracle's (candidates, nearest to an off-grid midpoint, within the float
-argmin's error).  The representatives are the seed and the attribute
-extremes, then, for ball_cap above 2D + 1, the extremes of x_a + x_b and
+is a multiple of 1/16 computed exactly in float (coordinates below 64 in
+magnitude, squared distances summing below 2^20), and alpha is an odd
+multiple of 1/32: float and double take every decision alike and statuses,
+boxes and counts must equal the oracle's (candidates, nearest to an
+off-grid midpoint, within the float argmin's error).  The representatives
+are the seed and the attribute extremes, then the extremes of x_a + x_b and
 x_a - x_b over the first 16 attribute pairs, at most min(ball_cap, 50) per
-cluster on both sides: D = 29 exercises the cap of 50 within the attribute
-extremes, D = 2 .. 16 with ball_cap = 50 the pair directions.  Sums and
-differences of grid coordinates are exact in float, so they order samples
-alike on both sides.
+cluster on both sides: D = 29 .. 128 exercise the cap of 50 within the
+attribute extremes, D = 2 .. 16 the pair directions.  Sums and differences
+of grid coordinates are exact in float, so they order samples alike on
+both sides.
 """
 import numpy as np
 import pytest
@@ -97,7 +97,8 @@ def _compare(X, lo, hi, alpha, seeds, g, cap):
 
 @pytest.mark.parametrize("n,d,k,cap,seeded", [
     (6_000, 12, 3, 50, False), (6_000, 16, 5, 50, True), (4_000, 29, 3, 9, False), (4_000, 29, 3, 25, False),
-    (4_000, 29, 3, 50, True), (8_000, 2, 5, 50, False), (6_000, 6, 3, 50, False), (3_000, 64, 2, 50, False)])
+    (4_000, 29, 3, 50, True), (8_000, 2, 5, 50, False), (6_000, 6, 3, 50, False), (3_000, 64, 2, 50, False),
+    (3_000, 68, 3, 50, False), (2_000, 128, 2, 50, True)])
 def test_wide_tighten_exact_on_grid(n, d, k, cap, seeded):
     X, c, fobj, lo, hi = _grid_case(n, d, k, seed=d + k, B=10, scale=(0.05, 0.5))
     kc = KCenter(_t(X), k)
@@ -112,7 +113,7 @@ def test_wide_tighten_exact_on_grid(n, d, k, cap, seeded):
 
 
 @pytest.mark.parametrize("n,d,k,seed", [(1_500, 12, 3, 1), (1_500, 16, 3, 1), (1_000, 29, 3, 1), (2_000, 2, 5, 1),
-                                        (1_500, 3, 6, 1)])
+                                        (1_500, 3, 6, 1), (800, 68, 3, 1)])
 def test_wide_solve_matches_oracle(n, d, k, seed):
     """Solves on the wide shapes (D > 8: one shared sample set without sample
     reduction; K = 5, 6 with D <= 8: per-node lists) reach the oracle's
@@ -277,3 +278,35 @@ def test_solve_with_every_sample_representatives():
     assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
     with pytest.raises(KCError, match="KC_BALLS_ALL"):
         kc.solve(tol=1e-12, ball_cap=KC_BALLS_ALL)
+
+
+def test_every_sample_representatives_argument_errors_and_edges():
+    """KC_BALLS_ALL is refused for double data and for D > 16 (KC_EINVAL,
+    the context stays usable); an empty batch is a no-op; a node whose boxes
+    assign nothing (every J_A^k empty) gets no sample-based step, as in the
+    oracle."""
+    from paper_2301_00061_gb300 import KC_BALLS_ALL, KCError
+    Xd = _blobs(400, 2, 3, 1, dtype=np.float64)
+    kd = KCenter(_t(Xd), 3)
+    lo = np.broadcast_to(Xd.min(0), (1, 3, 2)).copy()
+    hi = np.broadcast_to(Xd.max(0), (1, 3, 2)).copy()
+    with pytest.raises(KCError, match="KC_BALLS_ALL"):
+        kd.tighten(_t(lo), _t(hi), 10.0, ball_cap=KC_BALLS_ALL)
+    kd.tighten(_t(lo), _t(hi), 10.0)   # still usable
+    X17 = _blobs(300, 17, 2, 1)
+    k17 = KCenter(_t(X17), 2)
+    lo17 = np.broadcast_to(X17.min(0), (1, 2, 17)).copy()
+    hi17 = np.broadcast_to(X17.max(0), (1, 2, 17)).copy()
+    with pytest.raises(KCError, match="KC_BALLS_ALL"):
+        k17.tighten(_t(lo17), _t(hi17), 10.0, ball_cap=KC_BALLS_ALL)
+    X, c, fobj, glo, ghi = _grid_case(1_000, 2, 3, seed=7, B=4, scale=(0.05, 0.5))
+    kc = KCenter(_t(X), 3)
+    g = kc.tighten(_t(glo[:0]), _t(ghi[:0]), fobj, ball_cap=KC_BALLS_ALL)
+    assert g["status"].shape[0] == 0
+    # the root: equal boxes, nothing assigned, no sample-based step
+    L = np.broadcast_to(X.min(0).astype(np.float32), (1, 3, 2)).copy()
+    H = np.broadcast_to(X.max(0).astype(np.float32), (1, 3, 2)).copy()
+    alpha = (np.round(fobj * 16) + 0.5) / 16
+    g = kc.tighten(_t(L), _t(H), alpha, ball_cap=KC_BALLS_ALL)
+    torch.cuda.synchronize()
+    _compare(X, L, H, alpha, None, g, oracle.BALLS_ALL)
