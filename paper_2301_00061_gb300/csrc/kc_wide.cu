@@ -447,7 +447,10 @@ jall_kernel(const float *__restrict__ X, int64_t ld, int64_t n, int tile, int B,
                 const size_t o = (size_t)b * K + (kk < 0 ? 0 : kk);
                 if (kk >= 0 && lane == leader) slot = atomicAdd(&jcnt[o], (unsigned long long)__popc(grp));
                 slot = __shfl_sync(grp, slot, leader);
-                if (kk >= 0 && jpool) jpool[joff[o] + (int64_t)slot + rank] = (uint32_t)pos;
+                // the counting pass took the same decisions; the bound keeps a
+                // write inside its set regardless
+                const int64_t at = joff ? joff[o] + (int64_t)slot + rank : 0;
+                if (kk >= 0 && jpool && at < joff[o + 1]) jpool[at] = (uint32_t)pos;
             }
         }
     }
