@@ -848,8 +848,15 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
         // the parent's list when there is no room or little is dropped
         // The filter also bounds the children over the surviving samples
         // (flb/fraw[2 * row + side]); fused_row[i]: node i's row, or -1.
+        // by default a child shares its parent's list (also when no filter runs)
         std::vector<int> kid_list(NB, -1), fused_row(NB, -1);
         std::vector<int8_t> kid_fwait(NB, 0), kid_fstreak(NB, 0);
+        for (int i = 0; i < NB; ++i) {
+            const Node<T> &nd = batch[br[i]];
+            kid_list[i] = nd.list;
+            kid_fwait[i] = nd.fwait > 0 ? (int8_t)(nd.fwait - 1) : (int8_t)0;
+            kid_fstreak[i] = nd.fstreak;
+        }
         std::vector<double> flb, fraw;
         std::vector<int64_t> farg;
         if (lists && NB > 0 && o.i_sr > 0 && batches % o.i_sr == 0) {
@@ -859,9 +866,6 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
             const int64_t room = arena.cap - arena.used;
             for (int i = 0; i < NB; ++i) {
                 const Node<T> &nd = batch[br[i]];
-                kid_list[i] = nd.list;
-                kid_fwait[i] = nd.fwait > 0 ? (int8_t)(nd.fwait - 1) : (int8_t)0;
-                kid_fstreak[i] = nd.fstreak;
                 const int64_t n = list_n(nd.list);
                 if (n < 2 * LT || nd.fwait > 0) continue;
                 if (n > 4 * room) {

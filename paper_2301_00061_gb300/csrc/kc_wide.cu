@@ -651,7 +651,9 @@ kc_status launch_wide_a(kc_ctx *c, const View &v, const ListBatch *L, const floa
 {
     const int K = c->K, D = c->D, KD = K * D;
     if (ndir > 32) return set_err(c, KC_EINTERNAL, "wide tightening: at most 16 attribute pairs");
-    const int tile = (int)std::max<int64_t>(64, std::min<int64_t>(1024, (48 * 1024) / (8 * (int64_t)D)) / 32 * 32);
+    // a list batch is laid out in list_tile() entries per work item
+    const int tile = L ? list_tile()
+                       : (int)std::max<int64_t>(64, std::min<int64_t>(1024, (48 * 1024) / (8 * (int64_t)D)) / 32 * 32);
     const size_t smem = (size_t)D * tile * 8 + (size_t)KD * 24 + (size_t)K * ndir * 16 + 16 + 32 + (size_t)tile * 4 +
                         16;
     if (smem > 48 * 1024)
@@ -675,7 +677,9 @@ kc_status launch_wide_b(kc_ctx *c, const View &v, const ListBatch *L, const floa
                         unsigned *flags)
 {
     const int K = c->K, D = c->D;
-    const int tile = (int)std::max<int64_t>(64, std::min<int64_t>(1024, (48 * 1024) / (8 * (int64_t)D)) / 32 * 32);
+    // a list batch is laid out in list_tile() entries per work item
+    const int tile = L ? list_tile()
+                       : (int)std::max<int64_t>(64, std::min<int64_t>(1024, (48 * 1024) / (8 * (int64_t)D)) / 32 * 32);
     const size_t smem = (size_t)D * tile * 8 + wide_b_node_bytes(K, D) + (size_t)tile * 4 + 16;
     if (smem > 48 * 1024)
         KC_CUDA(c, cudaFuncSetAttribute(wide_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

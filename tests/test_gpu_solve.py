@@ -549,11 +549,14 @@ def test_solve_degenerate_and_edge_inputs():
     kc5.close()
 
 
-@pytest.mark.parametrize("d,k", [(3, 3), (3, 4), (6, 2), (8, 2), (4, 4)])
+@pytest.mark.parametrize("d,k", [(3, 3), (3, 4), (6, 2), (8, 2), (4, 4), (7, 3), (8, 3), (8, 4), (5, 5)])
 def test_solve_f32_lists_other_shapes(d, k):
     """Per-node lists with the remaining compiled tightening shapes (K=3 D=3,
-    K<=4 D<=4, K<=2 D<=8): the certified optimum equals the oracle's.  Seed 1
-    of each shape gives a tree of 15-1,600 oracle nodes."""
+    K<=4 D<=4, K<=2 D<=8) and with the shared-memory kernels in list mode
+    (K >= 3 at D = 7, 8, where their sample tile for a shared set is smaller
+    than a list batch's work item, and K = 5 at D = 5): the certified optimum
+    equals the oracle's.  Seed 1 of each shape gives a tree of 15-4,400
+    oracle nodes."""
     X = _blobs(2_500, d, k, seed=1, dtype=np.float32)
     g, r = _solve_both(X, k, lists=1)
     assert g["status"] == 0
@@ -587,3 +590,30 @@ def test_solve_limits_and_repeatability():
         for a, b in zip(outs[0], o):
             assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
     kc.close()
+
+
+@pytest.mark.parametrize("n,seed", [(600, 1), (1_000, 2)])
+def test_solve_at_the_microbenchmark_shape(n, seed):
+    """The lower-bound microbenchmark's shape (D = 8, K = 5, nested clusters of
+    the lb_microbench recipe) solved to the 1e-12 certificate on small N (per-
+    node lists, the shared-memory tightening kernels): the oracle's optimum,
+    and the objective is the exact double value of the returned centers."""
+    X, w = synth.make_workload("lb_microbench", n=n, seed=seed)
+    kc = KCenter(_t(X), w.k)
+    g = kc.solve(tol=1e-12, time_limit_s=120.0)
+    r = oracle.solve(X, w.k, tol=1e-12)
+    assert g["status"] == 0 and r["status"] == 0
+    assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
+    assert oracle.objective(X, g["centers"])[0] == g["objective"]
+
+
+@pytest.mark.parametrize("i_sr", [0, 2])
+def test_solve_lists_with_filters_off_or_every_other_batch(i_sr):
+    """Per-node lists with the children's filter off (i_sr = 0: every child
+    keeps its parent's list) or run every other batch: the oracle's optimum."""
+    X = _blobs(3_000, 2, 3, seed=5, dtype=np.float32)
+    kc = KCenter(_t(X), 3)
+    g = kc.solve(tol=1e-12, time_limit_s=60.0, i_sr=i_sr)
+    r = oracle.solve(X, 3, tol=1e-12)
+    assert g["status"] == 0 and r["status"] == 0
+    assert abs(g["objective"] - r["objective"]) <= 1e-12 * r["objective"], (g, r)
