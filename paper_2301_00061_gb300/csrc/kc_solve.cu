@@ -1068,7 +1068,14 @@ kc_status solve_impl(kc_ctx *c, const kc_solve_opts &o, kc_result *res)
                 ch.list = kid_list[i];
                 ch.fwait = kid_fwait[i];
                 ch.fstreak = kid_fstreak[i];
-                if (lists) arena.ref(ch.list);
+                if (lists) {
+                    // every node of a list-mode solve holds a list (an empty one is
+                    // a valid list of length 0; a missing one is a logic error)
+                    if (ch.list < 0 || ch.list >= (int)arena.recs.size())
+                        return set_err(c, KC_EINTERNAL, "kc_solve: child %lld without a sample list",
+                                       (long long)ch.id);
+                    arena.ref(ch.list);
+                }
                 kids.push_back(std::move(ch));
                 kid_fused.push_back(fused_row[i] >= 0 ? 2 * fused_row[i] + side : -1);
             }
