@@ -501,7 +501,10 @@ class KCenter:
         """Cluster assignment and bounds tightening of B nodes given the upper
         bound alpha (Algorithms 3-4): tightened boxes, |S_+^k| counts,
         candidates, the input boxes' certified bound and a status per node
-        (0 feasible, 1 infeasible, 2 leaf)."""
+        (0 feasible, 1 infeasible, 2 leaf).  ball_cap: representatives per
+        cluster, at most min(ball_cap, 50) (<= 0: 50; the seed, attribute
+        extremes, then for float data pair-direction extremes), or
+        KC_BALLS_ALL: every sample step A assigns to the cluster."""
         B = lo.shape[0]
         lo_o = self._alloc(lo, tuple(lo.shape), "data")
         hi_o = self._alloc(lo, tuple(lo.shape), "data")
