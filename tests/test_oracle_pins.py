@@ -233,6 +233,26 @@ def test_solve_matches_bruteforce(seed, use_bt, use_sr):
         assert oracle.objective(X, r["centers"])[0] == r["objective"]
 
 
+@pytest.mark.parametrize("ball_cap", [1, 5, oracle.BALLS_ALL])
+def test_solve_with_any_representatives_matches_bruteforce(ball_cap):
+    """Lemma 2 and the ball test are sound for any set of assigned samples as
+    representatives (Section 4.1.2): with one, five or every assigned sample,
+    in double and in float data, the branch and bound reaches the brute-force
+    optimum."""
+    for seed in range(4):
+        rng = np.random.default_rng(100 + seed)
+        n = int(rng.integers(10, 26))
+        for f32 in (False, True):
+            X = _blobs(n, 2, 40 + seed)
+            if f32:
+                X = X.astype(np.float32).astype(np.float64)
+            for k in (2, 3):
+                r = oracle.solve(X, k, tol=0.0, ball_cap=ball_cap, is_f32=f32, seed=seed)
+                z, _ = oracle.bruteforce(X, k)
+                assert r["objective"] == pytest.approx(z, rel=1e-12), (seed, f32, k)
+                assert r["lower_bound"] <= r["objective"]
+
+
 def test_solve_float32_data_matches_bruteforce():
     for seed in range(4):
         X = synth.gaussian_mixture(25, 2, (0.5, 0.5), (1.0, 1.0), (1.0, 1.0), 5.0, seed,
